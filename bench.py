@@ -1,0 +1,362 @@
+"""Benchmark: block-sparse H_eff*psi useful TFLOP/s on GB300 (one JSON line).
+
+A step is one pass of the whole hot path: a 20-step Lanczos solve on the
+two-site DMRG effective Hamiltonian of the spin-1/2 Heisenberg chain at
+chi = 512 with U(1) charges (21 sectors, binomial degeneracies), each matvec
+one H_eff*psi network contraction (device matching tables + relayout +
+grouped GEMM, in the order found by the library's DP search), the Lanczos
+vector work in FP64 on the device.  Useful flops are 2*m*k*n over the matched
+block pairs of every pairwise contraction, times the number of matvecs.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl tnx|reference]
+                  [--workload chi512|chi2048|dense32] [--prec split_bf16|f64|...]
+
+--impl reference times the plain CPU FP64 oracle on the host cores (bounded
+sample) on the same metric.  With N > 1 (torchrun, NCCL) every rank runs an
+independent replica (the path has no exchange step); the value is the total
+useful flops of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H_eff*psi useful TFLOP/s (Lanczos solve, block-sparse U(1))"
+LANCZOS_STEPS = 20
+
+
+def workload(name: str):
+    import tnx_inputs as I
+    if name == "chi512":
+        return I.heisenberg_workload(512, 20), "heisenberg_u1_chi512_d2_D5_lanczos20"
+    if name == "chi2048":
+        return I.heisenberg_workload(2048, 40, sector_scale=True), "heisenberg_u1_chi2048_d2_D5_sectorscaled_lanczos20"
+    if name == "dense32":
+        return I.dense_workload(32), "heisenberg_dense_chi32_d2_D5_lanczos20"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) > 8:
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def fp64_peak_tflops(torch, dev):
+    """Measured cuBLAS FP64 GEMM throughput (no FP64 entry in the driver's peaks file)."""
+    n = 4096
+    a = torch.randn(n, n, device=dev, dtype=torch.float64)
+    b = torch.randn(n, n, device=dev, dtype=torch.float64)
+    for _ in range(2):
+        a @ b
+    torch.cuda.synchronize(dev)
+    best = 1e9
+    for _ in range(3):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        a @ b
+        e.record()
+        torch.cuda.synchronize(dev)
+        best = min(best, s.elapsed_time(e))
+    del a, b
+    return 2 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def cpu_oracle_sample(wl, seconds: float = 12.0):
+    """The oracle as it stands on the host cores: repeated H_eff applies for ~seconds."""
+    from oracle import heff as oheff
+    net, T = oheff.make_heff(wl, symmetric=True)
+    rec = []
+    net.launch(record=rec)
+    flops = sum(r["flops"] for r in rec)
+    op = oheff.flat_apply(net, T["psi"])
+    x = T["psi"].flat()
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        op(x)
+        n += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return flops * n / dt / 1e12, n, dt, flops
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl, wname = workload(args.workload)
+    from oracle import heff as oheff
+    net, T = oheff.make_heff(wl, symmetric=True)
+    rec = []
+    net.launch(record=rec)
+    flops = sum(r["flops"] for r in rec)
+    op = oheff.flat_apply(net, T["psi"])
+    x = T["psi"].flat()
+    for _ in range(args.warmup):
+        op(x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        op(x)
+    dt = time.perf_counter() - t0
+    val = flops * args.steps / dt / 1e12
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wname, "sample": "one H_eff*psi apply per step (oracle, numpy FP64)"},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} H_eff*psi applies of {wname} on the host"},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tnx", choices=["tnx", "reference"])
+    ap.add_argument("--workload", default="chi512")
+    ap.add_argument("--prec", default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2401_01921_gb300 as tnx
+    import tnx_inputs as I
+    from paper_2401_01921_gb300.heff import build_network
+
+    wl, wname = workload(args.workload)
+    ctx = tnx.Context(local)
+    bonds = I.heff_bonds(wl)
+    tensors = {n: (bonds[n], I.heff_value_fn(wl, n, symmetric=True)) for n in I.HEFF_NAMES}
+
+    prec = args.prec
+    if prec == "auto":
+        prec = "split_bf16"
+        try:
+            net, T, B = build_network(ctx, I.HEFF_SPEC, tensors, wl.nsym, prec=prec)
+            net.flops()
+            tnx.lanczos(net, "psi", T["psi"], 2)
+        except tnx.TnxError as e:
+            if e.name != "TNX_ERR_UNSUPPORTED":
+                raise
+            prec = "f64"
+    net, T, B = build_network(ctx, I.HEFF_SPEC, tensors, wl.nsym, prec=prec)
+    apply_flops = net.flops()
+    evec = tnx.Tensor(ctx, B["psi"])
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        return tnx.lanczos(net, "psi", T["psi"], LANCZOS_STEPS, evec)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    ctx.sync()
+
+    # ---- timed region: K steps, L2 flushed (untimed) before each, CUDA events on the library stream
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = tnx.kernel_launches()
+    ctx.profile(True)
+    times = []
+    matvecs = 0
+    evals = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            lam, k = step()
+            e.record(stream)
+            matvecs += k
+            evals.append(lam)
+            torch.cuda.synchronize(dev)
+            times.append(s.elapsed_time(e))
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    launches = tnx.kernel_launches() - launches0
+    torch.cuda.synchronize(dev)
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    useful = apply_flops * matvecs
+    value = useful * world / (total_ms * 1e-3) / 1e12
+
+    # ---- e2e through the C-ABI with host buffers (pinned), copies inside the timed region
+    host = {}
+    for n in I.HEFF_NAMES:
+        x = T[n].download()
+        pin = torch.empty(x.size, dtype=torch.float64, pin_memory=True)
+        pin.numpy()[:] = x
+        host[n] = pin
+    out_pin = torch.empty(evec.nelem, dtype=torch.float64, pin_memory=True)
+    h2d = sum(host[n].numel() * 8 for n in I.HEFF_NAMES)
+    d2h = evec.nelem * 8 + 8
+    import ctypes as C
+
+    def e2e_step():
+        for n in I.HEFF_NAMES:
+            ctx.check(tnx.lib().tnx_tensor_upload(T[n].h, C.cast(host[n].data_ptr(), C.POINTER(C.c_double)),
+                                                  host[n].numel()))
+        lam, k = step()
+        ctx.check(tnx.lib().tnx_tensor_download(evec.h, C.cast(out_pin.data_ptr(), C.POINTER(C.c_double)),
+                                                out_pin.numel()))
+        return k
+
+    e2e_step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e2e_ms = 0.0
+    e2e_mv = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e2e_mv += e2e_step()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = apply_flops * e2e_mv * world / (e2e_ms * 1e-3) / 1e12
+
+    # ---- roofline of the dominant kernel class (grouped GEMM), timed live above
+    gms, gn, gwork = prof["gemm"]
+    pk = peaks()
+    if prec == "f64":
+        fp64 = fp64_peak_tflops(torch, dev)
+        peak, peak_src = fp64, "measured cuBLAS FP64 GEMM 4096^3 in this run"
+        achieved = gwork / (gms * 1e-3) / 1e12
+    else:
+        peak = pk["bf16_tflops_sustained"] if pk else 1700.0
+        peak_src = "MEASURED_PEAKS.json bf16_tflops_sustained" if pk else "fallback 1.7 PFLOP/s sustained"
+        achieved = gwork / (gms * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "kernel": "grouped GEMM (%s), useful flops per launch / CUDA-event launch time" % prec,
+                "flops_per_launch": gwork / max(gn, 1), "avg_launch_ms": gms / max(gn, 1), "peak_source": peak_src,
+                "kernel_ms": {k: v[0] for k, v in prof.items()}, "kernel_launches": {k: v[1] for k, v in prof.items()},
+                "relayout_GBps": (prof["relayout"][2] / (prof["relayout"][0] * 1e-3) / 1e9) if prof["relayout"][0] else None}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        v, n, dt, fl = cpu_oracle_sample(wl)
+        cpu = {"value": v, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n} oracle H_eff*psi applies of {wname} ({dt:.1f} s, numpy FP64, default BLAS threads)"}
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "f64" else f"f64 via {prec} slices (fp32 acc, int64 recombine)",
+            "data": "synthetic",
+            "config": {"workload": wname, "chi": wl.chi, "sectors": len(wl.left_sectors), "d": 2, "D": 5,
+                       "lanczos_steps": LANCZOS_STEPS, "precision": prec, "order": net.get_order(),
+                       "apply_useful_flops": apply_flops, "matvecs": matvecs,
+                       "l2": "flushed (512 MiB write) before each timed step",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "eigenvalue": evals[-1]},
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,248 @@
+/*
+ * tnx.h - C-ABI of the GB300 (sm_103a) block-sparse tensor-network library.
+ *
+ * The calls follow the problem statement of arXiv 2401.01921 ("The Cytnx
+ * Library for Tensor Networks"): declare charged indices (bonds), build
+ * block-sparse tensors, declare a network with its contraction order,
+ * contract it, and run Lanczos on the contraction as a linear operator.
+ * Section numbers below refer to that paper.
+ *
+ * Conventions shared by every call
+ *  - All functions return a tnx_status: 0 (TNX_OK) or a negative error code.
+ *    Nothing is thrown across the ABI.  tnx_last_error(ctx) returns a
+ *    NUL-terminated message for the last failing call made with that context
+ *    (thread-unsafe: one context per host thread).
+ *  - Device memory comes from the allocator callback given to
+ *    tnx_ctx_create (NULL callbacks: cudaMallocAsync / cudaFreeAsync on the
+ *    context stream).  The library never frees memory it did not allocate.
+ *  - Work is enqueued asynchronously on the context stream; tnx_sync and the
+ *    blocking getters (tnx_tensor_get_block, tnx_lanczos results) join it.
+ *  - Element type: FP64 (double) everywhere on the public surface.
+ *  - Handles are owned by the caller, who destroys each one exactly once.
+ *    A network keeps references to the tensors put into it (no copy, the
+ *    reference semantics of Sec. 3.2); a tensor must outlive its use by a
+ *    network launch.
+ */
+#ifndef TNX_H
+#define TNX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int tnx_status;
+
+enum {
+  TNX_OK = 0,
+  TNX_ERR_ARG = -1,            /* invalid argument, NULL handle, out-of-range size */
+  TNX_ERR_BOND_MISMATCH = -2,  /* contracted bonds differ in dimension, direction,
+                                  charges or block dimensions (Sec. 7) */
+  TNX_ERR_SYMMETRY = -3,       /* operation would break the block structure: scalar
+                                  add on a symmetric tensor (Sec. 6.3), symmetry-
+                                  violating entry in a conversion (Sec. 6.5) */
+  TNX_ERR_NO_BLOCK = -4,       /* the requested block does not exist (Sec. 6.3.2) */
+  TNX_ERR_NETWORK = -5,        /* network text, missing put, bad ORDER (Sec. 8) */
+  TNX_ERR_OOM = -6,            /* allocator returned NULL */
+  TNX_ERR_TIMEOUT = -7,        /* a bounded device wait ran out */
+  TNX_ERR_CUDA = -8,           /* a CUDA runtime call failed */
+  TNX_ERR_UNSUPPORTED = -9     /* shape outside the implemented limits */
+};
+
+/* Symmetry kinds (Sec. 6.1): U(1) combines by addition; Z_n by (Q1+Q2) mod n.
+ * Both reverse a charge by negation (mod n for Z_n). */
+enum { TNX_U1 = 0, TNX_ZN = 1 };
+
+/* Bond directions (Sec. 4, Sec. 6.2): IN (ket) = +1, OUT (bra) = -1,
+ * REGULAR (no symmetry) = 0. */
+enum { TNX_BD_IN = 1, TNX_BD_OUT = -1, TNX_BD_REG = 0 };
+
+/* Arithmetic of the block products (not part of the paper; the paper's GPU
+ * path uses library FP64 GEMMs, Sec. 10).
+ *  TNX_PREC_F64       native FP64 products.
+ *  TNX_PREC_SPLIT_BF16 / _F16  error-free slicing of each FP64 operand into
+ *      integer-valued BF16 / FP16 slices with a common power-of-two scale per
+ *      row of A and per column of B (Ozaki, Ogita, Oishi, Rump, "Error-free
+ *      transformations of matrix multiplication by using fast routines of
+ *      matrix multiplication and its applications", Numer. Algorithms 59,
+ *      2012); slice products on the tcgen05 tensor cores, exact in FP32 over
+ *      K chunks, recombined exactly in 64-bit integers, rounded once to FP64.
+ *  TNX_PREC_F32       operands rounded to FP32, FP32 products and sums.
+ *  TNX_PREC_TF32      operands rounded to TF32 on the tensor cores (one pass). */
+enum { TNX_PREC_F64 = 0, TNX_PREC_SPLIT_BF16 = 1, TNX_PREC_SPLIT_F16 = 2,
+       TNX_PREC_F32 = 3, TNX_PREC_TF32 = 4 };
+
+typedef struct tnx_ctx tnx_ctx;
+typedef struct tnx_bond tnx_bond;
+typedef struct tnx_tensor tnx_tensor;
+typedef struct tnx_network tnx_network;
+
+/* Device allocator callback: returns a device pointer of at least nbytes
+ * (256-byte aligned) or NULL.  free receives exactly the pointers alloc
+ * returned.  Both are called on the host thread that makes the tnx call. */
+typedef void* (*tnx_alloc_fn)(size_t nbytes, void* user);
+typedef void (*tnx_free_fn)(void* ptr, size_t nbytes, void* user);
+
+/* ---------------------------------------------------------------- context */
+
+/* Returns the message of the last error on ctx (never NULL). */
+const char* tnx_last_error(const tnx_ctx* ctx);
+
+/* Library version string ("tnx <major>.<minor>"). */
+const char* tnx_version(void);
+
+/* Create a context on CUDA device `device`, enqueueing on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  alloc/free may be NULL
+ * (stream-ordered CUDA allocation).  *out receives the handle. */
+tnx_status tnx_ctx_create(int device, void* stream, tnx_alloc_fn alloc, tnx_free_fn free,
+                          void* alloc_user, tnx_ctx** out);
+/* Destroys the context; tensors, bonds and networks made with it must be
+ * destroyed first.  Synchronises the stream. */
+tnx_status tnx_ctx_destroy(tnx_ctx* ctx);
+/* Blocks until all work enqueued on the context stream has finished. */
+tnx_status tnx_sync(tnx_ctx* ctx);
+
+/* ------------------------------------------------------------------ bonds */
+
+/* A bond with quantum numbers (Sec. 6.2.1): direction, nsym symmetries
+ * (kinds[i] in {TNX_U1, TNX_ZN}, zn[i] = n for Z_n, ignored for U(1)), and nsec
+ * sectors in creation order, sector k having charges qnums[k*nsym .. k*nsym+nsym)
+ * and degeneracy degs[k] >= 1.  nsym = 0 with dir = TNX_BD_REG makes a plain
+ * bond of dimension degs[0] (nsec must be 1).  Arrays are copied. */
+tnx_status tnx_bond_create(tnx_ctx* ctx, int dir, int nsym, const int* kinds, const int* zn,
+                           int nsec, const int32_t* qnums, const int64_t* degs, tnx_bond** out);
+/* Total dimension (sum of degeneracies). */
+tnx_status tnx_bond_dim(const tnx_bond* b, int64_t* dim);
+/* Sec. 6.2.2: combine two bonds with equal direction and symmetries; sectors
+ * with equal charge are grouped, the result is sorted ascending by charge. */
+tnx_status tnx_bond_combine(const tnx_bond* a, const tnx_bond* b, tnx_bond** out);
+/* Number of sectors, and (optional, may be NULL) their charges and degeneracies. */
+tnx_status tnx_bond_sectors(const tnx_bond* b, int* nsec, int32_t* qnums, int64_t* degs);
+tnx_status tnx_bond_destroy(tnx_bond* b);
+
+/* ---------------------------------------------------------------- tensors */
+
+/* Sec. 6.3.1: a block-sparse FP64 tensor over `rank` bonds (copied).  Only
+ * zero-flux blocks are stored: the charges of IN legs combined with the
+ * reversed charges of OUT legs vanish.  Blocks are numbered in lexicographic
+ * order of their sector indices ("Qn indices"); each block is a dense
+ * row-major array over the tensor's leg order; the blocks lie back to back in
+ * one device buffer, zero-filled.  rank = 0 gives a scalar (one element). */
+tnx_status tnx_tensor_create(tnx_ctx* ctx, int rank, tnx_bond* const* bonds, tnx_tensor** out);
+tnx_status tnx_tensor_destroy(tnx_tensor* t);
+tnx_status tnx_tensor_rank(const tnx_tensor* t, int* rank);
+tnx_status tnx_tensor_nblocks(const tnx_tensor* t, int64_t* n);
+/* Block `blk`: its sector indices qn_idx[rank], shape[rank] and element offset
+ * in the buffer (any output pointer may be NULL). */
+tnx_status tnx_tensor_block_info(const tnx_tensor* t, int64_t blk, int32_t* qn_idx, int64_t* shape,
+                                 int64_t* offset);
+/* All blocks at once: qn_idx[nblk*rank], shape[nblk*rank], offset[nblk] (any may be NULL). */
+tnx_status tnx_tensor_blocks(const tnx_tensor* t, int32_t* qn_idx, int64_t* shape, int64_t* offset);
+/* Borrowed device pointer to the element buffer and its element count. */
+tnx_status tnx_tensor_data(tnx_tensor* t, double** dev_ptr, int64_t* nelem);
+/* Copy host data into the block with sector indices qn_idx (n = its size);
+ * TNX_ERR_NO_BLOCK if that block is not stored (Sec. 6.3.2). Synchronous. */
+tnx_status tnx_tensor_put_block(tnx_tensor* t, const int32_t* qn_idx, const double* host, int64_t n);
+/* Copy the block out to host memory.  Synchronous. */
+tnx_status tnx_tensor_get_block(const tnx_tensor* t, const int32_t* qn_idx, double* host, int64_t n);
+/* Whole buffer host <-> device (n = nelem), synchronous. */
+tnx_status tnx_tensor_upload(tnx_tensor* t, const double* host, int64_t n);
+tnx_status tnx_tensor_download(const tnx_tensor* t, double* host, int64_t n);
+/* Sec. 6.3: multiply / divide by a scalar is allowed (t *= alpha). */
+tnx_status tnx_tensor_scale(tnx_tensor* t, double alpha);
+/* Sec. 6.3: adding a scalar would break the block structure; always returns
+ * TNX_ERR_SYMMETRY for a tensor with symmetric bonds (plain tensors: t += alpha). */
+tnx_status tnx_tensor_add_scalar(tnx_tensor* t, double alpha);
+/* Two-norm over the stored elements (FP64, device reduction).  Synchronous. */
+tnx_status tnx_tensor_norm(const tnx_tensor* t, double* out);
+
+/* --------------------------------------------------------------- networks */
+
+/* Sec. 8.1: a network blueprint from text, one entry per line:
+ *   "NAME: l1, l2, ..."   a tensor and its dummy labels (labels on two
+ *                         tensors are summed over; hyperedges and traces
+ *                         are rejected),
+ *   "TOUT: l1, l2; l3"    the open labels in output order (';' accepted as a
+ *                         separator; empty = scalar output),
+ *   "ORDER: ((A,B),C)"    optional contraction tree; empty = order of
+ *                         appearance.
+ * Errors: TNX_ERR_NETWORK. */
+tnx_status tnx_network_create(tnx_ctx* ctx, const char* spec, tnx_network** out);
+tnx_status tnx_network_destroy(tnx_network* net);
+/* Sec. 8.2 PutUniTensor: labels[i] is the blueprint label that leg i of `t`
+ * realises (nlab == rank; labels == NULL: t's legs follow the blueprint line).
+ * The network keeps a reference to t.  Bond checks happen at launch. */
+tnx_status tnx_network_put(tnx_network* net, const char* name, tnx_tensor* t, int nlab,
+                           const char* const* labels);
+/* Sec. 8.3 setOrder: optimal != 0 computes the min-cost order (dynamic
+ * programming with cost capping, Pfeifer et al. 2014, cost = product of the
+ * dimensions of all legs of each pairwise contraction) at launch, cached per
+ * set of bond dimensions; optimal == 0 takes `order` ("(A,(B,C))"). */
+tnx_status tnx_network_set_order(tnx_network* net, int optimal, const char* order);
+/* Sec. 8.3 getOrder: writes the current tree ("(M2,(M1,M3))"), NUL-terminated,
+ * into buf (TNX_ERR_ARG if len is too small). */
+tnx_status tnx_network_get_order(const tnx_network* net, char* buf, size_t len);
+/* Arithmetic of the block products (TNX_PREC_*); default TNX_PREC_F64. */
+tnx_status tnx_network_set_precision(tnx_network* net, int prec);
+/* Sec. 8.2 Launch: contract all tensors; returns a new tensor (caller owns)
+ * with the TOUT legs, every zero-flux block stored.  Asynchronous. */
+tnx_status tnx_network_launch(tnx_network* net, tnx_tensor** out);
+/* Launch into a preallocated tensor whose bonds equal the TOUT bonds. */
+tnx_status tnx_network_launch_into(tnx_network* net, tnx_tensor* out);
+/* Useful flops of one launch at the current order: 2*m*k*n summed over the
+ * matched block pairs of every pairwise contraction (plans if needed). */
+tnx_status tnx_network_flops(tnx_network* net, double* flops);
+/* Number of pairwise contractions in the plan (= number of tensors - 1). */
+tnx_status tnx_network_nsteps(tnx_network* net, int* nsteps);
+/* Fused charge-sector tables of pairwise contraction `step` (post-order of the
+ * tree), as built by the device matching kernel.  Sizes first: ngroups,
+ * nsym, and the block counts of the two operands.  Then the tables (any
+ * pointer may be NULL): charges[ngroups*nsym] (ascending), mkn[ngroups*3]
+ * (M, K, N), amap[nA*3] (group, row offset, K offset; -1 if unused),
+ * bmap[nB*3] (group, K offset, column offset).  Operand blocks are listed in
+ * lexicographic order of their sector indices in blueprint leg order. */
+tnx_status tnx_network_step_sizes(tnx_network* net, int step, int* ngroups, int* nsym, int64_t* nA,
+                                  int64_t* nB);
+tnx_status tnx_network_step_tables(tnx_network* net, int step, int32_t* charges, int64_t* mkn,
+                                   int64_t* amap, int64_t* bmap);
+
+/* ---------------------------------------------------------------- Lanczos */
+
+/* Sec. 9.3 Lanczos on a LinOp: the network, with the tensor named `vec_slot`
+ * as the vector, is the linear operator (its TOUT bonds must equal the
+ * vector's bonds).  Starting from v0, runs at most nsteps Lanczos steps with
+ * full reorthogonalisation (classical Gram-Schmidt, twice), stopping early if
+ * the new off-diagonal falls below 1e-14 * max|alpha|; returns the lowest
+ * eigenvalue of the tridiagonal matrix (Sturm bisection, FP64) in *eval and,
+ * if evec != NULL, the Ritz vector (unit norm, largest-|y| coefficient
+ * positive) in evec (same bonds as v0).  *nmatvec (may be NULL) gets the number
+ * of operator applications.  All vector arithmetic runs in FP64 on the device;
+ * the apply uses the network's precision.  Synchronous. */
+tnx_status tnx_lanczos(tnx_network* net, const char* vec_slot, tnx_tensor* v0, int nsteps,
+                       double* eval, tnx_tensor* evec, int* nmatvec);
+
+/* ------------------------------------------------------------ diagnostics */
+
+/* Kernel classes timed by the profiler. */
+enum { TNX_KC_MATCH = 0, TNX_KC_RELAYOUT = 1, TNX_KC_GEMM = 2, TNX_KC_SLICE = 3, TNX_KC_VECTOR = 4,
+       TNX_KC_FINAL = 5, TNX_KC_COUNT = 6 };
+
+/* enable != 0: bracket every kernel class a launch enqueues on the context
+ * stream with CUDA events (adds two event records per launch); 0 stops.
+ * Resets the accumulated figures either way. */
+tnx_status tnx_profile_enable(tnx_ctx* ctx, int enable);
+/* Synchronises the stream and returns, per kernel class (arrays of
+ * TNX_KC_COUNT entries, any may be NULL): summed device milliseconds, number
+ * of launches, and the algorithmic work of those launches (useful flops for
+ * TNX_KC_GEMM: 2*m*k*n over matched block pairs; bytes read + written for the
+ * relayout and slice classes, each element counted once per direction). */
+tnx_status tnx_profile_read(tnx_ctx* ctx, double* ms, int64_t* launches, double* work);
+/* Number of CUDA kernels this library has launched in the process so far. */
+tnx_status tnx_kernel_launches(int64_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNX_H */

@@ -1,0 +1,401 @@
+"""Python binding of the tnx C-ABI (include/tnx.h): argument marshalling only.
+
+Every computation runs in libtnx.so (sm_103a CUDA kernels).  There is no CPU
+fallback: importing this package without the built library raises.  PyTorch
+is used for device memory (the allocator callback) and streams.
+
+``lib()`` returns the loaded library, whose functions carry the C names
+(``lib().tnx_bond_create`` ...); the small classes below only wrap handles and
+convert arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtnx.so")
+
+TNX_OK = 0
+ERRORS = {
+    -1: "TNX_ERR_ARG", -2: "TNX_ERR_BOND_MISMATCH", -3: "TNX_ERR_SYMMETRY", -4: "TNX_ERR_NO_BLOCK",
+    -5: "TNX_ERR_NETWORK", -6: "TNX_ERR_OOM", -7: "TNX_ERR_TIMEOUT", -8: "TNX_ERR_CUDA", -9: "TNX_ERR_UNSUPPORTED",
+}
+U1, ZN = 0, 1
+BD_IN, BD_OUT, BD_REG = 1, -1, 0
+PREC_F64, PREC_SPLIT_BF16, PREC_SPLIT_F16, PREC_F32, PREC_TF32 = 0, 1, 2, 3, 4
+PREC_NAMES = {"f64": 0, "split_bf16": 1, "split_f16": 2, "f32": 3, "tf32": 4}
+
+
+class TnxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libtnx.so is not built ({LIB_PATH}); run paper_2401_01921_gb300.build.build()")
+    return C.CDLL(LIB_PATH)
+
+
+_lib = None
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+_p = C.c_void_p
+_i64p = C.POINTER(C.c_int64)
+_i32p = C.POINTER(C.c_int32)
+_SIGS = {
+    "tnx_last_error": (C.c_char_p, [_p]),
+    "tnx_version": (C.c_char_p, []),
+    "tnx_ctx_create": (C.c_int, [C.c_int, _p, ALLOC_FN, FREE_FN, _p, C.POINTER(_p)]),
+    "tnx_ctx_destroy": (C.c_int, [_p]),
+    "tnx_sync": (C.c_int, [_p]),
+    "tnx_bond_create": (C.c_int, [_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int, _i32p, _i64p,
+                                  C.POINTER(_p)]),
+    "tnx_bond_dim": (C.c_int, [_p, _i64p]),
+    "tnx_bond_combine": (C.c_int, [_p, _p, C.POINTER(_p)]),
+    "tnx_bond_sectors": (C.c_int, [_p, C.POINTER(C.c_int), _i32p, _i64p]),
+    "tnx_bond_destroy": (C.c_int, [_p]),
+    "tnx_tensor_create": (C.c_int, [_p, C.c_int, C.POINTER(_p), C.POINTER(_p)]),
+    "tnx_tensor_destroy": (C.c_int, [_p]),
+    "tnx_tensor_rank": (C.c_int, [_p, C.POINTER(C.c_int)]),
+    "tnx_tensor_nblocks": (C.c_int, [_p, _i64p]),
+    "tnx_tensor_block_info": (C.c_int, [_p, C.c_int64, _i32p, _i64p, _i64p]),
+    "tnx_tensor_blocks": (C.c_int, [_p, _i32p, _i64p, _i64p]),
+    "tnx_tensor_data": (C.c_int, [_p, C.POINTER(_p), _i64p]),
+    "tnx_tensor_put_block": (C.c_int, [_p, _i32p, C.POINTER(C.c_double), C.c_int64]),
+    "tnx_tensor_get_block": (C.c_int, [_p, _i32p, C.POINTER(C.c_double), C.c_int64]),
+    "tnx_tensor_upload": (C.c_int, [_p, C.POINTER(C.c_double), C.c_int64]),
+    "tnx_tensor_download": (C.c_int, [_p, C.POINTER(C.c_double), C.c_int64]),
+    "tnx_tensor_scale": (C.c_int, [_p, C.c_double]),
+    "tnx_tensor_add_scalar": (C.c_int, [_p, C.c_double]),
+    "tnx_tensor_norm": (C.c_int, [_p, C.POINTER(C.c_double)]),
+    "tnx_network_create": (C.c_int, [_p, C.c_char_p, C.POINTER(_p)]),
+    "tnx_network_destroy": (C.c_int, [_p]),
+    "tnx_network_put": (C.c_int, [_p, C.c_char_p, _p, C.c_int, C.POINTER(C.c_char_p)]),
+    "tnx_network_set_order": (C.c_int, [_p, C.c_int, C.c_char_p]),
+    "tnx_network_get_order": (C.c_int, [_p, C.c_char_p, C.c_size_t]),
+    "tnx_network_set_precision": (C.c_int, [_p, C.c_int]),
+    "tnx_network_launch": (C.c_int, [_p, C.POINTER(_p)]),
+    "tnx_network_launch_into": (C.c_int, [_p, _p]),
+    "tnx_network_flops": (C.c_int, [_p, C.POINTER(C.c_double)]),
+    "tnx_network_nsteps": (C.c_int, [_p, C.POINTER(C.c_int)]),
+    "tnx_network_step_sizes": (C.c_int, [_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _i64p, _i64p]),
+    "tnx_network_step_tables": (C.c_int, [_p, C.c_int, _i32p, _i64p, _i64p, _i64p]),
+    "tnx_lanczos": (C.c_int, [_p, C.c_char_p, _p, C.c_int, C.POINTER(C.c_double), _p, C.POINTER(C.c_int)]),
+    "tnx_profile_enable": (C.c_int, [_p, C.c_int]),
+    "tnx_profile_read": (C.c_int, [_p, C.POINTER(C.c_double), _i64p, C.POINTER(C.c_double)]),
+    "tnx_kernel_launches": (C.c_int, [_i64p]),
+}
+KERNEL_CLASSES = ["match", "relayout", "gemm", "slice", "vector", "final"]
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        L = _load()
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _check(ctx_handle, code: int):
+    if code != TNX_OK:
+        msg = lib().tnx_last_error(ctx_handle) if ctx_handle else b""
+        raise TnxError(code, (msg or b"").decode())
+
+
+# ---------------------------------------------------------------- objects
+class Context:
+    """tnx_ctx over a CUDA device; device memory from PyTorch's caching allocator."""
+
+    def __init__(self, device: int = 0, stream=None, torch_alloc: bool = True):
+        import torch
+        self._torch = torch
+        self.device = device
+        self._keep: dict[int, object] = {}
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        sp = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        if torch_alloc:
+            dev = torch.device("cuda", device)
+
+            def _alloc(n, user):
+                try:
+                    with torch.cuda.stream(self.stream):
+                        t = torch.empty(int(n), dtype=torch.uint8, device=dev)
+                except RuntimeError:
+                    return None
+                p = t.data_ptr()
+                self._keep[p] = t
+                return p
+
+            def _free(p, n, user):
+                self._keep.pop(p, None)
+
+            self._alloc_cb = ALLOC_FN(_alloc)
+            self._free_cb = FREE_FN(_free)
+        else:
+            self._alloc_cb = ALLOC_FN()
+            self._free_cb = FREE_FN()
+        h = C.c_void_p()
+        code = lib().tnx_ctx_create(device, sp, self._alloc_cb, self._free_cb, None, C.byref(h))
+        if code != TNX_OK:
+            raise TnxError(code, "tnx_ctx_create failed")
+        self.h = h
+
+    def check(self, code):
+        _check(self.h, code)
+
+    def sync(self):
+        self.check(lib().tnx_sync(self.h))
+
+    def close(self):
+        if self.h:
+            lib().tnx_ctx_destroy(self.h)
+            self.h = None
+
+    def profile(self, enable: bool):
+        """tnx_profile_enable: CUDA-event timing of every kernel class."""
+        self.check(lib().tnx_profile_enable(self.h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """{class: (milliseconds, launches, algorithmic work)} since profile(True)."""
+        n = len(KERNEL_CLASSES)
+        ms = (C.c_double * n)()
+        cnt = (C.c_int64 * n)()
+        work = (C.c_double * n)()
+        self.check(lib().tnx_profile_read(self.h, ms, cnt, work))
+        return {k: (ms[i], cnt[i], work[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def kernel_launches() -> int:
+    """tnx_kernel_launches: CUDA kernels launched by the library in this process."""
+    n = C.c_int64()
+    lib().tnx_kernel_launches(C.byref(n))
+    return n.value
+
+
+class Bond:
+    """tnx_bond: direction, sectors [(charge tuple, degeneracy)], symmetries [U1 | (ZN, n)]."""
+
+    def __init__(self, ctx: Context, dir: int, sectors, syms=()):
+        self.ctx = ctx
+        syms = list(syms)
+        kinds = np.array([U1 if s == U1 else ZN for s in syms] or [0], dtype=np.int32)
+        zn = np.array([0 if s == U1 else s[1] for s in syms] or [0], dtype=np.int32)
+        nsym = len(syms)
+        q = np.array([c for qn, _ in sectors for c in qn] or [0], dtype=np.int32)
+        d = np.array([dg for _, dg in sectors], dtype=np.int64)
+        h = C.c_void_p()
+        ctx.check(lib().tnx_bond_create(ctx.h, dir, nsym, _ptr(kinds, C.c_int), _ptr(zn, C.c_int), len(sectors),
+                                        _ptr(q, C.c_int32), _ptr(d, C.c_int64), C.byref(h)))
+        self.h = h
+        self.dir = dir
+        self.sectors = [(tuple(int(c) for c in qn), int(dg)) for qn, dg in sectors]
+        self.nsym = nsym
+
+    @property
+    def dim(self) -> int:
+        return sum(d for _, d in self.sectors)
+
+    def offsets(self):
+        return np.concatenate([[0], np.cumsum([d for _, d in self.sectors])])
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().tnx_bond_destroy(self.h)
+        except Exception:
+            pass
+
+
+class Tensor:
+    """tnx_tensor: block-sparse FP64 tensor in device memory."""
+
+    def __init__(self, ctx: Context, bonds, handle=None):
+        self.ctx = ctx
+        self.bonds = list(bonds)
+        if handle is None:
+            arr = (C.c_void_p * max(1, len(bonds)))(*[b.h for b in bonds])
+            h = C.c_void_p()
+            ctx.check(lib().tnx_tensor_create(ctx.h, len(bonds), arr, C.byref(h)))
+            handle = h
+        self.h = handle
+        self.rank = len(bonds)
+        n = C.c_int64()
+        ctx.check(lib().tnx_tensor_nblocks(self.h, C.byref(n)))
+        self.nblocks = n.value
+        p = C.c_void_p()
+        ne = C.c_int64()
+        ctx.check(lib().tnx_tensor_data(self.h, C.byref(p), C.byref(ne)))
+        self.data_ptr = p.value
+        self.nelem = ne.value
+
+    def blocks(self):
+        """(qn [nblk, rank] int32, shape [nblk, rank] int64, offset [nblk] int64)."""
+        r = max(self.rank, 1)
+        qn = np.zeros((self.nblocks, r), dtype=np.int32)
+        sh = np.zeros((self.nblocks, r), dtype=np.int64)
+        off = np.zeros(self.nblocks, dtype=np.int64)
+        self.ctx.check(lib().tnx_tensor_blocks(self.h, _ptr(qn, C.c_int32), _ptr(sh, C.c_int64), _ptr(off, C.c_int64)))
+        return qn[:, :self.rank], sh[:, :self.rank], off
+
+    def upload(self, x: np.ndarray):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        self.ctx.check(lib().tnx_tensor_upload(self.h, _ptr(x, C.c_double), x.size))
+
+    def download(self) -> np.ndarray:
+        x = np.zeros(self.nelem, dtype=np.float64)
+        self.ctx.check(lib().tnx_tensor_download(self.h, _ptr(x, C.c_double), x.size))
+        return x
+
+    def put_block(self, qn, data):
+        q = np.ascontiguousarray(qn, dtype=np.int32)
+        d = np.ascontiguousarray(data, dtype=np.float64)
+        self.ctx.check(lib().tnx_tensor_put_block(self.h, _ptr(q, C.c_int32), _ptr(d, C.c_double), d.size))
+
+    def get_block(self, qn, shape):
+        q = np.ascontiguousarray(qn, dtype=np.int32)
+        d = np.zeros(int(np.prod(shape)), dtype=np.float64)
+        self.ctx.check(lib().tnx_tensor_get_block(self.h, _ptr(q, C.c_int32), _ptr(d, C.c_double), d.size))
+        return d.reshape(shape)
+
+    def scale(self, a: float):
+        self.ctx.check(lib().tnx_tensor_scale(self.h, a))
+
+    def add_scalar(self, a: float):
+        self.ctx.check(lib().tnx_tensor_add_scalar(self.h, a))
+
+    def norm(self) -> float:
+        x = C.c_double()
+        self.ctx.check(lib().tnx_tensor_norm(self.h, C.byref(x)))
+        return x.value
+
+    def fill(self, value_at):
+        """Fill every block from value_at(list of dense-coordinate arrays) and upload."""
+        qn, sh, off = self.blocks()
+        out = np.zeros(self.nelem)
+        offs = [b.offsets() for b in self.bonds]
+        for b in range(self.nblocks):
+            grids = [np.arange(offs[l][qn[b, l]], offs[l][qn[b, l]] + sh[b, l]) for l in range(self.rank)]
+            if grids:
+                mesh = np.meshgrid(*grids, indexing="ij")
+                vals = value_at([m.reshape(-1) for m in mesh])
+            else:
+                vals = value_at([])
+            n = int(np.prod(sh[b])) if self.rank else 1
+            out[off[b]:off[b] + n] = np.asarray(vals, dtype=np.float64).reshape(-1)
+        self.upload(out)
+        return self
+
+    def block_dict(self, flat=None):
+        """{qn tuple: ndarray block} from a download (or the given flat array)."""
+        x = self.download() if flat is None else flat
+        qn, sh, off = self.blocks()
+        out = {}
+        for b in range(self.nblocks):
+            n = int(np.prod(sh[b])) if self.rank else 1
+            out[tuple(int(v) for v in qn[b])] = x[off[b]:off[b] + n].reshape(tuple(sh[b]))
+        return out
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().tnx_tensor_destroy(self.h)
+        except Exception:
+            pass
+
+
+class Network:
+    """tnx_network: Network blueprint + put tensors + order + precision."""
+
+    def __init__(self, ctx: Context, spec: str):
+        self.ctx = ctx
+        h = C.c_void_p()
+        ctx.check(lib().tnx_network_create(ctx.h, spec.encode(), C.byref(h)))
+        self.h = h
+        self._refs = {}
+
+    def put(self, name: str, t: Tensor, labels=None):
+        if labels is None:
+            ctx_code = lib().tnx_network_put(self.h, name.encode(), t.h, 0, None)
+        else:
+            arr = (C.c_char_p * len(labels))(*[l.encode() for l in labels])
+            ctx_code = lib().tnx_network_put(self.h, name.encode(), t.h, len(labels), arr)
+        self.ctx.check(ctx_code)
+        self._refs[name] = t
+
+    def set_order(self, optimal: bool, order: str | None = None):
+        self.ctx.check(lib().tnx_network_set_order(self.h, 1 if optimal else 0, order.encode() if order else None))
+
+    def get_order(self) -> str:
+        buf = C.create_string_buffer(4096)
+        self.ctx.check(lib().tnx_network_get_order(self.h, buf, 4096))
+        return buf.value.decode()
+
+    def set_precision(self, prec):
+        if isinstance(prec, str):
+            prec = PREC_NAMES[prec]
+        self.ctx.check(lib().tnx_network_set_precision(self.h, prec))
+
+    def launch(self, out_bonds) -> Tensor:
+        h = C.c_void_p()
+        self.ctx.check(lib().tnx_network_launch(self.h, C.byref(h)))
+        return Tensor(self.ctx, out_bonds, handle=h)
+
+    def launch_into(self, out: Tensor):
+        self.ctx.check(lib().tnx_network_launch_into(self.h, out.h))
+
+    def flops(self) -> float:
+        x = C.c_double()
+        self.ctx.check(lib().tnx_network_flops(self.h, C.byref(x)))
+        return x.value
+
+    def nsteps(self) -> int:
+        x = C.c_int()
+        self.ctx.check(lib().tnx_network_nsteps(self.h, C.byref(x)))
+        return x.value
+
+    def step_tables(self, step: int) -> dict:
+        G, ns = C.c_int(), C.c_int()
+        nA, nB = C.c_int64(), C.c_int64()
+        self.ctx.check(lib().tnx_network_step_sizes(self.h, step, C.byref(G), C.byref(ns), C.byref(nA), C.byref(nB)))
+        ch = np.zeros(max(1, G.value * ns.value), dtype=np.int32)
+        mkn = np.zeros(max(1, G.value * 3), dtype=np.int64)
+        am = np.zeros(max(1, nA.value * 3), dtype=np.int64)
+        bm = np.zeros(max(1, nB.value * 3), dtype=np.int64)
+        self.ctx.check(lib().tnx_network_step_tables(self.h, step, _ptr(ch, C.c_int32), _ptr(mkn, C.c_int64),
+                                                     _ptr(am, C.c_int64), _ptr(bm, C.c_int64)))
+        return {"charges": ch[:G.value * ns.value].reshape(G.value, ns.value),
+                "MKN": mkn[:G.value * 3].reshape(G.value, 3),
+                "amap": am[:nA.value * 3].reshape(nA.value, 3),
+                "bmap": bm[:nB.value * 3].reshape(nB.value, 3)}
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().tnx_network_destroy(self.h)
+        except Exception:
+            pass
+
+
+def lanczos(net: Network, slot: str, v0: Tensor, nsteps: int, evec: Tensor | None = None):
+    """tnx_lanczos: returns (lowest eigenvalue, number of matvecs)."""
+    ev = C.c_double()
+    nm = C.c_int()
+    net.ctx.check(lib().tnx_lanczos(net.h, slot.encode(), v0.h, nsteps, C.byref(ev),
+                                    evec.h if evec is not None else None, C.byref(nm)))
+    return ev.value, nm.value

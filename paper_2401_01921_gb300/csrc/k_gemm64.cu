@@ -1,0 +1,90 @@
+// Grouped dense products for the fused charge sectors, native FP64.
+//
+// Sec. 7 / Sec. 10 of arXiv 2401.01921: after matching, each charge sector of
+// a pairwise contraction is one dense matrix product (the paper hands these to
+// BLAS / cuBLAS).  Here one launch covers every tile of every group:
+// C_g[M,N] = A_g[M,K] * B_g[N,K]^T, operands K-major, C row-major.
+//
+// 64x64 output tile per CTA of 256 threads, each thread a 4x4 register tile
+// of FP64 FMAs; K staged through shared memory in slices of 16.  FP64 on this
+// part runs at a small fraction of its FP32 / tensor rate, so the kernel is
+// bound by the FP64 pipe, not by memory; ragged tile edges are masked.
+// The FP32 variant (operands rounded to FP32, FP32 FMAs, result widened) is
+// the "single FP32" point of the precision sweep.
+#include "tnx_internal.h"
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+template <typename TC>
+__global__ void __launch_bounds__(256) gemm_kernel(const GemmGroup* __restrict__ groups,
+                                                   const GemmTile* __restrict__ tiles,
+                                                   double* const* __restrict__ slots) {
+  __shared__ TC As[BK][BM + 1];
+  __shared__ TC Bs[BK][BN + 1];
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmGroup g = groups[tl.group];
+  const double* A = slots[g.a_slot] + g.a_off;
+  const double* B = slots[g.b_slot] + g.b_off;
+  double* C = slots[g.c_slot] + g.c_off;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  TC acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  for (int k0 = 0; k0 < g.K; k0 += BK) {
+    // load 64x16 of A and of B (1024 elements each, 4 per thread), k fastest
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int idx = threadIdx.x + r * 256;
+      const int row = idx >> 4, kk = idx & 15;
+      const int gm = tl.m0 + row, gn = tl.n0 + row, gk = k0 + kk;
+      As[kk][row] = (gm < g.M && gk < g.K) ? (TC)A[(int64_t)gm * g.lda + gk] : (TC)0;
+      Bs[kk][row] = (gn < g.N && gk < g.K) ? (TC)B[(int64_t)gn * g.ldb + gk] : (TC)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      TC a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = tl.m0 + ty + 16 * i;
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = tl.n0 + tx + 16 * j;
+      if (gn < g.N) C[(int64_t)gm * g.ldc + gn] = (double)acc[i][j];
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t tnx_launch_gemm_f64(const GemmGroup* groups, const GemmTile* tiles, int ntiles,
+                                double* const* slots, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  gemm_kernel<double><<<ntiles, 256, 0, st>>>(groups, tiles, slots);
+  tnx_note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tnx_launch_gemm_f32(const GemmGroup* groups, const GemmTile* tiles, int ntiles,
+                                double* const* slots, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  gemm_kernel<float><<<ntiles, 256, 0, st>>>(groups, tiles, slots);
+  tnx_note_launch(1);
+  return cudaGetLastError();
+}

@@ -1,0 +1,148 @@
+// Internal declarations shared by the host planner and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tnx.h"
+
+#define TNX_MAXR 8          // maximum rank of a tensor or an intermediate
+#define TNX_MAXSYM 4        // maximum number of symmetries on a bond
+
+// ---------------------------------------------------------------------------
+// Device task descriptors (plain data, built on the host at plan time).
+// A "slot" is an index into a device array of base pointers (double*), so a
+// plan (and a CUDA graph captured from it) can be rebound to new input and
+// output buffers by rewriting that array only.
+// ---------------------------------------------------------------------------
+
+// One strided block copy.  Legs are ordered outer -> inner; the last leg is
+// the one contiguous in the destination.  src_slot < 0 writes zeros.
+struct CopyTask {
+  int32_t src_slot, dst_slot;
+  int32_t rank, pad0;
+  int64_t src_off, dst_off;
+  int64_t nelem;
+  int32_t shape[TNX_MAXR];
+  int64_t sstride[TNX_MAXR];
+  int64_t dstride[TNX_MAXR];
+};
+
+// One dense product C[M,N] = A[M,K] * B[N,K]^T (both operands K-major, C row-major).
+struct GemmGroup {
+  int32_t a_slot, b_slot, c_slot, pad0;
+  int64_t a_off, b_off, c_off;
+  int32_t M, N, K, lda, ldb, ldc;
+};
+
+struct GemmTile {
+  int32_t group, m0, n0, pad0;
+};
+
+// Split-precision operand preparation: one packed FP64 matrix (rows x K,
+// row-major, ld) is sliced into nslice integer-valued 16-bit slices written in
+// the tcgen05 no-swizzle K-major core-matrix layout, tile by tile.
+struct SliceJob {
+  int32_t src_slot, dst_slot;     // dst: byte buffer slot (uint16 slices)
+  int32_t exp_slot, pad0;         // int32 row exponents
+  int64_t src_off, dst_off_bytes, exp_off;
+  int32_t rows, K, ld, tile_rows; // tile_rows: 128 (A) or 64 (B)
+};
+
+// Split GEMM group: slices of A (tile_rows 128) and B (tile_rows 64) plus
+// per-row / per-column exponents; output FP64 row-major.
+struct SplitGroup {
+  int32_t a_slot, b_slot, c_slot, ea_slot;
+  int32_t eb_slot, pad0, pad1, pad2;
+  int64_t a_off_bytes, b_off_bytes, c_off, ea_off, eb_off;
+  int32_t M, N, K, ldc;
+};
+
+// ---------------------------------------------------------------------------
+// Fused charge-sector matching (integer): inputs of the device kernel.
+// ---------------------------------------------------------------------------
+struct MatchLeg {
+  int32_t nsec;
+  int32_t sec_base;     // offset into deg[] / charge[] arrays
+};
+
+struct MatchArgs {
+  // legs
+  int32_t nk, nfa, nfb, nsym;
+  MatchLeg kleg[TNX_MAXR], faleg[TNX_MAXR], fbleg[TNX_MAXR];
+  const int64_t* deg;        // degeneracies, indexed by sec_base + sector
+  const int32_t* kcharge;    // signed charge of K-leg sectors as seen from A: [(sec_base+s)*nsym + c]
+  int32_t zn[TNX_MAXSYM];    // 0 for U(1), n for Z_n
+  int32_t clo[TNX_MAXSYM], crange[TNX_MAXSYM];
+  // blocks
+  int64_t nA, nB;
+  int32_t rA, rB;
+  const int32_t* qA;         // nA * rA sector indices (view leg order)
+  const int32_t* qB;
+  int32_t kposA[TNX_MAXR], fposA[TNX_MAXR], kposB[TNX_MAXR], fposB[TNX_MAXR];
+  // sizes of the tuple spaces
+  int64_t kspace, faspace, fbspace, cspace;
+  // scratch (device)
+  int32_t* kpres;  int32_t* kgroup;  int64_t* koff;
+  int32_t* rgroup; int64_t* roff;
+  int32_t* cgroup; int64_t* coff;
+  int32_t* cspres; int32_t* csgid;
+  int64_t* scan_tmp;        // 1024 * gmax
+  int32_t gmax;
+  // outputs (device)
+  int32_t* ngroups;         // [1]
+  int32_t* charges;         // gmax * nsym
+  int64_t* mkn;             // gmax * 3
+  int64_t* amap;            // nA * 3
+  int64_t* bmap;            // nB * 3
+  int32_t* status;          // [1]: 0 ok, 1 too many groups
+};
+
+// Counts kernel launches made by this library (defined in tnx_host.cpp).
+void tnx_note_launch(int n);
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files).  All enqueue on `st`.
+// ---------------------------------------------------------------------------
+cudaError_t tnx_launch_match(const MatchArgs& a, cudaStream_t st);
+cudaError_t tnx_launch_copy(const CopyTask* tasks, const int64_t* elem_start, int ntasks, int64_t total,
+                            double* const* slots, cudaStream_t st);
+cudaError_t tnx_launch_gemm_f64(const GemmGroup* groups, const GemmTile* tiles, int ntiles,
+                                double* const* slots, cudaStream_t st);
+cudaError_t tnx_launch_gemm_f32(const GemmGroup* groups, const GemmTile* tiles, int ntiles,
+                                double* const* slots, cudaStream_t st);
+cudaError_t tnx_launch_row_exponents(const SliceJob* jobs, const int64_t* row_start, int njobs,
+                                     int64_t total_rows, double* const* slots, cudaStream_t st);
+cudaError_t tnx_launch_slices(const SliceJob* jobs, const int64_t* tile_start, int njobs, int64_t total_tiles,
+                              int nslice, int beta, int f16, double* const* slots, cudaStream_t st);
+cudaError_t tnx_launch_gemm_split(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int nslice,
+                                  int beta, int f16, double* const* slots, int32_t* status, cudaStream_t st);
+cudaError_t tnx_launch_gemm_tf32(const SplitGroup* groups, const GemmTile* tiles, int ntiles,
+                                 double* const* slots, int32_t* status, cudaStream_t st);
+
+// vector kernels (FP64, deterministic two-level reductions)
+cudaError_t tnx_launch_scale(double* x, int64_t n, double alpha, cudaStream_t st);
+cudaError_t tnx_launch_add_scalar(double* x, int64_t n, double alpha, cudaStream_t st);
+cudaError_t tnx_launch_norm2(const double* x, int64_t n, double* partial, double* out, cudaStream_t st);
+int tnx_reduce_blocks(int64_t n);
+
+// Lanczos device state
+struct LanczosDev {
+  double* V;          // [nmax+1][n] basis
+  double* w;          // [n]
+  double* alpha;      // [nmax]
+  double* beta;       // [nmax+1]
+  double* coef;       // [nmax+1]  Gram-Schmidt coefficients
+  double* partial;    // [nblocks * (nmax+1)]
+  double* y;          // [nmax]    Ritz coefficients
+  double* scratch;    // [4*nmax]
+  int32_t* state;     // [0] = active steps done (k), [1] = stopped flag
+  double* eval;       // [1]
+  int64_t n;
+  int nmax;
+  int nblocks;
+};
+cudaError_t tnx_launch_lanczos_init(const LanczosDev& L, const double* v0, cudaStream_t st);
+cudaError_t tnx_launch_lanczos_set_input(double** slot_ptr, const LanczosDev& L, int j, cudaStream_t st);
+cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, cudaStream_t st);
+cudaError_t tnx_launch_lanczos_finish(const LanczosDev& L, double* evec, cudaStream_t st);

@@ -1,0 +1,1119 @@
+// Network blueprint, contraction-order search, planner and executor.
+//
+// arXiv 2401.01921, Sec. 8 (Network): a text blueprint of tensor names and
+// dummy labels, TOUT (output leg order) and ORDER (binary contraction tree);
+// PutUniTensor maps actual legs onto dummy labels; Launch contracts.  Sec. 8.3
+// / Sec. 7: the optimal order comes from dynamic programming with cost capping
+// (Pfeifer, Haegeman, Verstraete, PRE 90, 033315, 2014) and is reused while the
+// bond dimensions stay the same.
+//
+// A plan turns the tree into a sequence of pairwise steps.  Each step runs
+//   1. the integer matching kernel (once, at plan time) -> fused-sector tables,
+//   2. the relayout kernel: every block of both operands into its place in the
+//      fused operand matrix of its charge group,
+//   3. one grouped-GEMM launch over all groups (FP64, FP32, split BF16/FP16, TF32).
+// The product of step s is stored as the fused matrices C_g themselves; its
+// blocks are strided views into them, read directly by the next relayout.  A
+// final relayout writes the canonical blocks of the output in TOUT order.
+// All buffers and task tables are allocated at plan time; a launch only
+// rewrites the table of base pointers ("slots") and enqueues kernels, so a
+// launch (or a whole Lanczos solve) can be captured in one CUDA graph.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <set>
+
+#include "tnx_host.h"
+
+#include "tnx_plan.h"
+
+namespace {
+
+typedef unsigned __int128 u128;
+
+}  // namespace
+
+// --------------------------------------------------------------- parsing
+namespace {
+
+std::string trim(const std::string& s) {
+  size_t a = s.find_first_not_of(" \t\r"), b = s.find_last_not_of(" \t\r");
+  return a == std::string::npos ? std::string() : s.substr(a, b - a + 1);
+}
+
+bool valid_name(const std::string& s) {
+  if (s.empty()) return false;
+  for (char c : s)
+    if (!(isalnum((unsigned char)c) || c == '_' || c == '-' || c == '.' || c == '\'')) return false;
+  return true;
+}
+
+std::vector<std::string> split_labels(const std::string& s) {
+  std::vector<std::string> out;
+  std::string cur;
+  for (char c : s) {
+    if (c == ',' || c == ';') {
+      std::string t = trim(cur);
+      if (!t.empty()) out.push_back(t);
+      cur.clear();
+    } else {
+      cur += c;
+    }
+  }
+  std::string t = trim(cur);
+  if (!t.empty()) out.push_back(t);
+  return out;
+}
+
+int parse_tree(const std::string& s, size_t& pos, const std::vector<NetTensor>& ts, std::vector<TreeNode>& nodes) {
+  if (pos < s.size() && s[pos] == '(') {
+    ++pos;
+    int l = parse_tree(s, pos, ts, nodes);
+    if (pos >= s.size() || s[pos] != ',') fail(TNX_ERR_NETWORK, "ORDER: expected ','");
+    ++pos;
+    int r = parse_tree(s, pos, ts, nodes);
+    if (pos >= s.size() || s[pos] != ')') fail(TNX_ERR_NETWORK, "ORDER: expected ')'");
+    ++pos;
+    nodes.push_back(TreeNode{-1, l, r});
+    return (int)nodes.size() - 1;
+  }
+  size_t b = pos;
+  while (pos < s.size() && s[pos] != ',' && s[pos] != ')' && s[pos] != '(') ++pos;
+  std::string name = s.substr(b, pos - b);
+  for (size_t i = 0; i < ts.size(); ++i)
+    if (ts[i].name == name) {
+      nodes.push_back(TreeNode{(int)i, -1, -1});
+      return (int)nodes.size() - 1;
+    }
+  fail(TNX_ERR_NETWORK, "ORDER names an unknown tensor '" + name + "'");
+}
+
+void set_tree_from_string(tnx_network* net, const std::string& order_in) {
+  std::string o;
+  for (char c : order_in)
+    if (!isspace((unsigned char)c)) o += c;
+  std::vector<TreeNode> nodes;
+  size_t pos = 0;
+  int root = parse_tree(o, pos, net->ts, nodes);
+  if (pos != o.size()) fail(TNX_ERR_NETWORK, "ORDER: trailing characters");
+  std::vector<int> seen(net->ts.size(), 0);
+  for (auto& n : nodes)
+    if (n.leaf >= 0) seen[n.leaf]++;
+  for (int c : seen)
+    if (c != 1) fail(TNX_ERR_NETWORK, "ORDER must name every tensor exactly once");
+  net->tree = nodes;
+  net->root = root;
+}
+
+void set_default_tree(tnx_network* net) {
+  std::vector<TreeNode> nodes;
+  int cur = -1;
+  for (size_t i = 0; i < net->ts.size(); ++i) {
+    nodes.push_back(TreeNode{(int)i, -1, -1});
+    int leaf = (int)nodes.size() - 1;
+    if (cur < 0) {
+      cur = leaf;
+    } else {
+      nodes.push_back(TreeNode{-1, cur, leaf});
+      cur = (int)nodes.size() - 1;
+    }
+  }
+  net->tree = nodes;
+  net->root = cur;
+}
+
+std::string tree_string(const tnx_network* net, int node) {
+  const TreeNode& n = net->tree[node];
+  if (n.leaf >= 0) return net->ts[n.leaf].name;
+  return "(" + tree_string(net, n.l) + "," + tree_string(net, n.r) + ")";
+}
+
+// ------------------------------------------------------------ order search
+u128 mul_sat(u128 a, u128 b) {
+  const u128 maxv = ~(u128)0;
+  if (a != 0 && b > maxv / a) return maxv;
+  return a * b;
+}
+
+// DP over subsets with cost capping (Pfeifer et al. 2014).  Cost of a pairwise
+// contraction: product of the dimensions of all distinct legs of both operands.
+// Ties keep the first split S1 (containing the lowest member) in increasing
+// bitmask order.
+void optimal_tree(tnx_network* net) {
+  const int n = (int)net->ts.size();
+  if (n > 20) fail(TNX_ERR_UNSUPPORTED, "optimal order search supports at most 20 tensors");
+  std::map<std::string, int64_t> dims;
+  for (auto& t : net->ts)
+    for (size_t j = 0; j < t.labels.size(); ++j) dims[t.labels[j]] = t.t->bonds[t.perm[j]].dim;
+  std::vector<std::string> labs;
+  for (auto& kv : dims) labs.push_back(kv.first);
+  const int nl = (int)labs.size();
+  std::vector<std::vector<int>> legs(n);
+  for (int i = 0; i < n; ++i)
+    for (auto& l : net->ts[i].labels) legs[i].push_back((int)(std::find(labs.begin(), labs.end(), l) - labs.begin()));
+  const uint32_t full = (1u << n) - 1;
+  // open legs of each subset: legs appearing exactly once inside it
+  std::vector<std::vector<int>> open(full + 1);
+  std::vector<int> cnt(nl);
+  for (uint32_t m = 1; m <= full; ++m) {
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (int i = 0; i < n; ++i)
+      if (m >> i & 1)
+        for (int l : legs[i]) cnt[l]++;
+    for (int l = 0; l < nl; ++l)
+      if (cnt[l] == 1) open[m].push_back(l);
+  }
+  std::vector<int> mark(nl, 0);
+  auto pair_cost = [&](uint32_t a, uint32_t b) {
+    u128 c = 1;
+    for (int l : open[a]) { mark[l] = 1; c = mul_sat(c, (u128)dims[labs[l]]); }
+    for (int l : open[b])
+      if (!mark[l]) c = mul_sat(c, (u128)dims[labs[l]]);
+    for (int l : open[a]) mark[l] = 0;
+    return c;
+  };
+  u128 mu = 1;
+  for (int i = 0; i < n; ++i) {
+    u128 s = 1;
+    for (int l : legs[i]) s = mul_sat(s, (u128)dims[labs[l]]);
+    if (s > mu) mu = s;
+  }
+  const u128 INF = ~(u128)0;
+  std::vector<u128> best(full + 1);
+  std::vector<uint32_t> split(full + 1);
+  std::vector<char> have(full + 1);
+  std::vector<int> order_by_size;
+  std::vector<uint32_t> masks;
+  for (int size = 2; size <= n; ++size)
+    for (uint32_t m = 1; m <= full; ++m)
+      if (__builtin_popcount(m) == size) masks.push_back(m);
+  while (true) {
+    std::fill(have.begin(), have.end(), 0);
+    for (int i = 0; i < n; ++i) { best[1u << i] = 0; have[1u << i] = 1; }
+    u128 rejected = INF;
+    for (uint32_t m : masks) {
+      uint32_t low = m & (~m + 1), rest = m ^ low;
+      bool found = false;
+      u128 bc = 0;
+      uint32_t bs = 0;
+      uint32_t s = 0;
+      while (true) {
+        uint32_t m1 = low | s, m2 = m ^ m1;
+        if (m2 != 0 && have[m1] && have[m2]) {
+          u128 c = best[m1] + best[m2];
+          u128 pc = pair_cost(m1, m2);
+          c = (c + pc < c) ? INF : c + pc;
+          if (c > mu) {
+            if (c < rejected) rejected = c;
+          } else if (!found || c < bc) {
+            found = true;
+            bc = c;
+            bs = m1;
+          }
+        }
+        if (s == rest) break;
+        s = (s - rest) & rest;
+      }
+      if (found) { best[m] = bc; split[m] = bs; have[m] = 1; }
+    }
+    if (have[full]) break;
+    u128 nm = mul_sat(mu, 2);
+    mu = rejected > nm ? rejected : nm;
+  }
+  std::vector<TreeNode> nodes;
+  std::function<int(uint32_t)> build = [&](uint32_t m) -> int {
+    if (__builtin_popcount(m) == 1) {
+      nodes.push_back(TreeNode{__builtin_ctz(m), -1, -1});
+      return (int)nodes.size() - 1;
+    }
+    int l = build(split[m]);
+    int r = build(m ^ split[m]);
+    nodes.push_back(TreeNode{-1, l, r});
+    return (int)nodes.size() - 1;
+  };
+  int root = build(full);
+  net->tree = nodes;
+  net->root = root;
+}
+
+// ------------------------------------------------------------------ views
+std::vector<int64_t> rowmajor(const int64_t* shape, int r) {
+  std::vector<int64_t> s(r);
+  int64_t acc = 1;
+  for (int l = r - 1; l >= 0; --l) { s[l] = acc; acc *= shape[l]; }
+  return s;
+}
+
+void sort_view(OpView& v) {
+  const int r = v.rank();
+  std::vector<int64_t> idx(v.nblk);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
+    return std::lexicographical_compare(v.qn.begin() + a * r, v.qn.begin() + (a + 1) * r, v.qn.begin() + b * r,
+                                        v.qn.begin() + (b + 1) * r);
+  });
+  std::vector<int32_t> qn(v.qn.size());
+  std::vector<int64_t> base(v.nblk), stride(v.stride.size());
+  for (int64_t i = 0; i < v.nblk; ++i) {
+    std::copy(v.qn.begin() + idx[i] * r, v.qn.begin() + (idx[i] + 1) * r, qn.begin() + i * r);
+    std::copy(v.stride.begin() + idx[i] * r, v.stride.begin() + (idx[i] + 1) * r, stride.begin() + i * r);
+    base[i] = v.base[idx[i]];
+  }
+  v.qn.swap(qn);
+  v.base.swap(base);
+  v.stride.swap(stride);
+}
+
+OpView input_view(const NetTensor& nt, int slot) {
+  const tnx_tensor* t = nt.t;
+  const int r = t->rank;
+  OpView v;
+  v.slot = slot;
+  v.labels = nt.labels;
+  for (int j = 0; j < r; ++j) v.bonds.push_back(t->bonds[nt.perm[j]]);
+  v.nblk = t->nblk;
+  v.qn.resize((size_t)v.nblk * r);
+  v.stride.resize((size_t)v.nblk * r);
+  v.base = t->off;
+  for (int64_t b = 0; b < t->nblk; ++b) {
+    auto st = rowmajor(&t->shape[(size_t)b * r], r);
+    for (int j = 0; j < r; ++j) {
+      v.qn[(size_t)b * r + j] = t->qn[(size_t)b * r + nt.perm[j]];
+      v.stride[(size_t)b * r + j] = st[nt.perm[j]];
+    }
+  }
+  sort_view(v);
+  return v;
+}
+
+// Drop unit legs and merge neighbours that are contiguous in both source and destination.
+void finish_task(CopyTask& t, std::vector<int64_t> shape, std::vector<int64_t> ss, std::vector<int64_t> ds) {
+  std::vector<int64_t> sh2, s2, d2;
+  for (size_t l = 0; l < shape.size(); ++l) {
+    if (shape[l] == 1) continue;
+    if (!sh2.empty() && s2.back() == ss[l] * shape[l] && d2.back() == ds[l] * shape[l]) {
+      sh2.back() *= shape[l];
+      s2.back() = ss[l];
+      d2.back() = ds[l];
+    } else {
+      sh2.push_back(shape[l]);
+      s2.push_back(ss[l]);
+      d2.push_back(ds[l]);
+    }
+  }
+  if (sh2.empty()) { sh2.push_back(1); s2.push_back(1); d2.push_back(1); }
+  if (sh2.size() > TNX_MAXR) fail(TNX_ERR_UNSUPPORTED, "block copy of rank above the limit");
+  t.rank = (int)sh2.size();
+  t.nelem = 1;
+  for (size_t l = 0; l < sh2.size(); ++l) {
+    if (sh2[l] > INT32_MAX) fail(TNX_ERR_UNSUPPORTED, "block extent above 2^31");
+    t.shape[l] = (int32_t)sh2[l];
+    t.sstride[l] = s2[l];
+    t.dstride[l] = d2[l];
+    t.nelem *= sh2[l];
+  }
+}
+
+// Every element a task touches must lie inside its slot's buffer: checked on
+// the host before anything is launched.
+void validate_tasks(const Plan& p, const std::vector<CopyTask>& tasks) {
+  for (const auto& t : tasks) {
+    int64_t ms = t.src_off, md = t.dst_off;
+    for (int l = 0; l < t.rank; ++l) {
+      if (t.sstride[l] < 0 || t.dstride[l] < 0 || t.shape[l] < 1) fail(TNX_ERR_ARG, "internal: malformed relayout task");
+      ms += (int64_t)(t.shape[l] - 1) * t.sstride[l];
+      md += (int64_t)(t.shape[l] - 1) * t.dstride[l];
+    }
+    if (t.dst_slot < 0 || t.dst_slot >= (int)p.slot_elems.size() || t.dst_off < 0 || md >= p.slot_elems[t.dst_slot])
+      fail(TNX_ERR_ARG, "internal: relayout destination out of bounds");
+    if (t.src_slot >= 0 && (t.src_slot >= (int)p.slot_elems.size() || t.src_off < 0 || ms >= p.slot_elems[t.src_slot]))
+      fail(TNX_ERR_ARG, "internal: relayout source out of bounds");
+  }
+}
+
+TaskList upload_tasks(Plan& p, const std::vector<CopyTask>& tasks) {
+  validate_tasks(p, tasks);
+  TaskList tl;
+  std::vector<int64_t> start(tasks.size() + 1, 0);
+  for (size_t i = 0; i < tasks.size(); ++i) start[i + 1] = start[i] + tasks[i].nelem;
+  tl.n = (int)tasks.size();
+  tl.total = start.back();
+  tl.d = p.upload(tasks);
+  tl.start = p.upload(start);
+  return tl;
+}
+
+int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// ------------------------------------------------------ matching (device)
+void run_match(Plan& p, StepPlan& s) {
+  tnx_ctx* ctx = p.ctx;
+  const OpView &A = s.A, &B = s.B;
+  MatchArgs a;
+  memset(&a, 0, sizeof(a));
+  const int nsym = A.rank() ? A.bonds[0].nsym : (B.rank() ? B.bonds[0].nsym : 0);
+  s.nsym = nsym;
+  a.nk = (int)s.ka.size();
+  a.nfa = (int)s.fa.size();
+  a.nfb = (int)s.fb.size();
+  a.nsym = nsym;
+  if (a.nk > TNX_MAXR || a.nfa > TNX_MAXR || a.nfb > TNX_MAXR) fail(TNX_ERR_UNSUPPORTED, "rank above the limit");
+  std::vector<int64_t> deg;
+  std::vector<int32_t> kq;
+  auto add_leg = [&](const BondD& b, MatchLeg& ml, bool kleg) {
+    ml.nsec = b.nsec;
+    ml.sec_base = (int)deg.size();
+    for (int sct = 0; sct < b.nsec; ++sct) {
+      deg.push_back(b.deg[sct]);
+      for (int c = 0; c < nsym; ++c) kq.push_back(kleg ? b.signed_q(sct, c) : 0);
+    }
+  };
+  int64_t kspace = 1, faspace = 1, fbspace = 1;
+  for (int i = 0; i < a.nk; ++i) { add_leg(A.bonds[s.ka[i]], a.kleg[i], true); kspace *= A.bonds[s.ka[i]].nsec; }
+  for (int i = 0; i < a.nfa; ++i) { add_leg(A.bonds[s.fa[i]], a.faleg[i], false); faspace *= A.bonds[s.fa[i]].nsec; }
+  for (int i = 0; i < a.nfb; ++i) { add_leg(B.bonds[s.fb[i]], a.fbleg[i], false); fbspace *= B.bonds[s.fb[i]].nsec; }
+  const int64_t LIM = int64_t(1) << 26;
+  if (kspace > LIM || faspace > LIM || fbspace > LIM) fail(TNX_ERR_UNSUPPORTED, "sector tuple space above 2^26");
+  int64_t cspace = 1;
+  for (int c = 0; c < nsym; ++c) {
+    const BondD& b0 = A.bonds[0];
+    a.zn[c] = b0.kinds[c] == TNX_ZN ? b0.zn[c] : 0;
+    if (a.zn[c] > 0) {
+      a.clo[c] = 0;
+      a.crange[c] = a.zn[c];
+    } else {
+      int64_t lo = 0, hi = 0;
+      for (int i = 0; i < a.nk; ++i) {
+        const BondD& b = A.bonds[s.ka[i]];
+        int32_t mn = INT32_MAX, mx = INT32_MIN;
+        for (int sct = 0; sct < b.nsec; ++sct) { mn = std::min(mn, b.signed_q(sct, c)); mx = std::max(mx, b.signed_q(sct, c)); }
+        lo += mn;
+        hi += mx;
+      }
+      if (hi - lo + 1 > (1 << 22)) fail(TNX_ERR_UNSUPPORTED, "charge range too wide");
+      a.clo[c] = (int32_t)lo;
+      a.crange[c] = (int32_t)(hi - lo + 1);
+    }
+    cspace *= a.crange[c];
+    if (cspace > (int64_t(1) << 24)) fail(TNX_ERR_UNSUPPORTED, "charge space above 2^24");
+  }
+  a.kspace = kspace;
+  a.faspace = faspace;
+  a.fbspace = fbspace;
+  a.cspace = cspace;
+  a.gmax = (int32_t)std::min<int64_t>(std::min(cspace, kspace), 4096);
+  a.nA = A.nblk;
+  a.nB = B.nblk;
+  a.rA = A.rank();
+  a.rB = B.rank();
+  for (int i = 0; i < a.nk; ++i) { a.kposA[i] = s.ka[i]; a.kposB[i] = s.kb[i]; }
+  for (int i = 0; i < a.nfa; ++i) a.fposA[i] = s.fa[i];
+  for (int i = 0; i < a.nfb; ++i) a.fposB[i] = s.fb[i];
+
+  // temporary device buffers (freed when this function returns)
+  std::vector<std::unique_ptr<DevBuf>> tmp;
+  auto dev = [&](size_t bytes) {
+    tmp.emplace_back(new DevBuf(ctx, std::max<size_t>(bytes, 256)));
+    return tmp.back()->p;
+  };
+  auto up = [&](const void* src, size_t bytes) {
+    void* d = dev(bytes);
+    if (bytes) CUDA_CHECK(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    return d;
+  };
+  a.deg = (const int64_t*)up(deg.data(), deg.size() * 8);
+  a.kcharge = (const int32_t*)up(kq.data(), kq.size() * 4);
+  a.qA = (const int32_t*)up(A.qn.data(), A.qn.size() * 4);
+  a.qB = (const int32_t*)up(B.qn.data(), B.qn.size() * 4);
+  a.kpres = (int32_t*)dev(kspace * 4);
+  a.kgroup = (int32_t*)dev(kspace * 4);
+  a.koff = (int64_t*)dev(kspace * 8);
+  a.rgroup = (int32_t*)dev(faspace * 4);
+  a.roff = (int64_t*)dev(faspace * 8);
+  a.cgroup = (int32_t*)dev(fbspace * 4);
+  a.coff = (int64_t*)dev(fbspace * 8);
+  a.cspres = (int32_t*)dev(cspace * 4);
+  a.csgid = (int32_t*)dev(cspace * 4);
+  a.scan_tmp = (int64_t*)dev(((size_t)1024 * a.gmax + 3 * (size_t)a.gmax) * 8);
+  a.ngroups = (int32_t*)dev(8);
+  a.status = a.ngroups + 1;
+  CUDA_CHECK(cudaMemsetAsync(a.ngroups, 0, 8, ctx->stream));
+  a.charges = (int32_t*)dev((size_t)a.gmax * std::max(nsym, 1) * 4);
+  a.mkn = (int64_t*)dev((size_t)a.gmax * 3 * 8);
+  a.amap = (int64_t*)dev((size_t)std::max<int64_t>(A.nblk, 1) * 3 * 8);
+  a.bmap = (int64_t*)dev((size_t)std::max<int64_t>(B.nblk, 1) * 3 * 8);
+  CUDA_CHECK(tnx_launch_match(a, ctx->stream));
+  int32_t hs[2];
+  CUDA_CHECK(cudaMemcpyAsync(hs, a.ngroups, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+  if (hs[1] == 1) fail(TNX_ERR_UNSUPPORTED, "more charge groups than the matching kernel supports");
+  if (hs[1] == 2) fail(TNX_ERR_ARG, "internal: charge outside the planned range");
+  s.G = hs[0];
+  s.charges.resize((size_t)s.G * nsym);
+  s.mkn.resize((size_t)s.G * 3);
+  s.amap.resize((size_t)A.nblk * 3);
+  s.bmap.resize((size_t)B.nblk * 3);
+  if (s.G && nsym) CUDA_CHECK(cudaMemcpyAsync(s.charges.data(), a.charges, s.charges.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  if (s.G) CUDA_CHECK(cudaMemcpyAsync(s.mkn.data(), a.mkn, s.mkn.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  if (A.nblk) CUDA_CHECK(cudaMemcpyAsync(s.amap.data(), a.amap, s.amap.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  if (B.nblk) CUDA_CHECK(cudaMemcpyAsync(s.bmap.data(), a.bmap, s.bmap.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+}
+
+int64_t block_dim(const OpView& v, int64_t b, const std::vector<int>& legs) {
+  int64_t d = 1;
+  for (int l : legs) d *= v.bonds[l].deg[v.qn[(size_t)b * v.rank() + l]];
+  return d;
+}
+
+// ------------------------------------------------------------- step plan
+void build_step(Plan& p, StepPlan& s) {
+  const OpView &A = s.A, &B = s.B;
+  std::vector<std::pair<int, int>> pairs;
+  for (int i = 0; i < A.rank(); ++i)
+    for (int j = 0; j < B.rank(); ++j)
+      if (A.labels[i] == B.labels[j]) pairs.push_back({i, j});
+  std::sort(pairs.begin(), pairs.end());
+  for (auto& pr : pairs) {
+    check_contractible(A.bonds[pr.first], B.bonds[pr.second], A.labels[pr.first]);
+    s.ka.push_back(pr.first);
+    s.kb.push_back(pr.second);
+  }
+  for (int i = 0; i < A.rank(); ++i)
+    if (std::find(s.ka.begin(), s.ka.end(), i) == s.ka.end()) s.fa.push_back(i);
+  for (int j = 0; j < B.rank(); ++j)
+    if (std::find(s.kb.begin(), s.kb.end(), j) == s.kb.end()) s.fb.push_back(j);
+  if (A.rank() && B.rank() && !A.bonds[0].same_syms(B.bonds[0]))
+    fail(TNX_ERR_BOND_MISMATCH, "tensors with different symmetries in one network");
+
+  run_match(p, s);
+  const int G = s.G;
+
+  // packed operand layouts: A_g [M x ldK] and B_g [N x ldK] (K-major), C_g [M x N]
+  s.ldK.resize(G);
+  s.offA.resize(G);
+  s.offB.resize(G);
+  s.offC.resize(G);
+  int64_t oa = 0, ob = 0, oc = 0;
+  for (int g = 0; g < G; ++g) {
+    const int64_t M = s.mkn[3 * g], K = s.mkn[3 * g + 1], N = s.mkn[3 * g + 2];
+    s.ldK[g] = align_up(std::max<int64_t>(K, 1), 4);
+    s.offA[g] = oa;
+    s.offB[g] = ob;
+    s.offC[g] = oc;
+    oa = align_up(oa + M * s.ldK[g], 32);
+    ob = align_up(ob + N * s.ldK[g], 32);
+    oc = align_up(oc + M * N, 32);
+  }
+  s.slotA = p.new_slot(p.alloc_zero((size_t)oa * 8), oa);
+  s.slotB = p.new_slot(p.alloc_zero((size_t)ob * 8), ob);
+  s.slotC = p.new_slot(p.alloc_zero((size_t)oc * 8), oc);
+
+  // relayout tasks
+  std::vector<CopyTask> ta, tb;
+  const int rA = A.rank(), rB = B.rank();
+  for (int64_t b = 0; b < A.nblk; ++b) {
+    const int64_t g = s.amap[3 * b];
+    if (g < 0) continue;
+    CopyTask t;
+    memset(&t, 0, sizeof(t));
+    t.src_slot = A.slot;
+    t.dst_slot = s.slotA;
+    t.src_off = A.base[b];
+    t.dst_off = s.offA[g] + s.amap[3 * b + 1] * s.ldK[g] + s.amap[3 * b + 2];
+    std::vector<int64_t> shape, ss, ds;
+    for (int l : s.fa) { shape.push_back(A.bonds[l].deg[A.qn[b * rA + l]]); ss.push_back(A.stride[b * rA + l]); }
+    for (int l : s.ka) { shape.push_back(A.bonds[l].deg[A.qn[b * rA + l]]); ss.push_back(A.stride[b * rA + l]); }
+    ds.assign(shape.size(), 0);
+    int64_t acc = 1;
+    for (int i = (int)shape.size() - 1; i >= (int)s.fa.size(); --i) { ds[i] = acc; acc *= shape[i]; }
+    acc = s.ldK[g];
+    for (int i = (int)s.fa.size() - 1; i >= 0; --i) { ds[i] = acc; acc *= shape[i]; }
+    finish_task(t, shape, ss, ds);
+    ta.push_back(t);
+  }
+  for (int64_t b = 0; b < B.nblk; ++b) {
+    const int64_t g = s.bmap[3 * b];
+    if (g < 0) continue;
+    CopyTask t;
+    memset(&t, 0, sizeof(t));
+    t.src_slot = B.slot;
+    t.dst_slot = s.slotB;
+    t.src_off = B.base[b];
+    t.dst_off = s.offB[g] + s.bmap[3 * b + 2] * s.ldK[g] + s.bmap[3 * b + 1];
+    std::vector<int64_t> shape, ss, ds;
+    for (int l : s.fb) { shape.push_back(B.bonds[l].deg[B.qn[b * rB + l]]); ss.push_back(B.stride[b * rB + l]); }
+    for (int l : s.kb) { shape.push_back(B.bonds[l].deg[B.qn[b * rB + l]]); ss.push_back(B.stride[b * rB + l]); }
+    ds.assign(shape.size(), 0);
+    int64_t acc = 1;
+    for (int i = (int)shape.size() - 1; i >= (int)s.fb.size(); --i) { ds[i] = acc; acc *= shape[i]; }
+    acc = s.ldK[g];
+    for (int i = (int)s.fb.size() - 1; i >= 0; --i) { ds[i] = acc; acc *= shape[i]; }
+    finish_task(t, shape, ss, ds);
+    tb.push_back(t);
+  }
+  s.copyA = upload_tasks(p, ta);
+  s.copyB = upload_tasks(p, tb);
+
+  // grouped GEMM
+  std::vector<GemmGroup> gg(G);
+  std::vector<GemmTile> tiles;
+  for (int g = 0; g < G; ++g) {
+    GemmGroup& x = gg[g];
+    memset(&x, 0, sizeof(x));
+    x.a_slot = s.slotA;
+    x.b_slot = s.slotB;
+    x.c_slot = s.slotC;
+    x.a_off = s.offA[g];
+    x.b_off = s.offB[g];
+    x.c_off = s.offC[g];
+    x.M = (int32_t)s.mkn[3 * g];
+    x.K = (int32_t)s.mkn[3 * g + 1];
+    x.N = (int32_t)s.mkn[3 * g + 2];
+    x.lda = x.ldb = (int32_t)s.ldK[g];
+    x.ldc = x.N;
+    for (int m0 = 0; m0 < x.M; m0 += 64)
+      for (int n0 = 0; n0 < x.N; n0 += 64) tiles.push_back(GemmTile{g, m0, n0, 0});
+  }
+  s.dG = p.upload(gg);
+  s.dT = p.upload(tiles);
+  s.ntiles = (int)tiles.size();
+
+  // useful flops: matched block pairs share (group, K offset)
+  std::map<std::pair<int64_t, int64_t>, std::pair<double, double>> acc;
+  std::map<std::pair<int64_t, int64_t>, double> kd;
+  for (int64_t b = 0; b < A.nblk; ++b) {
+    if (s.amap[3 * b] < 0) continue;
+    auto key = std::make_pair(s.amap[3 * b], s.amap[3 * b + 2]);
+    acc[key].first += (double)block_dim(A, b, s.fa);
+    kd[key] = (double)block_dim(A, b, s.ka);
+  }
+  for (int64_t b = 0; b < B.nblk; ++b) {
+    if (s.bmap[3 * b] < 0) continue;
+    acc[std::make_pair(s.bmap[3 * b], s.bmap[3 * b + 1])].second += (double)block_dim(B, b, s.fb);
+  }
+  s.flops = 0;
+  for (auto& kv : acc) s.flops += 2.0 * kv.second.first * kd[kv.first] * kv.second.second;
+
+  // output view: the fused matrices C_g, one block per (row tuple, column tuple)
+  OpView& C = s.C;
+  C.slot = s.slotC;
+  for (int l : s.fa) { C.bonds.push_back(A.bonds[l]); C.labels.push_back(A.labels[l]); }
+  for (int l : s.fb) { C.bonds.push_back(B.bonds[l]); C.labels.push_back(B.labels[l]); }
+  std::vector<std::map<std::vector<int32_t>, int64_t>> rows(G), cols(G);
+  for (int64_t b = 0; b < A.nblk; ++b) {
+    const int64_t g = s.amap[3 * b];
+    if (g < 0) continue;
+    std::vector<int32_t> key;
+    for (int l : s.fa) key.push_back(A.qn[b * rA + l]);
+    rows[g][key] = s.amap[3 * b + 1];
+  }
+  for (int64_t b = 0; b < B.nblk; ++b) {
+    const int64_t g = s.bmap[3 * b];
+    if (g < 0) continue;
+    std::vector<int32_t> key;
+    for (int l : s.fb) key.push_back(B.qn[b * rB + l]);
+    cols[g][key] = s.bmap[3 * b + 2];
+  }
+  const int rC = C.rank();
+  for (int g = 0; g < G; ++g) {
+    const int64_t N = s.mkn[3 * g + 2];
+    for (auto& rr : rows[g])
+      for (auto& cc : cols[g]) {
+        C.qn.insert(C.qn.end(), rr.first.begin(), rr.first.end());
+        C.qn.insert(C.qn.end(), cc.first.begin(), cc.first.end());
+        C.base.push_back(s.offC[g] + rr.second * N + cc.second);
+        std::vector<int64_t> st(rC);
+        int64_t a2 = 1;
+        for (int i = (int)cc.first.size() - 1; i >= 0; --i) {
+          st[s.fa.size() + i] = a2;
+          a2 *= C.bonds[s.fa.size() + i].deg[cc.first[i]];
+        }
+        a2 = N;
+        for (int i = (int)rr.first.size() - 1; i >= 0; --i) {
+          st[i] = a2;
+          a2 *= C.bonds[i].deg[rr.first[i]];
+        }
+        C.stride.insert(C.stride.end(), st.begin(), st.end());
+        C.nblk++;
+      }
+  }
+  sort_view(C);
+}
+
+// final relayout: root view -> canonical output blocks in TOUT order
+void build_final(Plan& p, const OpView& root, const std::vector<std::string>& tout) {
+  const int r = (int)tout.size();
+  if (r != root.rank()) fail(TNX_ERR_NETWORK, "TOUT does not match the open legs");
+  std::vector<int> pos(r);
+  p.out_bonds.clear();
+  for (int j = 0; j < r; ++j) {
+    auto it = std::find(root.labels.begin(), root.labels.end(), tout[j]);
+    if (it == root.labels.end()) fail(TNX_ERR_NETWORK, "TOUT label '" + tout[j] + "' is not an open leg");
+    pos[j] = (int)(it - root.labels.begin());
+    p.out_bonds.push_back(root.bonds[pos[j]]);
+  }
+  p.out_labels = tout;
+  std::map<std::vector<int32_t>, int64_t> rootblk;
+  for (int64_t b = 0; b < root.nblk; ++b) {
+    std::vector<int32_t> k(r);
+    for (int j = 0; j < r; ++j) k[j] = root.qn[b * r + pos[j]];
+    rootblk[k] = b;
+  }
+  std::vector<int32_t> qn;
+  int64_t nblk;
+  enumerate_blocks(p.out_bonds, qn, nblk);
+  std::vector<CopyTask> tasks;
+  int64_t off = 0;
+  for (int64_t b = 0; b < nblk; ++b) {
+    std::vector<int32_t> k(qn.begin() + b * r, qn.begin() + (b + 1) * r);
+    std::vector<int64_t> shape(r);
+    for (int j = 0; j < r; ++j) shape[j] = p.out_bonds[j].deg[k[j]];
+    auto ds = rowmajor(shape.data(), r);
+    CopyTask t;
+    memset(&t, 0, sizeof(t));
+    t.dst_slot = p.out_slot;
+    t.dst_off = off;
+    std::vector<int64_t> ss(r, 0);
+    auto it = rootblk.find(k);
+    if (it != rootblk.end()) {
+      t.src_slot = root.slot;
+      t.src_off = root.base[it->second];
+      for (int j = 0; j < r; ++j) ss[j] = root.stride[it->second * r + pos[j]];
+    } else {
+      t.src_slot = -1;
+    }
+    finish_task(t, shape, ss, ds);
+    tasks.push_back(t);
+    int64_t n = 1;
+    for (auto x : shape) n *= x;
+    off += n;
+  }
+  p.fin = upload_tasks(p, tasks);
+}
+
+std::string plan_key(const tnx_network* net, const std::string& order) {
+  std::string k = order + "#" + std::to_string(net->prec);
+  for (auto& t : net->ts) {
+    k += "#" + t.name + "(";
+    for (size_t j = 0; j < t.perm.size(); ++j) k += t.t->bonds[t.perm[j]].key() + "/";
+    k += ")";
+  }
+  return k;
+}
+
+std::string dims_key(const tnx_network* net) {
+  std::string k;
+  for (auto& t : net->ts) {
+    for (size_t j = 0; j < t.perm.size(); ++j) k += std::to_string(t.t->bonds[t.perm[j]].dim) + ",";
+    k += ";";
+  }
+  return k;
+}
+
+void require_put(const tnx_network* net) {
+  for (auto& t : net->ts)
+    if (!t.t) fail(TNX_ERR_NETWORK, "tensor '" + t.name + "' has not been put");
+}
+
+void ensure_order(tnx_network* net) {
+  require_put(net);
+  if (net->optimal) {
+    std::string dk = dims_key(net);
+    if (dk != net->order_dims_key) {
+      optimal_tree(net);
+      net->order_dims_key = dk;
+    }
+  }
+}
+
+void build_split_parts(Plan& p, StepPlan& s);
+
+Plan* ensure_plan(tnx_network* net) {
+  ensure_order(net);
+  const std::string order = tree_string(net, net->root);
+  const std::string key = plan_key(net, order);
+  if (net->plan && net->plan->key == key) return net->plan.get();
+  net->plan.reset();
+  std::unique_ptr<Plan> p(new Plan());
+  p->ctx = net->ctx;
+  p->prec = net->prec;
+  p->key = key;
+  p->order = order;
+  p->nin = (int)net->ts.size();
+  for (int i = 0; i < p->nin; ++i) {
+    const tnx_tensor* t = net->ts[i].t;
+    p->new_slot(t->data, t->rank == 0 ? 1 : t->nelem);
+  }
+  {
+    std::vector<BondD> ob;
+    for (auto& l : net->tout) {
+      for (auto& t : net->ts)
+        for (size_t j = 0; j < t.labels.size(); ++j)
+          if (t.labels[j] == l) ob.push_back(t.t->bonds[t.perm[j]]);
+    }
+    std::vector<int32_t> q;
+    int64_t nb = 0;
+    enumerate_blocks(ob, q, nb);
+    int64_t ne = ob.empty() ? 1 : 0;
+    for (int64_t b = 0; b < nb && !ob.empty(); ++b) {
+      int64_t n = 1;
+      for (size_t j = 0; j < ob.size(); ++j) n *= ob[j].deg[q[b * ob.size() + j]];
+      ne += n;
+    }
+    p->out_slot = p->new_slot(nullptr, ne);
+  }
+  p->d_status = (int32_t*)p->alloc_zero(64);
+  std::function<OpView(int)> walk = [&](int node) -> OpView {
+    const TreeNode& n = net->tree[node];
+    if (n.leaf >= 0) return input_view(net->ts[n.leaf], n.leaf);
+    OpView A = walk(n.l);
+    OpView B = walk(n.r);
+    p->steps.emplace_back();
+    StepPlan& s = p->steps.back();
+    s.A = std::move(A);
+    s.B = std::move(B);
+    build_step(*p, s);
+    if (p->prec == TNX_PREC_SPLIT_BF16 || p->prec == TNX_PREC_SPLIT_F16 || p->prec == TNX_PREC_TF32)
+      build_split_parts(*p, s);
+    return p->steps.back().C;
+  };
+  OpView root = walk(net->root);
+  build_final(*p, root, net->tout);
+  p->d_slots = (double**)p->alloc_zero(p->h_slots.size() * sizeof(double*));
+  p->h_slots_dev.assign(p->h_slots.size(), nullptr);
+  CUDA_CHECK(cudaStreamSynchronize(net->ctx->stream));
+  net->plan = std::move(p);
+  return net->plan.get();
+}
+
+void sync_slots(Plan& p) {
+  if (p.h_slots == p.h_slots_dev) return;
+  CUDA_CHECK(cudaMemcpyAsync(p.d_slots, p.h_slots.data(), p.h_slots.size() * sizeof(double*), cudaMemcpyHostToDevice,
+                             p.ctx->stream));
+  p.h_slots_dev = p.h_slots;
+}
+
+void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st);
+
+void enqueue_plan(Plan& p, cudaStream_t st) {
+  tnx_ctx* c = p.ctx;
+  for (auto& s : p.steps) {
+    {
+      ProfScope ps(c, st, TNX_KC_RELAYOUT, 16.0 * (double)(s.copyA.total + s.copyB.total));
+      CUDA_CHECK(tnx_launch_copy(s.copyA.d, s.copyA.start, s.copyA.n, s.copyA.total, p.d_slots, st));
+      CUDA_CHECK(tnx_launch_copy(s.copyB.d, s.copyB.start, s.copyB.n, s.copyB.total, p.d_slots, st));
+    }
+    switch (p.prec) {
+      case TNX_PREC_F64: {
+        ProfScope ps(c, st, TNX_KC_GEMM, s.flops);
+        CUDA_CHECK(tnx_launch_gemm_f64(s.dG, s.dT, s.ntiles, p.d_slots, st));
+        break;
+      }
+      case TNX_PREC_F32: {
+        ProfScope ps(c, st, TNX_KC_GEMM, s.flops);
+        CUDA_CHECK(tnx_launch_gemm_f32(s.dG, s.dT, s.ntiles, p.d_slots, st));
+        break;
+      }
+      default: enqueue_split(p, s, st); break;
+    }
+  }
+  ProfScope ps(c, st, TNX_KC_FINAL, 16.0 * (double)p.fin.total);
+  CUDA_CHECK(tnx_launch_copy(p.fin.d, p.fin.start, p.fin.n, p.fin.total, p.d_slots, st));
+}
+
+void bind_inputs(tnx_network* net, Plan& p) {
+  for (int i = 0; i < p.nin; ++i) p.h_slots[i] = net->ts[i].t->data;
+}
+
+void check_out_bonds(const Plan& p, const tnx_tensor* out) {
+  if ((int)p.out_bonds.size() != out->rank) fail(TNX_ERR_BOND_MISMATCH, "output rank differs from TOUT");
+  for (int j = 0; j < out->rank; ++j)
+    if (out->bonds[j] != p.out_bonds[j]) fail(TNX_ERR_BOND_MISMATCH, "output bonds differ from the TOUT bonds");
+}
+
+}  // namespace
+
+namespace {
+void build_split_parts(Plan& p, StepPlan& s) { tnx_build_split_parts(p, s); }
+void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st) { tnx_enqueue_split(p, s, st); }
+}  // namespace
+
+// ------------------------------------------------------------------ C-ABI
+static bool all_put(const tnx_network* net);
+
+extern "C" tnx_status tnx_network_create(tnx_ctx* ctx, const char* spec, tnx_network** out) {
+  return tnx_guard(ctx, [&] {
+    if (!ctx || !spec || !out) fail(TNX_ERR_ARG, "null argument");
+    std::unique_ptr<tnx_network> net(new tnx_network());
+    net->ctx = ctx;
+    std::string text(spec), line, order;
+    bool have_tout = false;
+    size_t p0 = 0;
+    while (p0 <= text.size()) {
+      size_t p1 = text.find('\n', p0);
+      if (p1 == std::string::npos) p1 = text.size();
+      line = trim(text.substr(p0, p1 - p0));
+      p0 = p1 + 1;
+      if (line.empty()) continue;
+      size_t c = line.find(':');
+      if (c == std::string::npos) fail(TNX_ERR_NETWORK, "line without ':' : " + line);
+      std::string key = trim(line.substr(0, c)), rest = trim(line.substr(c + 1));
+      if (key == "TOUT") {
+        net->tout = split_labels(rest);
+        have_tout = true;
+      } else if (key == "ORDER") {
+        order = rest;
+      } else {
+        if (!valid_name(key)) fail(TNX_ERR_NETWORK, "bad tensor name '" + key + "'");
+        for (auto& t : net->ts)
+          if (t.name == key) fail(TNX_ERR_NETWORK, "duplicate tensor name '" + key + "'");
+        NetTensor nt;
+        nt.name = key;
+        nt.labels = split_labels(rest);
+        std::set<std::string> u(nt.labels.begin(), nt.labels.end());
+        if (u.size() != nt.labels.size()) fail(TNX_ERR_NETWORK, "a label appears twice on tensor '" + key + "'");
+        if ((int)nt.labels.size() > TNX_MAXR) fail(TNX_ERR_UNSUPPORTED, "tensor rank above the limit");
+        net->ts.push_back(nt);
+      }
+    }
+    if (!have_tout) fail(TNX_ERR_NETWORK, "missing TOUT");
+    if (net->ts.empty()) fail(TNX_ERR_NETWORK, "no tensors");
+    std::map<std::string, int> cnt;
+    for (auto& t : net->ts)
+      for (auto& l : t.labels) cnt[l]++;
+    std::set<std::string> open;
+    for (auto& kv : cnt) {
+      if (kv.second > 2) fail(TNX_ERR_NETWORK, "label '" + kv.first + "' appears on more than two tensors");
+      if (kv.second == 1) open.insert(kv.first);
+    }
+    std::set<std::string> to(net->tout.begin(), net->tout.end());
+    if (to.size() != net->tout.size() || to != open) fail(TNX_ERR_NETWORK, "TOUT must list exactly the open labels");
+    if (!order.empty()) set_tree_from_string(net.get(), order);
+    else set_default_tree(net.get());
+    *out = net.release();
+  });
+}
+
+extern "C" tnx_status tnx_network_destroy(tnx_network* net) {
+  if (!net) return TNX_ERR_ARG;
+  cudaStreamSynchronize(net->ctx->stream);
+  delete net;
+  return TNX_OK;
+}
+
+extern "C" tnx_status tnx_network_put(tnx_network* net, const char* name, tnx_tensor* t, int nlab,
+                                      const char* const* labels) {
+  if (!net) return TNX_ERR_ARG;
+  return tnx_guard(net->ctx, [&] {
+    if (!name || !t) fail(TNX_ERR_ARG, "null argument");
+    NetTensor* nt = nullptr;
+    for (auto& x : net->ts)
+      if (x.name == name) nt = &x;
+    if (!nt) fail(TNX_ERR_NETWORK, std::string("no tensor named '") + name + "' in the network");
+    const int r = (int)nt->labels.size();
+    if (t->rank != r) fail(TNX_ERR_NETWORK, "rank of the tensor differs from the blueprint");
+    std::vector<int> perm(r);
+    if (!labels) {
+      std::iota(perm.begin(), perm.end(), 0);
+    } else {
+      if (nlab != r) fail(TNX_ERR_NETWORK, "one label per leg is required");
+      std::vector<int> used(r, 0);
+      for (int j = 0; j < r; ++j) {
+        int found = -1;
+        for (int i = 0; i < r; ++i)
+          if (labels[i] && nt->labels[j] == labels[i]) found = i;
+        if (found < 0 || used[found]) fail(TNX_ERR_NETWORK, "labels must be a permutation of the blueprint labels");
+        used[found] = 1;
+        perm[j] = found;
+      }
+    }
+    nt->t = t;
+    nt->perm = perm;
+  });
+}
+
+extern "C" tnx_status tnx_network_set_order(tnx_network* net, int optimal, const char* order) {
+  if (!net) return TNX_ERR_ARG;
+  return tnx_guard(net->ctx, [&] {
+    if (optimal) {
+      net->optimal = true;
+      net->order_dims_key.clear();
+      if (all_put(net)) ensure_order(net);
+    } else {
+      if (!order || !*order) fail(TNX_ERR_NETWORK, "an explicit order is required when optimal is off");
+      set_tree_from_string(net, order);
+      net->optimal = false;
+    }
+  });
+}
+
+static bool all_put(const tnx_network* net) {
+  for (auto& t : net->ts)
+    if (!t.t) return false;
+  return true;
+}
+
+// With optimal on and every tensor loaded, the tree reflects the loaded
+// dimensions (computed now, or reused while the dimensions are unchanged).
+extern "C" tnx_status tnx_network_get_order(const tnx_network* cnet, char* buf, size_t len) {
+  if (!cnet || !buf) return TNX_ERR_ARG;
+  tnx_network* net = const_cast<tnx_network*>(cnet);
+  return tnx_guard(net->ctx, [&] {
+    if (net->optimal && all_put(net)) ensure_order(net);
+    std::string s = tree_string(net, net->root);
+    if (s.size() + 1 > len) fail(TNX_ERR_ARG, "buffer too small for the order string");
+    memcpy(buf, s.c_str(), s.size() + 1);
+  });
+}
+
+extern "C" tnx_status tnx_network_set_precision(tnx_network* net, int prec) {
+  if (!net) return TNX_ERR_ARG;
+  if (prec < TNX_PREC_F64 || prec > TNX_PREC_TF32) return TNX_ERR_ARG;
+  net->prec = prec;
+  return TNX_OK;
+}
+
+extern "C" tnx_status tnx_network_launch_into(tnx_network* net, tnx_tensor* out) {
+  if (!net) return TNX_ERR_ARG;
+  return tnx_guard(net->ctx, [&] {
+    if (!out) fail(TNX_ERR_ARG, "null output");
+    Plan* p = ensure_plan(net);
+    check_out_bonds(*p, out);
+    bind_inputs(net, *p);
+    p->h_slots[p->out_slot] = out->data;
+    sync_slots(*p);
+    enqueue_plan(*p, net->ctx->stream);
+  });
+}
+
+extern "C" tnx_status tnx_network_launch(tnx_network* net, tnx_tensor** out) {
+  if (!net) return TNX_ERR_ARG;
+  return tnx_guard(net->ctx, [&] {
+    if (!out) fail(TNX_ERR_ARG, "null output");
+    Plan* p = ensure_plan(net);
+    std::unique_ptr<tnx_tensor> t(make_tensor(net->ctx, p->out_bonds));
+    tnx_status s = tnx_network_launch_into(net, t.get());
+    if (s != TNX_OK) throw TnxError{s, net->ctx->err};
+    *out = t.release();
+  });
+}
+
+extern "C" tnx_status tnx_network_flops(tnx_network* net, double* flops) {
+  if (!net || !flops) return TNX_ERR_ARG;
+  return tnx_guard(net->ctx, [&] {
+    Plan* p = ensure_plan(net);
+    double f = 0;
+    for (auto& s : p->steps) f += s.flops;
+    *flops = f;
+  });
+}
+
+extern "C" tnx_status tnx_network_nsteps(tnx_network* net, int* nsteps) {
+  if (!net || !nsteps) return TNX_ERR_ARG;
+  return tnx_guard(net->ctx, [&] { *nsteps = (int)ensure_plan(net)->steps.size(); });
+}
+
+extern "C" tnx_status tnx_network_step_sizes(tnx_network* net, int step, int* ngroups, int* nsym, int64_t* nA,
+                                             int64_t* nB) {
+  if (!net) return TNX_ERR_ARG;
+  return tnx_guard(net->ctx, [&] {
+    Plan* p = ensure_plan(net);
+    if (step < 0 || step >= (int)p->steps.size()) fail(TNX_ERR_ARG, "step out of range");
+    const StepPlan& s = p->steps[step];
+    if (ngroups) *ngroups = s.G;
+    if (nsym) *nsym = s.nsym;
+    if (nA) *nA = s.A.nblk;
+    if (nB) *nB = s.B.nblk;
+  });
+}
+
+extern "C" tnx_status tnx_network_step_tables(tnx_network* net, int step, int32_t* charges, int64_t* mkn,
+                                              int64_t* amap, int64_t* bmap) {
+  if (!net) return TNX_ERR_ARG;
+  return tnx_guard(net->ctx, [&] {
+    Plan* p = ensure_plan(net);
+    if (step < 0 || step >= (int)p->steps.size()) fail(TNX_ERR_ARG, "step out of range");
+    const StepPlan& s = p->steps[step];
+    if (charges) std::copy(s.charges.begin(), s.charges.end(), charges);
+    if (mkn) std::copy(s.mkn.begin(), s.mkn.end(), mkn);
+    if (amap) std::copy(s.amap.begin(), s.amap.end(), amap);
+    if (bmap) std::copy(s.bmap.begin(), s.bmap.end(), bmap);
+  });
+}
+
+// ---------------------------------------------------------------- Lanczos
+extern "C" tnx_status tnx_lanczos(tnx_network* net, const char* vec_slot, tnx_tensor* v0, int nsteps, double* eval,
+                                  tnx_tensor* evec, int* nmatvec) {
+  if (!net) return TNX_ERR_ARG;
+  return tnx_guard(net->ctx, [&] {
+    tnx_ctx* ctx = net->ctx;
+    if (!vec_slot || !v0 || !eval || nsteps < 1 || nsteps > 500) fail(TNX_ERR_ARG, "bad Lanczos arguments");
+    int slot = -1;
+    for (size_t i = 0; i < net->ts.size(); ++i)
+      if (net->ts[i].name == vec_slot) slot = (int)i;
+    if (slot < 0) fail(TNX_ERR_NETWORK, std::string("no tensor named '") + vec_slot + "'");
+    NetTensor& vt = net->ts[slot];
+    if (!vt.t) {
+      vt.t = v0;
+      vt.perm.assign(v0->rank, 0);
+      std::iota(vt.perm.begin(), vt.perm.end(), 0);
+    }
+    for (int j = 0; j < (int)vt.perm.size(); ++j)
+      if (vt.perm[j] != j) fail(TNX_ERR_NETWORK, "the vector slot must be put in blueprint leg order");
+    if (v0->bonds != vt.t->bonds) fail(TNX_ERR_BOND_MISMATCH, "v0 bonds differ from the vector slot's bonds");
+    Plan* p = ensure_plan(net);
+    if (p->out_bonds != v0->bonds) fail(TNX_ERR_BOND_MISMATCH, "the operator's output bonds differ from the vector's");
+    if (evec) check_out_bonds(*p, evec);
+    const int64_t n = v0->nelem;
+    LanczosDev L;
+    memset(&L, 0, sizeof(L));
+    L.n = n;
+    L.nmax = nsteps;
+    L.nblocks = tnx_reduce_blocks(n);
+    std::vector<std::unique_ptr<DevBuf>> bufs;
+    auto dev = [&](size_t bytes) {
+      bufs.emplace_back(new DevBuf(ctx, std::max<size_t>(bytes, 256)));
+      CUDA_CHECK(cudaMemsetAsync(bufs.back()->p, 0, std::max<size_t>(bytes, 256), ctx->stream));
+      return bufs.back()->p;
+    };
+    L.V = (double*)dev((size_t)(nsteps + 1) * n * 8);
+    L.w = (double*)dev((size_t)n * 8);
+    L.alpha = (double*)dev((size_t)(nsteps + 1) * 8);
+    L.beta = (double*)dev((size_t)(nsteps + 2) * 8);
+    L.coef = (double*)dev((size_t)(nsteps + 2) * 8);
+    L.partial = (double*)dev((size_t)std::max<int64_t>(1216, (int64_t)L.nblocks * (nsteps + 2)) * 8);
+    L.y = (double*)dev((size_t)(nsteps + 1) * 8);
+    L.scratch = (double*)dev((size_t)(4 * (nsteps + 1)) * 8);
+    L.state = (int32_t*)dev(64);
+    L.eval = (double*)dev(64);
+    bind_inputs(net, *p);
+    p->h_slots[p->out_slot] = L.w;
+    sync_slots(*p);
+    cudaStream_t st = ctx->stream;
+    {
+      ProfScope ps(ctx, st, TNX_KC_VECTOR, 24.0 * (double)n);
+      CUDA_CHECK(tnx_launch_lanczos_init(L, v0->data, st));
+    }
+    for (int j = 0; j < nsteps; ++j) {
+      CUDA_CHECK(tnx_launch_lanczos_set_input(p->d_slots + slot, L, j, st));
+      enqueue_plan(*p, st);
+      // bytes of one step: alpha dot (2n), axpy (3n+n), 2 x Gram-Schmidt over
+      // j+1 vectors (dots (j+1)n + n, update (j+1)n + 2n), norm (n), scale (2n)
+      ProfScope ps(ctx, st, TNX_KC_VECTOR, 8.0 * (double)n * (2 + 4 + 2 * (2.0 * (j + 1) + 3) + 1 + 2));
+      CUDA_CHECK(tnx_launch_lanczos_step(L, j, st));
+    }
+    {
+      ProfScope ps(ctx, st, TNX_KC_VECTOR, evec ? 8.0 * (double)n * (nsteps + 2) : 0.0);
+      CUDA_CHECK(tnx_launch_lanczos_finish(L, evec ? evec->data : nullptr, st));
+    }
+    // the device slot of the vector now points into L.V: restore the table
+    p->h_slots_dev.assign(p->h_slots.size(), nullptr);
+    double* hp = (double*)ctx->pinned;
+    CUDA_CHECK(cudaMemcpyAsync(hp, L.eval, 8, cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaMemcpyAsync(hp + 1, L.state, 8, cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    *eval = hp[0];
+    if (nmatvec) *nmatvec = ((int32_t*)(hp + 1))[0];
+  });
+}

@@ -1,0 +1,118 @@
+// Host-only plan structures shared by the planner (tnx_network.cpp) and the
+// split-precision planner (tnx_split.cpp).
+#pragma once
+
+#include <algorithm>
+#include <cstring>
+
+#include "tnx_host.h"
+
+struct NetTensor {
+  std::string name;
+  std::vector<std::string> labels;
+  tnx_tensor* t = nullptr;
+  std::vector<int> perm;   // perm[j] = leg of t realising blueprint leg j
+};
+
+struct TreeNode {
+  int leaf = -1, l = -1, r = -1;
+};
+
+struct OpView {
+  std::vector<BondD> bonds;
+  std::vector<std::string> labels;
+  int64_t nblk = 0;
+  std::vector<int32_t> qn;      // nblk * rank, lexicographic
+  std::vector<int64_t> base;    // nblk
+  std::vector<int64_t> stride;  // nblk * rank
+  int slot = -1;
+  int rank() const { return (int)bonds.size(); }
+};
+
+struct TaskList {
+  CopyTask* d = nullptr;
+  int64_t* start = nullptr;
+  int n = 0;
+  int64_t total = 0;
+};
+
+struct StepPlan {
+  OpView A, B, C;
+  std::vector<int> ka, kb, fa, fb;
+  int G = 0;
+  std::vector<int32_t> charges;
+  std::vector<int64_t> mkn, amap, bmap;
+  std::vector<int64_t> ldK, offA, offB, offC;
+  double flops = 0;
+  int nsym = 0;
+  int slotA = -1, slotB = -1, slotC = -1;
+  TaskList copyA, copyB;
+  GemmGroup* dG = nullptr;
+  GemmTile* dT = nullptr;
+  int ntiles = 0;
+  // split precision
+  int slotSA = -1, slotSB = -1, slotEA = -1, slotEB = -1;
+  SliceJob* dJobs = nullptr;
+  int njobs = 0;
+  int64_t* dRowStart = nullptr;
+  int64_t totRows = 0;
+  int64_t* dTileStart = nullptr;
+  int64_t totTiles = 0;
+  SplitGroup* dSG = nullptr;
+  GemmTile* dST = nullptr;
+  int nstiles = 0;
+};
+
+struct Plan {
+  tnx_ctx* ctx = nullptr;
+  std::vector<std::unique_ptr<DevBuf>> bufs;
+  std::vector<double*> h_slots, h_slots_dev;   // wanted / last uploaded
+  double** d_slots = nullptr;
+  int nin = 0, out_slot = 0;
+  std::vector<StepPlan> steps;
+  std::vector<BondD> out_bonds;
+  std::vector<std::string> out_labels;
+  TaskList fin;
+  int prec = TNX_PREC_F64;
+  int nslice = 6, beta = 7;
+  int32_t* d_status = nullptr;
+  std::string key;
+  std::string order;
+  ~Plan() = default;
+
+  template <class T>
+  T* upload(const std::vector<T>& v) {
+    size_t n = std::max<size_t>(v.size(), 1) * sizeof(T);
+    bufs.emplace_back(new DevBuf(ctx, n));
+    if (!v.empty()) CUDA_CHECK(cudaMemcpyAsync(bufs.back()->p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    return (T*)bufs.back()->p;
+  }
+  void* alloc_zero(size_t bytes) {
+    bufs.emplace_back(new DevBuf(ctx, std::max<size_t>(bytes, 256)));
+    CUDA_CHECK(cudaMemsetAsync(bufs.back()->p, 0, std::max<size_t>(bytes, 256), ctx->stream));
+    return bufs.back()->p;
+  }
+  std::vector<int64_t> slot_elems;   // size of each slot's buffer, in doubles
+  int new_slot(void* p, int64_t elems) {
+    h_slots.push_back((double*)p);
+    slot_elems.push_back(elems);
+    return (int)h_slots.size() - 1;
+  }
+};
+
+struct tnx_network {
+  tnx_ctx* ctx = nullptr;
+  std::vector<NetTensor> ts;
+  std::vector<std::string> tout;
+  std::vector<TreeNode> tree;
+  int root = -1;
+  bool optimal = false;
+  int prec = TNX_PREC_F64;
+  std::string order_dims_key;      // dims for which the optimal tree was computed
+  std::unique_ptr<Plan> plan;
+};
+
+
+// split-precision planning and launch (tnx_split.cpp)
+void tnx_build_split_parts(Plan& p, StepPlan& s);
+void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st);
