@@ -1,0 +1,458 @@
+// Split-precision grouped GEMM on the tcgen05 tensor cores (sm_103a).
+//
+// The fused-sector products of a pairwise contraction (Sec. 7 of
+// arXiv 2401.01921; the paper runs them as FP64 library GEMMs) are computed to
+// FP64 accuracy from 16-bit tensor-core products with the error-free slicing
+// of Ozaki, Ogita, Oishi and Rump (Numer. Algorithms 59, 2012):
+//
+//  * every row of A (and every column of B) gets a common power-of-two scale
+//    2^(E+1) from the exponent E of its largest entry; an entry x becomes the
+//    fixed-point integer fix = floor(|x| 2^(F-E-1)) < 2^F, F = n*beta, which is
+//    cut into n slices of beta bits, s_i in [0, 2^beta), so that
+//    |x| ~ sum_i s_i 2^(E+1-beta(i+1)); each slice (with the sign of x) is an
+//    integer, exact in BF16 or FP16;
+//  * the product sum_k a_k b_k becomes sum over slice pairs (i, j); pairs with
+//    the same level t = i + j share one FP32 accumulator in tensor memory; all
+//    pairs with t <= n-1 are formed (terms below 2^-(beta n) are dropped);
+//  * the K loop runs in chunks of KC = 128: with beta = 7 a level sums at most
+//    n * KC * 127^2 < 2^24, so every FP32 accumulation is exact; after each
+//    chunk the levels are read out of tensor memory and added, exactly, into
+//    a 64-bit integer fixed-point accumulator I = sum_t L_t 2^(beta(n-1-t));
+//  * the result is rounded once: C = I * 2^(E_r + E_c + 2 - beta(n+1)).
+// The only error is the truncation of each operand to F bits below its
+// row / column maximum and the dropped levels: about 2^-40 relative to
+// max|row| * max|col| * K.
+//
+// Kernel layout: one CTA per 128 x 64 output tile, 6 warps: warp 0 issues the
+// bulk copies (the TMA engine, cp.async.bulk) of pre-tiled slices into a
+// 3-stage shared-memory ring, warp 1 issues tcgen05.mma (one elected lane),
+// warps 2-5 drain tensor memory (tcgen05.ld) into the integer accumulators
+// and write FP64.  Operands sit in global memory already in the canonical
+// no-swizzle K-major core-matrix layout, so a stage is one contiguous copy.
+// Every wait on an mbarrier is bounded (about a second of clock); a wait that
+// runs out records an error code and the CTA winds down without hanging.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "tnx_internal.h"
+
+namespace {
+
+constexpr int TM = 128;            // tile rows (A)
+constexpr int TN = 64;             // tile columns (B rows)
+constexpr int TK = 32;             // K per stage
+constexpr int KC = 128;            // K per exact chunk
+constexpr int STAGES = 3;
+constexpr int MAXN = 6;            // slices
+constexpr int ATILE = TM * TK * 2; // bytes of one A slice tile (8 KB)
+constexpr int BTILE = TN * TK * 2; // bytes of one B slice tile (4 KB)
+constexpr long long WAIT_LIMIT = 2000000000LL;   // clock cycles (~1 s)
+
+// ------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; returns false (and records `code`) if the limit runs out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, int32_t* status, int code,
+                                          volatile int* abort_flag) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, phase)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > WAIT_LIMIT) {
+      atomicExch(status, code);
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: no swizzle, K-major, core matrices of
+// 8 rows x 16 bytes; LBO = stride between core matrices along K (128 B),
+// SBO = stride between 8-row groups (512 B for a 32-wide K tile).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version for tcgen05
+  return d;                 // base offset 0, swizzle none
+}
+
+// instruction descriptor, kind::f16: D f32, A/B bf16 (1) or f16 (0), both K-major
+__device__ __forceinline__ uint32_t instr_desc(int f16) {
+  const uint32_t ab = f16 ? 0u : 1u;
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ------------------------------------------------------- exponent pass
+// One warp per row of a packed operand: biased exponent of the row's largest |x|.
+__global__ void row_exponent_kernel(const SliceJob* __restrict__ jobs, const int64_t* __restrict__ row_start,
+                                    int njobs, int64_t total, double* const* __restrict__ slots) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < total; r += warps) {
+    int lo = 0, hi = njobs;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (__ldg(row_start + mid) <= r) lo = mid; else hi = mid;
+    }
+    const SliceJob& j = jobs[lo];
+    const int64_t row = r - __ldg(row_start + lo);
+    const unsigned long long* x = (const unsigned long long*)(slots[j.src_slot] + j.src_off + row * j.ld);
+    unsigned long long m = 0;
+    for (int k = lane; k < j.K; k += 32) {
+      const unsigned long long b = x[k] & 0x7FFFFFFFFFFFFFFFull;
+      m = b > m ? b : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+      m = v > m ? v : m;
+    }
+    if (lane == 0) ((int32_t*)slots[j.exp_slot])[j.exp_off + row] = (int32_t)(m >> 52);
+  }
+}
+
+// ------------------------------------------------------------ slicing
+__device__ __forceinline__ uint16_t slice_bits(uint32_t s, uint32_t neg, int f16) {
+  // s < 2^beta <= 256: exact as float via the 2^23 magic, exact in bf16 / f16
+  const float f = __int_as_float(0x4B000000 | s) - 8388608.0f;
+  uint16_t b;
+  if (f16) b = __half_as_ushort(__float2half_rn(f));
+  else b = (uint16_t)(__float_as_uint(f) >> 16);
+  return (s != 0 && neg) ? (uint16_t)(b | 0x8000) : b;
+}
+
+// One warp per (8-row group, 32-wide K tile) of a padded operand; lane =
+// (row in group) * 4 + (8-column group).  Writes 16 bytes per slice per lane.
+__global__ void slice_kernel(const SliceJob* __restrict__ jobs, const int64_t* __restrict__ warp_start, int njobs,
+                             int64_t total, int nslice, int beta, int f16, double* const* __restrict__ slots) {
+  const int lane = threadIdx.x & 31;
+  const int r8 = lane >> 2, kq = lane & 3;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int F = nslice * beta;
+  const uint32_t mask = (1u << beta) - 1u;
+  for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += warps) {
+    int lo = 0, hi = njobs;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (__ldg(warp_start + mid) <= w) lo = mid; else hi = mid;
+    }
+    const SliceJob& j = jobs[lo];
+    const int64_t wl = w - __ldg(warp_start + lo);
+    const int KT = (j.K + TK - 1) / TK;
+    const int64_t rg = wl / KT;       // 8-row group in the padded operand
+    const int kt = (int)(wl % KT);
+    const int64_t row = rg * 8 + r8;
+    const int k0 = kt * TK + kq * 8;
+    const double* src = slots[j.src_slot] + j.src_off + row * j.ld;
+    const bool live = row < j.rows;
+    const int eb_r = live ? ((const int32_t*)slots[j.exp_slot])[j.exp_off + row] : 0;
+    uint32_t sl[MAXN][4];
+#pragma unroll
+    for (int i = 0; i < MAXN; ++i)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sl[i][q] = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = k0 + e;
+      unsigned long long bits = 0;
+      if (live && k < j.K) bits = __double_as_longlong(src[k]);
+      const uint32_t neg = (uint32_t)(bits >> 63);
+      const int eb = (int)((bits >> 52) & 0x7FF);
+      unsigned long long fix = 0;
+      if (eb != 0 && eb_r != 0) {
+        const unsigned long long m53 = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const int rs = 53 - F + (eb_r - eb);
+        fix = rs >= 64 ? 0ull : (m53 >> rs);
+      }
+#pragma unroll
+      for (int i = 0; i < MAXN; ++i) {
+        if (i < nslice) {
+          const uint32_t s = (uint32_t)(fix >> (beta * (nslice - 1 - i))) & mask;
+          const uint32_t b = slice_bits(s, neg, f16);
+          sl[i][e >> 1] |= (e & 1) ? (b << 16) : b;
+        }
+      }
+    }
+    const int tile_rows = j.tile_rows;
+    const int64_t mt = row / tile_rows;
+    const int rin = (int)(row % tile_rows);
+    const int64_t tile_bytes = (int64_t)tile_rows * TK * 2;
+    char* base = (char*)slots[j.dst_slot] + j.dst_off_bytes;
+    const int64_t inner = (int64_t)(rin >> 3) * 512 + kq * 128 + (rin & 7) * 16;
+#pragma unroll
+    for (int i = 0; i < MAXN; ++i) {
+      if (i < nslice) {
+        uint4 v = make_uint4(sl[i][0], sl[i][1], sl[i][2], sl[i][3]);
+        *(uint4*)(base + ((mt * KT + kt) * nslice + i) * tile_bytes + inner) = v;
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------- split GEMM
+struct SplitShared {
+  uint64_t full[STAGES], empty[STAGES];
+  uint64_t accfull, accempty, done;
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+template <int NS>
+__global__ void __launch_bounds__(192, 1) split_gemm_kernel(const SplitGroup* __restrict__ groups,
+                                                             const GemmTile* __restrict__ tiles, int beta, int f16,
+                                                             double* const* __restrict__ slots, int32_t* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // stage ring: STAGES x (NS A tiles + NS B tiles), 1024-byte aligned
+  unsigned char* ring = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int STAGE_BYTES = NS * (ATILE + BTILE);
+  SplitShared* sh = (SplitShared*)(ring + STAGES * STAGE_BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  const GemmTile tl = tiles[blockIdx.x];
+  const SplitGroup g = groups[tl.group];
+  const int KT = (g.K + TK - 1) / TK;
+  const int KTPC = KC / TK;                      // K tiles per exact chunk
+  const int nchunks = (KT + KTPC - 1) / KTPC;
+  const int mt = tl.m0 / TM, nt = tl.n0 / TN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&sh->full[s], 1);
+      mbar_init(&sh->empty[s], 1);
+    }
+    mbar_init(&sh->accfull, 1);
+    mbar_init(&sh->accempty, 4);
+    mbar_init(&sh->done, 1);
+    sh->abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&sh->tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sh->tmem_base;
+  volatile int* abort_flag = &sh->abort_flag;
+
+  if (warp == 0) {
+    // ---------------- producer: bulk copies of pre-tiled slices
+    if (lane == 0) {
+      const char* Ab = (const char*)slots[g.a_slot] + g.a_off_bytes;
+      const char* Bb = (const char*)slots[g.b_slot] + g.b_off_bytes;
+      int issued = 0;
+      for (int kt = 0; kt < KT && !*abort_flag; ++kt) {
+        const int s = kt % STAGES;
+        const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+        if (kt >= STAGES && !mbar_wait(&sh->empty[s], ph ^ 1u, status, 11, abort_flag)) break;
+        unsigned char* sa = ring + s * STAGE_BYTES;
+        unsigned char* sb = sa + NS * ATILE;
+        mbar_expect_tx(&sh->full[s], NS * (ATILE + BTILE));
+        bulk_g2s(sa, Ab + ((int64_t)mt * KT + kt) * NS * ATILE, NS * ATILE, &sh->full[s]);
+        bulk_g2s(sb, Bb + ((int64_t)nt * KT + kt) * NS * BTILE, NS * BTILE, &sh->full[s]);
+        issued = kt + 1;
+      }
+      // never leave copies in flight: wait (bounded) for every issued stage to land
+      for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt) {
+        const int s = kt % STAGES;
+        const long long t0 = clock64();
+        while (!mbar_try(&sh->full[s], (uint32_t)(kt / STAGES) & 1u) && clock64() - t0 < WAIT_LIMIT) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(f16);
+      for (int kt = 0; kt < KT; ++kt) {
+        const int s = kt % STAGES;
+        const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+        const int chunk = kt / KTPC;
+        const bool first_in_chunk = (kt % KTPC) == 0;
+        const bool last_in_chunk = ((kt + 1) % KTPC) == 0 || kt == KT - 1;
+        if (first_in_chunk && chunk > 0 && !mbar_wait(&sh->accempty, (uint32_t)(chunk - 1) & 1u, status, 12, abort_flag))
+          break;
+        if (!mbar_wait(&sh->full[s], ph, status, 13, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t sa = smem_u32(ring + s * STAGE_BYTES);
+        const uint32_t sb = sa + NS * ATILE;
+#pragma unroll
+        for (int ks = 0; ks < TK / 16; ++ks) {
+#pragma unroll
+          for (int t = 0; t < NS; ++t) {
+#pragma unroll
+            for (int i = 0; i <= t; ++i) {
+              const int jj = t - i;
+              const uint64_t ad = smem_desc(sa + i * ATILE + ks * 256);
+              const uint64_t bd = smem_desc(sb + jj * BTILE + ks * 256);
+              const uint32_t acc = (first_in_chunk && ks == 0 && i == 0) ? 0u : 1u;
+              mma_f16(tmem + (uint32_t)(t * TN), ad, bd, idesc, acc);
+            }
+          }
+        }
+        mma_commit(&sh->empty[s]);
+        if (last_in_chunk) mma_commit(&sh->accfull);
+      }
+      // all MMAs issued by this thread have completed before tensor memory is freed
+      mma_commit(&sh->done);
+      const long long t0 = clock64();
+      while (!mbar_try(&sh->done, 0) && clock64() - t0 < WAIT_LIMIT) {
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5, TMEM lanes 32*(warp%4) ..
+    const int sub = warp & 3;
+    const int row = tl.m0 + sub * 32 + lane;
+    long long acc[TN];
+#pragma unroll
+    for (int c = 0; c < TN; ++c) acc[c] = 0;
+    bool ok = true;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      if (!mbar_wait(&sh->accfull, (uint32_t)ch & 1u, status, 14, abort_flag)) { ok = false; break; }
+      tc_fence_after();
+#pragma unroll
+      for (int cg = 0; cg < TN / 16; ++cg) {
+#pragma unroll
+        for (int t = 0; t < NS; ++t) {
+          uint32_t v[16];
+          tmem_ld16(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(t * TN + cg * 16), v);
+          tmem_wait_ld();
+          const long long scale_t = 1LL << (beta * (NS - 1 - t));
+#pragma unroll
+          for (int c = 0; c < 16; ++c) acc[cg * 16 + c] += (long long)__float2int_rn(__uint_as_float(v[c])) * scale_t;
+        }
+      }
+      tc_fence_before();
+      if (lane == 0) mbar_arrive(&sh->accempty);
+    }
+    if (ok && row < g.M) {
+      const int eb_r = ((const int32_t*)slots[g.ea_slot])[g.ea_off + row];
+      double* crow = slots[g.c_slot] + g.c_off + (int64_t)row * g.ldc;
+      const int32_t* eb_c = (const int32_t*)slots[g.eb_slot] + g.eb_off;
+#pragma unroll
+      for (int c = 0; c < TN; ++c) {
+        const int col = tl.n0 + c;
+        if (col < g.N) {
+          const int e = eb_r + eb_c[col] - 2046 + 2 - beta * (NS + 1);
+          crow[col] = acc[c] == 0 ? 0.0 : scalbn((double)acc[c], e);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+}
+
+}  // namespace
+
+cudaError_t tnx_launch_row_exponents(const SliceJob* jobs, const int64_t* row_start, int njobs, int64_t total_rows,
+                                     double* const* slots, cudaStream_t st) {
+  if (total_rows <= 0) return cudaSuccess;
+  int64_t blocks = (total_rows + 7) / 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  row_exponent_kernel<<<(int)blocks, 256, 0, st>>>(jobs, row_start, njobs, total_rows, slots);
+  tnx_note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tnx_launch_slices(const SliceJob* jobs, const int64_t* warp_start, int njobs, int64_t total_warps,
+                              int nslice, int beta, int f16, double* const* slots, cudaStream_t st) {
+  if (total_warps <= 0) return cudaSuccess;
+  if (nslice < 1 || nslice > MAXN || beta < 1 || beta > 8 || nslice * beta > 53) return cudaErrorInvalidValue;
+  int64_t blocks = (total_warps + 7) / 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  slice_kernel<<<(int)blocks, 256, 0, st>>>(jobs, warp_start, njobs, total_warps, nslice, beta, f16, slots);
+  tnx_note_launch(1);
+  return cudaGetLastError();
+}
+
+size_t tnx_split_smem_bytes(int nslice) {
+  return 1024 + (size_t)STAGES * nslice * (ATILE + BTILE) + sizeof(SplitShared) + 64;
+}
+
+cudaError_t tnx_launch_gemm_split(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int nslice, int beta,
+                                  int f16, double* const* slots, int32_t* status, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (nslice != MAXN || beta != 7) return cudaErrorInvalidValue;
+  const size_t smem = tnx_split_smem_bytes(nslice);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<MAXN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  split_gemm_kernel<MAXN><<<ntiles, 192, smem, st>>>(groups, tiles, beta, f16, slots, status);
+  tnx_note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tnx_launch_gemm_tf32(const SplitGroup*, const GemmTile*, int, double* const*, int32_t*, cudaStream_t) {
+  return cudaErrorNotSupported;
+}

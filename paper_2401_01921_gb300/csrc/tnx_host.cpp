@@ -154,6 +154,8 @@ extern "C" tnx_status tnx_ctx_create(int device, void* stream, tnx_alloc_fn allo
   c->user = user;
   tnx_status s = tnx_guard(c, [&] {
     c->scratch = new DevBuf(c, 64 * 1024);
+    c->d_status = (int32_t*)((char*)c->scratch->p + 63 * 1024);
+    CUDA_CHECK(cudaMemsetAsync(c->d_status, 0, 64, c->stream));
     c->pinned = nullptr;
     CUDA_CHECK(cudaMallocHost(&c->pinned, 4096));
   });
@@ -177,9 +179,24 @@ extern "C" tnx_status tnx_ctx_destroy(tnx_ctx* ctx) {
   return TNX_OK;
 }
 
+void check_device_status(tnx_ctx* ctx) {
+  int32_t* h = (int32_t*)ctx->pinned + 512;
+  CUDA_CHECK(cudaMemcpyAsync(h, ctx->d_status, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+  if (*h != 0) {
+    const int code = *h;
+    CUDA_CHECK(cudaMemsetAsync(ctx->d_status, 0, 4, ctx->stream));
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    fail(TNX_ERR_TIMEOUT, "a bounded device wait ran out (site " + std::to_string(code) + ")");
+  }
+}
+
 extern "C" tnx_status tnx_sync(tnx_ctx* ctx) {
   if (!ctx) return TNX_ERR_ARG;
-  return tnx_guard(ctx, [&] { CUDA_CHECK(cudaStreamSynchronize(ctx->stream)); });
+  return tnx_guard(ctx, [&] {
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    check_device_status(ctx);
+  });
 }
 
 // -------------------------------------------------------------------- bonds

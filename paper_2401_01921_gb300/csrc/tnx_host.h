@@ -39,6 +39,7 @@ struct tnx_ctx {
   std::string err;
   DevBuf* scratch = nullptr;   // small device scratch (norm partials)
   void* pinned = nullptr;      // small pinned host buffer
+  int32_t* d_status = nullptr; // device status word written by bounded waits (0 = ok)
   // profiler (CUDA events around kernel classes)
   bool prof = false;
   std::vector<ProfRec> prof_pending;
@@ -111,6 +112,8 @@ struct tnx_tensor {
 };
 
 tnx_status tnx_guard(tnx_ctx* ctx, const std::function<void()>& f);
+// after a stream sync: fail with TNX_ERR_TIMEOUT if a device wait ran out (and clear it)
+void check_device_status(tnx_ctx* ctx);
 void check_contractible(const BondD& a, const BondD& b, const std::string& label);
 void enumerate_blocks(const std::vector<BondD>& bonds, std::vector<int32_t>& qn, int64_t& nblk);
 tnx_tensor* make_tensor(tnx_ctx* ctx, const std::vector<BondD>& bonds);

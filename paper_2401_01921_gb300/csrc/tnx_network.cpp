@@ -1113,6 +1113,7 @@ extern "C" tnx_status tnx_lanczos(tnx_network* net, const char* vec_slot, tnx_te
     CUDA_CHECK(cudaMemcpyAsync(hp, L.eval, 8, cudaMemcpyDeviceToHost, st));
     CUDA_CHECK(cudaMemcpyAsync(hp + 1, L.state, 8, cudaMemcpyDeviceToHost, st));
     CUDA_CHECK(cudaStreamSynchronize(st));
+    check_device_status(ctx);
     *eval = hp[0];
     if (nmatvec) *nmatvec = ((int32_t*)(hp + 1))[0];
   });

@@ -1,0 +1,95 @@
+"""GPU parity of the reduced / split-precision products against the FP64 oracle.
+
+Split BF16 / FP16 (Ozaki-style slices on tcgen05, exact FP32 chunks, int64
+recombination): relative Frobenius error <= 1e-10 on every workload, and
+bit-exact on integer inputs whose slices carry them exactly.  FP32: the error
+is reported, bounded loosely (1e-5).
+"""
+import numpy as np
+import pytest
+
+import tnx_inputs as I
+
+from gpu_harness import lib_heff, oracle_heff, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+TOL_SPLIT = 1e-10
+
+WORKLOADS = {
+    "u1_chi40_ragged": lambda: I.heisenberg_workload(40, 9),
+    "u1_chi512": lambda: I.heisenberg_workload(512, 20),
+    "u1_chi2048_scaled": lambda: I.heisenberg_workload(2048, 40, sector_scale=True),
+    "dense_chi32": lambda: I.dense_workload(32),
+    "hubbard_chi128": lambda: I.hubbard_workload(128),
+}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2401_01921_gb300 as tnx
+    from paper_2401_01921_gb300 import build
+    build.build()
+    return tnx.Context(0)
+
+
+_REF = {}
+
+
+def reference(name):
+    if name not in _REF:
+        onet, _ = oracle_heff(WORKLOADS[name]())
+        _REF[name] = onet.launch()
+    return _REF[name]
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "split_f16"])
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_split_parity(ctx, name, prec):
+    wl = WORKLOADS[name]()
+    net, T, B = lib_heff(ctx, wl, prec=prec)
+    out = net.launch(B["psi"])
+    err = rel_fro(out.block_dict(), reference(name))
+    print(f"{name} {prec}: rel err {err:.3e}")
+    assert err <= TOL_SPLIT, err
+
+
+def test_f32_error_reported(ctx):
+    wl = WORKLOADS["u1_chi512"]()
+    net, T, B = lib_heff(ctx, wl, prec="f32")
+    err = rel_fro(net.launch(B["psi"]).block_dict(), reference("u1_chi512"))
+    print(f"u1_chi512 f32: rel err {err:.3e}")
+    assert 1e-12 < err < 1e-5
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "split_f16"])
+def test_split_exact_on_integers(ctx, prec):
+    """Integer entries in [-3, 3]: every slice is exact, so the split products equal the FP64 ones bit for bit."""
+    import paper_2401_01921_gb300 as tnx
+    from paper_2401_01921_gb300.heff import build_network
+    wl = I.heisenberg_workload(40, 9)
+    bonds = I.heff_bonds(wl)
+
+    def ints(name):
+        base = I.heff_value_fn(wl, name)
+        if name in ("W1", "W2"):
+            return lambda c: np.round(2 * base(c))        # MPO entries 0, +-1/2, 1 -> 0, +-1, 2
+        return lambda c: np.clip(np.round(base(c) * 1.5), -3, 3)
+
+    res = {}
+    for p in ("f64", prec):
+        tensors = {n: (bonds[n], ints(n)) for n in I.HEFF_NAMES}
+        net, T, B = build_network(ctx, I.HEFF_SPEC, tensors, wl.nsym, prec=p)
+        res[p] = net.launch(B["psi"]).download()
+    assert np.abs(res["f64"]).max() > 100
+    assert np.array_equal(res["f64"], res[prec])
+
+
+def test_split_lanczos(ctx):
+    wl = I.heisenberg_workload(512, 20)
+    import paper_2401_01921_gb300 as tnx
+    lam = {}
+    for p in ("f64", "split_bf16"):
+        net, T, B = lib_heff(ctx, wl, symmetric=True, prec=p)
+        lam[p], _ = tnx.lanczos(net, "psi", T["psi"], 20)
+    assert abs(lam["f64"] - lam["split_bf16"]) <= 1e-10 * abs(lam["f64"])
