@@ -226,7 +226,7 @@ def main():
     net, T, B = build_network(ctx, I.HEFF_SPEC, tensors, wl.nsym, prec=prec)
     apply_flops = net.flops()
     evec = tnx.Tensor(ctx, B["psi"])
-    stream = torch.cuda.current_stream(dev)
+    stream = ctx.stream          # the library's stream: events are recorded on it
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def step():
@@ -248,6 +248,7 @@ def main():
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.zero_()
+            torch.cuda.synchronize(dev)
             s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             s.record(stream)
             lam, k = step()

@@ -126,7 +126,8 @@ class Context:
         self.device = device
         self._keep: dict[int, object] = {}
         if stream is None:
-            stream = torch.cuda.current_stream(device)
+            # a stream of its own: CUDA graphs cannot be captured on the legacy default stream
+            stream = torch.cuda.Stream(device)
         self.stream = stream
         sp = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         if torch_alloc:

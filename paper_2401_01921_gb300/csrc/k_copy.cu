@@ -9,54 +9,116 @@
 //
 // A task copies one block: per leg a shape, a source stride and a destination
 // stride (elements); the legs are ordered so that the last one is contiguous
-// in the destination.  Threads walk destination order, so stores coalesce;
-// when the source is contiguous along the same leg the loads coalesce too.
+// in the destination.  The planner cuts every task into chunks of at most
+// CHUNK elements; one CTA takes one chunk (one descriptor load, no search),
+// its threads walk destination order so stores coalesce, and loads coalesce
+// whenever the source is contiguous along the same leg.  When the source is
+// contiguous along another leg, the task is moved in 32 x 32 tiles staged
+// through shared memory instead, so both sides coalesce.  Index arithmetic is
+// 32-bit inside a task.
 #include "tnx_internal.h"
 
 namespace {
 
 constexpr int CT = 256;
 
-__device__ __forceinline__ int find_task(const int64_t* start, int n, int64_t e) {
-  int lo = 0, hi = n;   // start[lo] <= e < start[hi]
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (__ldg(start + mid) <= e) lo = mid; else hi = mid;
+// Transposing task: the source is contiguous along leg S = t.tleg, the
+// destination along the last leg.  View the block as a matrix with one column
+// per index of S and one row per index of the other legs (in task order), and
+// move it in 32 x 32 tiles through shared memory: loads run along S, stores
+// along the rows (consecutive rows are consecutive in the destination).
+__device__ void copy_transpose(const CopyTask& t, int tile, double* const* __restrict__ slots) {
+  __shared__ double sm[32][33];
+  const int r = t.rank, S = t.tleg;
+  const int ncols = t.shape[S];
+  const int nrows = (int)(t.nelem / ncols);
+  const int nct = (ncols + 31) >> 5;
+  const int r0 = (tile / nct) << 5, c0 = (tile % nct) << 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double* src = t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr;
+  double* dst = slots[t.dst_slot] + t.dst_off;
+  // row index -> (source offset, destination offset) over the legs other than S
+  auto bases = [&](int row, int64_t& so, int64_t& dof) {
+    so = 0;
+    dof = 0;
+    for (int l = r - 1; l >= 0; --l) {
+      if (l == S) continue;
+      const int q = row / t.shape[l];
+      const int rem = row - q * t.shape[l];
+      row = q;
+      so += rem * t.sstride[l];
+      dof += rem * t.dstride[l];
+    }
+  };
+  const int c = c0 + lane;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int rr = wid + 8 * i, row = r0 + rr;
+    if (row < nrows && c < ncols) {
+      int64_t so, dof;
+      bases(row, so, dof);
+      sm[rr][lane] = src ? __ldg(src + so + (int64_t)c * t.sstride[S]) : 0.0;
+    }
   }
-  return lo;
+  __syncthreads();
+  const int row = r0 + lane;
+  if (row < nrows) {
+    int64_t so, dof;
+    bases(row, so, dof);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int cc = wid + 8 * i, col = c0 + cc;
+      if (col < ncols) dst[dof + (int64_t)col * t.dstride[S]] = sm[lane][cc];
+    }
+  }
 }
 
-__global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ tasks,
-                                                  const int64_t* __restrict__ start, int ntasks, int64_t total,
+__global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ tasks, const int2* __restrict__ chunks,
                                                   double* const* __restrict__ slots) {
-  for (int64_t e = (int64_t)blockIdx.x * CT + threadIdx.x; e < total; e += (int64_t)gridDim.x * CT) {
-    const int ti = find_task(start, ntasks, e);
-    const CopyTask& t = tasks[ti];
-    int64_t i = e - __ldg(start + ti);
-    int64_t so = t.src_off, dof = t.dst_off;
-    for (int l = t.rank - 1; l >= 0; --l) {
-      const int s = t.shape[l];
-      const int64_t q = i / s;
-      const int64_t r = i - q * s;
-      i = q;
-      so += r * t.sstride[l];
-      dof += r * t.dstride[l];
+  const int2 ch = chunks[blockIdx.x];           // (task, first element of the chunk, or tile index)
+  const CopyTask& t = tasks[ch.x];
+  if (t.tleg >= 0) {
+    copy_transpose(t, ch.y, slots);
+    return;
+  }
+  const int r = t.rank;
+  int shape[TNX_MAXR];
+  int64_t ss[TNX_MAXR], ds[TNX_MAXR];
+#pragma unroll
+  for (int l = 0; l < TNX_MAXR; ++l) {
+    if (l < r) {
+      shape[l] = t.shape[l];
+      ss[l] = t.sstride[l];
+      ds[l] = t.dstride[l];
     }
-    double v = 0.0;
-    if (t.src_slot >= 0) v = __ldg(slots[t.src_slot] + so);
-    slots[t.dst_slot][dof] = v;
+  }
+  const double* src = t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr;
+  double* dst = slots[t.dst_slot] + t.dst_off;
+  const int64_t lim = (int64_t)ch.y + TNX_COPY_CHUNK;
+  const int end = (int)(t.nelem < lim ? t.nelem : lim);
+  for (int e = ch.y + threadIdx.x; e < end; e += CT) {
+    int i = e;
+    int64_t so = 0, dof = 0;
+#pragma unroll
+    for (int l = TNX_MAXR - 1; l >= 0; --l) {
+      if (l < r) {
+        const int q = i / shape[l];
+        const int rem = i - q * shape[l];
+        i = q;
+        so += rem * ss[l];
+        dof += rem * ds[l];
+      }
+    }
+    dst[dof] = src ? __ldg(src + so) : 0.0;
   }
 }
 
 }  // namespace
 
-cudaError_t tnx_launch_copy(const CopyTask* tasks, const int64_t* elem_start, int ntasks, int64_t total,
-                            double* const* slots, cudaStream_t st) {
-  if (total <= 0) return cudaSuccess;
-  int64_t blocks = (total + CT - 1) / CT;
-  const int64_t cap = 152 * 16;
-  if (blocks > cap) blocks = cap;
-  copy_kernel<<<(int)blocks, CT, 0, st>>>(tasks, elem_start, ntasks, total, slots);
+cudaError_t tnx_launch_copy(const CopyTask* tasks, const int2* chunks, int nchunks, double* const* slots,
+                            cudaStream_t st) {
+  if (nchunks <= 0) return cudaSuccess;
+  copy_kernel<<<nchunks, CT, 0, st>>>(tasks, chunks, slots);
   tnx_note_launch(1);
   return cudaGetLastError();
 }

@@ -71,7 +71,50 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmGroup* __restrict__
   }
 }
 
+// Skinny products (K <= 16): one thread per row of a 128 x 64 tile keeps its
+// K entries of A in registers and walks the 64 columns, reading B from shared
+// memory (every thread reads the same B entry: a broadcast).  Used for the
+// MPO steps of H_eff (K, N ~ 10), where a square tile would be mostly padding.
+constexpr int SK_MAXK = 16;
+
+__global__ void __launch_bounds__(128) gemm_skinny_kernel(const GemmGroup* __restrict__ groups,
+                                                          const GemmTile* __restrict__ tiles,
+                                                          double* const* __restrict__ slots) {
+  __shared__ double Bs[64][SK_MAXK];
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmGroup g = groups[tl.group];
+  const double* A = slots[g.a_slot] + g.a_off;
+  const double* B = slots[g.b_slot] + g.b_off;
+  double* C = slots[g.c_slot] + g.c_off;
+  const int nn = min(64, g.N - tl.n0);
+  for (int i = threadIdx.x; i < 64 * SK_MAXK; i += 128) {
+    const int n = i / SK_MAXK, k = i % SK_MAXK;
+    Bs[n][k] = (n < nn && k < g.K) ? B[(int64_t)(tl.n0 + n) * g.ldb + k] : 0.0;
+  }
+  __syncthreads();
+  const int m = tl.m0 + threadIdx.x;
+  if (m >= g.M) return;
+  double a[SK_MAXK];
+#pragma unroll
+  for (int k = 0; k < SK_MAXK; ++k) a[k] = k < g.K ? A[(int64_t)m * g.lda + k] : 0.0;
+  double* crow = C + (int64_t)m * g.ldc + tl.n0;
+  for (int n = 0; n < nn; ++n) {
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < SK_MAXK; ++k) acc = fma(a[k], Bs[n][k], acc);
+    crow[n] = acc;
+  }
+}
+
 }  // namespace
+
+cudaError_t tnx_launch_gemm_skinny(const GemmGroup* groups, const GemmTile* tiles, int ntiles, double* const* slots,
+                                   cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  gemm_skinny_kernel<<<ntiles, 128, 0, st>>>(groups, tiles, slots);
+  tnx_note_launch(1);
+  return cudaGetLastError();
+}
 
 cudaError_t tnx_launch_gemm_f64(const GemmGroup* groups, const GemmTile* tiles, int ntiles,
                                 double* const* slots, cudaStream_t st) {

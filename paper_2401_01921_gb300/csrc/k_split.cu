@@ -13,7 +13,10 @@
 //    integer, exact in BF16 or FP16;
 //  * the product sum_k a_k b_k becomes sum over slice pairs (i, j); pairs with
 //    the same level t = i + j share one FP32 accumulator in tensor memory; all
-//    pairs with t <= n-1 are formed (terms below 2^-(beta n) are dropped);
+//    pairs with t <= n-1 are formed (terms below 2^-(beta n) are dropped); the
+//    accumulators of consecutive levels sit in consecutive TMEM columns, so
+//    one MMA of A slice i against the stacked B slices 0..n-1-i feeds all of
+//    its levels at once;
 //  * the K loop runs in chunks of KC = 128: with beta = 7 a level sums at most
 //    n * KC * 127^2 < 2^24, so every FP32 accumulation is exact; after each
 //    chunk the levels are read out of tensor memory and added, exactly, into
@@ -114,10 +117,33 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;                 // base offset 0, swizzle none
 }
 
-// instruction descriptor, kind::f16: D f32, A/B bf16 (1) or f16 (0), both K-major
-__device__ __forceinline__ uint32_t instr_desc(int f16) {
+// instruction descriptor, kind::f16: D f32, A/B bf16 (1) or f16 (0), both K-major, M = 128, N = n
+__device__ __forceinline__ uint32_t instr_desc(int f16, int n) {
   const uint32_t ab = f16 ? 0u : 1u;
-  return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+// (value of a 64-bit integer) * 2^e rounded to nearest-even FP64, with integer
+// operations only (the FP64 pipe of this part is slow); results below the
+// normal range flush to zero.
+__device__ __forceinline__ double i64_scaled_to_double(long long v, int e) {
+  if (v == 0) return 0.0;
+  const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
+  unsigned long long u = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int lz = __clzll(u);
+  u <<= lz;                                   // leading one at bit 63
+  unsigned long long mant = u >> 11;          // 53 bits
+  const unsigned long long rem = u & 0x7FFull;
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) mant += 1;
+  int ex = 63 - lz + e;
+  if (mant >> 53) {
+    mant >>= 1;
+    ex += 1;
+  }
+  const int biased = ex + 1023;
+  if (biased <= 0) return __longlong_as_double((long long)sign);
+  if (biased >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)biased << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -328,7 +354,6 @@ __global__ void __launch_bounds__(192, 1) split_gemm_kernel(const SplitGroup* __
   } else if (warp == 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = instr_desc(f16);
       for (int kt = 0; kt < KT; ++kt) {
         const int s = kt % STAGES;
         const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
@@ -341,17 +366,22 @@ __global__ void __launch_bounds__(192, 1) split_gemm_kernel(const SplitGroup* __
         tc_fence_after();
         const uint32_t sa = smem_u32(ring + s * STAGE_BYTES);
         const uint32_t sb = sa + NS * ATILE;
+        // A slice i meets the B slices j = 0 .. NS-1-i stacked along N (they are
+        // consecutive 64-row tiles, so the stack is one taller K-major operand);
+        // its output columns are the accumulators of levels i .. NS-1, also
+        // consecutive: one MMA (N <= 256, else two) per A slice and K step.
 #pragma unroll
         for (int ks = 0; ks < TK / 16; ++ks) {
 #pragma unroll
-          for (int t = 0; t < NS; ++t) {
+          for (int i = 0; i < NS; ++i) {
+            const uint64_t ad = smem_desc(sa + i * ATILE + ks * 256);
+            const uint32_t acc = (first_in_chunk && ks == 0 && i == 0) ? 0u : 1u;
+            const int nj = NS - i;
 #pragma unroll
-            for (int i = 0; i <= t; ++i) {
-              const int jj = t - i;
-              const uint64_t ad = smem_desc(sa + i * ATILE + ks * 256);
-              const uint64_t bd = smem_desc(sb + jj * BTILE + ks * 256);
-              const uint32_t acc = (first_in_chunk && ks == 0 && i == 0) ? 0u : 1u;
-              mma_f16(tmem + (uint32_t)(t * TN), ad, bd, idesc, acc);
+            for (int j0 = 0; j0 < nj; j0 += 4) {
+              const int cnt = (nj - j0) < 4 ? (nj - j0) : 4;
+              const uint64_t bd = smem_desc(sb + j0 * BTILE + ks * 256);
+              mma_f16(tmem + (uint32_t)((i + j0) * TN), ad, bd, instr_desc(f16, cnt * TN), acc);
             }
           }
         }
@@ -399,7 +429,7 @@ __global__ void __launch_bounds__(192, 1) split_gemm_kernel(const SplitGroup* __
         const int col = tl.n0 + c;
         if (col < g.N) {
           const int e = eb_r + eb_c[col] - 2046 + 2 - beta * (NS + 1);
-          crow[col] = acc[c] == 0 ? 0.0 : scalbn((double)acc[c], e);
+          crow[col] = i64_scaled_to_double(acc[c], e);
         }
       }
     }

@@ -4,8 +4,10 @@
 // vector (a LinOp).  Everything except that action runs here, in FP64, with
 // no host round trip inside the loop (so a whole solve can be captured in one
 // CUDA graph):
-//   alpha_j = <v_j, w>;  w -= alpha_j v_j + beta_j v_{j-1};
-//   twice: c = V^T w, w -= V c   (classical Gram-Schmidt, full reorthogonalisation);
+//   twice: c = V^T w, w -= V c   (classical Gram-Schmidt against every previous
+//   vector: full reorthogonalisation; the first pass's coefficient of v_j is
+//   alpha_j = <v_j, w>, and subtracting all coefficients subsumes the
+//   three-term recurrence);
 //   beta_{j+1} = ||w||; stop if beta_{j+1} < 1e-14 max|alpha|; v_{j+1} = w / beta_{j+1};
 // then Sturm bisection on the tridiagonal T and inverse iteration for its
 // eigenvector, and the Ritz vector V y.
@@ -87,66 +89,95 @@ __global__ void lanczos_init_kernel(LanczosDev L, const double* v0) {
 
 __global__ void set_slot_kernel(double** slot, double* p) { *slot = p; }
 
-// w -= a * v_j + b * v_{j-1}
-__global__ void lanczos_axpy2_kernel(LanczosDev L, int j) {
-  if (stopped(L.state)) return;
-  const double a = L.alpha[j];
-  const double b = L.beta[j];
-  const double* vj = L.V + (int64_t)j * L.n;
-  const double* vm = j > 0 ? L.V + (int64_t)(j - 1) * L.n : nullptr;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += (int64_t)gridDim.x * blockDim.x) {
-    double w = L.w[i] - a * vj[i];
-    if (vm) w -= b * vm[i];
-    L.w[i] = w;
-  }
-}
+// partial[b*m + i] = <V_i, w> over this block's contiguous chunk, i < m.  A
+// fixed grid of MD_BLOCKS blocks keeps the number of partial sums (and so the
+// FP64 additions of the reduction tree) small; each thread keeps 16 running
+// sums, w is read once per group of 16 vectors, and the block reduction goes
+// through shared memory: 16 rows of MD_T values, 8 threads per row.
+constexpr int MD_T = 128;
+constexpr int MD_BLOCKS = 152;
 
-// partial[b*(m) + i] = <V_i, w> over this block's contiguous chunk, i < m
-__global__ void __launch_bounds__(RT) multidot_kernel(LanczosDev L, int m) {
-  __shared__ double sh[32];
+__global__ void __launch_bounds__(MD_T) multidot_kernel(LanczosDev L, int m) {
+  __shared__ double sh[16][MD_T + 1];
   if (stopped(L.state)) return;
   const int64_t chunk = (L.n + gridDim.x - 1) / gridDim.x;
   const int64_t c0 = chunk * blockIdx.x, c1 = min(L.n, c0 + chunk);
-  for (int i = 0; i < m; ++i) {
-    const double* v = L.V + (int64_t)i * L.n;
-    double acc = 0.0;
-    for (int64_t x = c0 + threadIdx.x; x < c1; x += RT) acc = fma(v[x], L.w[x], acc);
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) L.partial[(int64_t)blockIdx.x * m + i] = acc;
+  for (int g0 = 0; g0 < m; g0 += 16) {
+    double acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = 0.0;
+    for (int64_t x = c0 + threadIdx.x; x < c1; x += MD_T) {
+      const double wx = L.w[x];
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (g0 + i < m) acc[i] = fma(L.V[(int64_t)(g0 + i) * L.n + x], wx, acc[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) sh[i][threadIdx.x] = acc[i];
+    __syncthreads();
+    // thread t sums 16 consecutive entries of row t/8, then 8 partners combine
+    const int row = threadIdx.x >> 3, part = threadIdx.x & 7;
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < MD_T / 8; ++q) v += sh[row][part * (MD_T / 8) + q];
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, 8);
+    if (part == 0 && g0 + row < m) L.partial[(int64_t)blockIdx.x * m + g0 + row] = v;
+    __syncthreads();
   }
 }
 
-// coef[i] = sum_b partial[b*m + i]   (one block per i, fixed order)
-__global__ void __launch_bounds__(RT) multidot_finalize_kernel(LanczosDev L, int m, int nb) {
+// coef[i] = sum_b partial[b*m + i]   (one block per i, fixed order);
+// on the first pass, the coefficient of v_j is alpha_j = <v_j, H v_j>.
+__global__ void __launch_bounds__(RT) multidot_finalize_kernel(LanczosDev L, int m, int nb, int alpha_j) {
   __shared__ double sh[32];
   if (stopped(L.state)) return;
   const int i = blockIdx.x;
   double acc = 0.0;
   for (int b = threadIdx.x; b < nb; b += RT) acc += L.partial[(int64_t)b * m + i];
   acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) L.coef[i] = acc;
+  if (threadIdx.x == 0) {
+    L.coef[i] = acc;
+    if (i == alpha_j) L.alpha[alpha_j] = acc;
+  }
 }
 
-// w -= sum_i coef[i] V_i
-__global__ void __launch_bounds__(RT) gs_update_kernel(LanczosDev L, int m) {
+// w -= sum_i coef[i] V_i; with norm != 0 also partial[b] = sum of the new w^2
+// over this block's grid-stride share (fixed order).
+__global__ void __launch_bounds__(RT) gs_update_kernel(LanczosDev L, int m, int norm) {
   __shared__ double c[512];
+  __shared__ double sh[32];
   if (stopped(L.state)) return;
   for (int i = threadIdx.x; i < m; i += RT) c[i] = L.coef[i];
   __syncthreads();
+  double nrm = 0.0;
   for (int64_t x = (int64_t)blockIdx.x * RT + threadIdx.x; x < L.n; x += (int64_t)gridDim.x * RT) {
     double w = L.w[x];
     for (int i = 0; i < m; ++i) w -= c[i] * L.V[(int64_t)i * L.n + x];
     L.w[x] = w;
+    nrm = fma(w, w, nrm);
+  }
+  if (norm) {
+    nrm = block_sum(nrm, sh);
+    if (threadIdx.x == 0) L.partial[blockIdx.x] = nrm;
   }
 }
 
-// beta_{j+1} already in L.beta[j+1]: decide stop, record k
-__global__ void lanczos_decide_kernel(LanczosDev L, int j, int last) {
+// beta_{j+1} = sqrt(sum of the norm partials); decide stop; record k
+__global__ void __launch_bounds__(RT) lanczos_beta_decide_kernel(LanczosDev L, int j, int nb, int last) {
+  __shared__ double sh[32];
   if (stopped(L.state)) return;
-  double amax = 0.0;
-  for (int i = 0; i <= j; ++i) amax = fmax(amax, fabs(L.alpha[i]));
-  L.state[0] = j + 1;
-  if (last || L.beta[j + 1] < 1e-14 * amax) L.state[1] = 1;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += RT) acc += L.partial[b];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    const double beta = sqrt(acc);
+    L.beta[j + 1] = beta;
+    double amax = 0.0;
+    for (int i = 0; i <= j; ++i) amax = fmax(amax, fabs(L.alpha[i]));
+    L.state[0] = j + 1;
+    if (last || beta < 1e-14 * amax) L.state[1] = 1;
+  }
 }
 
 __global__ void lanczos_normalize_kernel(LanczosDev L, int j) {
@@ -168,39 +199,68 @@ __device__ int sturm_count(const double* a, const double* b, int k, double x) {
   return cnt;
 }
 
-// Sturm bisection for the lowest eigenvalue of T, inverse iteration for y.
-// beta[j] couples rows j-1 and j (beta[0] unused).  Single thread: k is small.
-__global__ void tridiag_kernel(LanczosDev L) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Lowest eigenvalue of T by Sturm-sequence multisection: each of the RT
+// threads counts the eigenvalues below its own point of the current bracket,
+// and the bracket shrinks to the one sub-interval where the count first
+// reaches 1 (the same test as bisection, RT points per round), until it stops
+// shrinking.  Then inverse iteration (Thomas algorithm, 3 sweeps) for the
+// eigenvector y on thread 0.  beta[j] couples rows j-1 and j (beta[0] unused).
+__global__ void __launch_bounds__(RT) tridiag_kernel(LanczosDev L) {
+  __shared__ double s_lo, s_hi;
+  __shared__ int s_first;
   const int k = L.state[0];
   const double* a = L.alpha;
   const double* b = L.beta;
-  double lo = 0.0, hi = 0.0;
-  for (int j = 0; j < k; ++j) {
-    const double r = (j > 0 ? fabs(b[j]) : 0.0) + (j + 1 < k ? fabs(b[j + 1]) : 0.0);
-    if (j == 0 || a[j] - r < lo) lo = a[j] - r;
-    if (j == 0 || a[j] + r > hi) hi = a[j] + r;
+  if (threadIdx.x == 0) {
+    double lo = 0.0, hi = 0.0;
+    for (int j = 0; j < k; ++j) {
+      const double r = (j > 0 ? fabs(b[j]) : 0.0) + (j + 1 < k ? fabs(b[j + 1]) : 0.0);
+      if (j == 0 || a[j] - r < lo) lo = a[j] - r;
+      if (j == 0 || a[j] + r > hi) hi = a[j] + r;
+    }
+    s_lo = lo;
+    s_hi = hi;
   }
-  for (int it = 0; it < 2000; ++it) {
+  __syncthreads();
+  for (int round = 0; round < 64; ++round) {
+    const double lo = s_lo, hi = s_hi;
+    const double x = lo + (hi - lo) * (double)(threadIdx.x + 1) / (double)(RT + 1);
+    if (threadIdx.x == 0) s_first = RT;
+    __syncthreads();
+    if (x > lo && x < hi && sturm_count(a, b, k, x) >= 1) atomicMin(&s_first, (int)threadIdx.x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int f = s_first;
+      const double nlo = f == 0 ? lo : lo + (hi - lo) * (double)f / (double)(RT + 1);
+      const double nhi = f == RT ? hi : lo + (hi - lo) * (double)(f + 1) / (double)(RT + 1);
+      s_lo = nlo > lo ? nlo : lo;
+      s_hi = nhi < hi ? nhi : hi;
+    }
+    __syncthreads();
+    if (!(s_lo < s_hi) || (s_lo == lo && s_hi == hi)) break;
+  }
+  if (threadIdx.x != 0) return;
+  // finish with plain bisection on the (tiny) bracket, as the oracle does
+  double lo = s_lo, hi = s_hi;
+  for (int it = 0; it < 200; ++it) {
     const double mid = 0.5 * (lo + hi);
     if (mid <= lo || mid >= hi) break;
     if (sturm_count(a, b, k, mid) >= 1) hi = mid; else lo = mid;
   }
   const double lam = hi;
   *L.eval = lam;
-  // inverse iteration (Thomas algorithm), 3 sweeps, from the normalised ones vector
   double* y = L.y;
-  double* dd = L.scratch;          // k
-  double* rhs = L.scratch + L.nmax; // k
+  double* dd = L.scratch;
+  double* rhs = L.scratch + L.nmax;
   const double shift = lam - 1e-13 * fmax(1.0, fabs(lam));
   for (int j = 0; j < k; ++j) y[j] = 1.0 / sqrt((double)k);
   for (int sweep = 0; sweep < 3; ++sweep) {
     for (int j = 0; j < k; ++j) { dd[j] = a[j] - shift; rhs[j] = y[j]; }
     for (int j = 1; j < k; ++j) {
       const double piv = dd[j - 1] != 0.0 ? dd[j - 1] : 1e-300;
-      const double m = b[j] / piv;
-      dd[j] -= m * b[j];
-      rhs[j] -= m * rhs[j - 1];
+      const double mm = b[j] / piv;
+      dd[j] -= mm * b[j];
+      rhs[j] -= mm * rhs[j - 1];
     }
     y[k - 1] = rhs[k - 1] / (dd[k - 1] != 0.0 ? dd[k - 1] : 1e-300);
     for (int j = k - 2; j >= 0; --j) y[j] = (rhs[j] - b[j + 1] * y[j + 1]) / (dd[j] != 0.0 ? dd[j] : 1e-300);
@@ -277,30 +337,23 @@ cudaError_t tnx_launch_lanczos_set_input(double** slot_ptr, const LanczosDev& L,
   return cudaGetLastError();
 }
 
-// The operator has been applied: L.w = H v_j.  One Lanczos step.
+// The operator has been applied: L.w = H v_j.  One Lanczos step: classical
+// Gram-Schmidt against v_0..v_j done twice (the first pass also yields
+// alpha_j = <v_j, H v_j> and removes the three-term recurrence), the norm of
+// the result folded into the second update, then beta_{j+1}, the stopping
+// test and v_{j+1} = w / beta_{j+1}.
 cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, cudaStream_t st) {
   const int nb = grid_for(L.n);
-  const double* vj = L.V + (int64_t)j * L.n;
-  dot_partial_kernel<<<nb, RT, 0, st>>>(vj, L.w, L.n, L.partial, L.state);
-  tnx_note_launch(1);
-  finalize_kernel<<<1, RT, 0, st>>>(L.partial, nb, L.alpha + j, 0, L.state);
-  tnx_note_launch(1);
-  lanczos_axpy2_kernel<<<nb, RT, 0, st>>>(L, j);
-  tnx_note_launch(1);
   const int m = j + 1;
   for (int pass = 0; pass < 2; ++pass) {
-    multidot_kernel<<<L.nblocks, RT, 0, st>>>(L, m);
+    multidot_kernel<<<MD_BLOCKS, MD_T, 0, st>>>(L, m);
     tnx_note_launch(1);
-    multidot_finalize_kernel<<<m, RT, 0, st>>>(L, m, L.nblocks);
+    multidot_finalize_kernel<<<m, RT, 0, st>>>(L, m, MD_BLOCKS, pass == 0 ? j : -1);
     tnx_note_launch(1);
-    gs_update_kernel<<<nb, RT, 0, st>>>(L, m);
+    gs_update_kernel<<<nb, RT, 0, st>>>(L, m, pass == 1);
     tnx_note_launch(1);
   }
-  dot_partial_kernel<<<nb, RT, 0, st>>>(L.w, L.w, L.n, L.partial, L.state);
-  tnx_note_launch(1);
-  finalize_kernel<<<1, RT, 0, st>>>(L.partial, nb, L.beta + j + 1, 1, L.state);
-  tnx_note_launch(1);
-  lanczos_decide_kernel<<<1, 1, 0, st>>>(L, j, j == L.nmax - 1);
+  lanczos_beta_decide_kernel<<<1, RT, 0, st>>>(L, j, nb, j == L.nmax - 1);
   tnx_note_launch(1);
   lanczos_normalize_kernel<<<nb, RT, 0, st>>>(L, j);
   tnx_note_launch(1);
@@ -308,7 +361,7 @@ cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, cudaStream_t st)
 }
 
 cudaError_t tnx_launch_lanczos_finish(const LanczosDev& L, double* evec, cudaStream_t st) {
-  tridiag_kernel<<<1, 1, 0, st>>>(L);
+  tridiag_kernel<<<1, RT, 0, st>>>(L);
   tnx_note_launch(1);
   if (evec) {
     ritz_kernel<<<grid_for(L.n), RT, 0, st>>>(L, evec);

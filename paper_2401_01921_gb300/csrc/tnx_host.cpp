@@ -14,6 +14,7 @@
 #include <cstring>
 #include <map>
 #include <numeric>
+#include <cstdlib>
 
 // ------------------------------------------------------------------ context
 void* tnx_ctx::dalloc(size_t n) {
@@ -63,18 +64,42 @@ cudaEvent_t tnx_ctx::get_event() {
   return e;
 }
 
+// Inside a stream capture an event must be recorded as an external event node
+// to carry a timestamp when the graph runs.
+static void record_event(tnx_ctx* c, cudaEvent_t e, cudaStream_t st) {
+  if (c->capture_recs) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  else cudaEventRecord(e, st);
+}
+
 ProfScope::ProfScope(tnx_ctx* c_, cudaStream_t s_, int cls_, double work_) : c(c_), st(s_), cls(cls_), work(work_) {
   if (c->prof) {
-    a = c->get_event();
-    cudaEventRecord(a, st);
+    if (c->capture_recs) cudaEventCreate(&a);
+    else a = c->get_event();
+    record_event(c, a, st);
   }
 }
 
 ProfScope::~ProfScope() {
   if (!a) return;
-  cudaEvent_t b = c->get_event();
-  cudaEventRecord(b, st);
-  c->prof_pending.push_back(ProfRec{a, b, cls, work});
+  cudaEvent_t b;
+  if (c->capture_recs) cudaEventCreate(&b);
+  else b = c->get_event();
+  record_event(c, b, st);
+  if (c->capture_recs) c->capture_recs->push_back(ProfRec{a, b, cls, work});
+  else c->prof_pending.push_back(ProfRec{a, b, cls, work});
+}
+
+void prof_accumulate(tnx_ctx* c, const std::vector<ProfRec>& recs) {
+  for (auto& r : recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      c->prof_ms[r.cls] += ms;
+      c->prof_n[r.cls] += 1;
+      c->prof_work[r.cls] += r.work;
+    } else {
+      cudaGetLastError();   // leave no stale error behind for the caller
+    }
+  }
 }
 
 static void prof_drain(tnx_ctx* c) {
@@ -84,6 +109,8 @@ static void prof_drain(tnx_ctx* c) {
       c->prof_ms[r.cls] += ms;
       c->prof_n[r.cls] += 1;
       c->prof_work[r.cls] += r.work;
+    } else {
+      cudaGetLastError();
     }
     c->event_pool.push_back(r.a);
     c->event_pool.push_back(r.b);
@@ -128,6 +155,7 @@ tnx_status tnx_guard(tnx_ctx* ctx, const std::function<void()>& f) {
     f();
     return TNX_OK;
   } catch (const TnxError& e) {
+    if (e.code == TNX_ERR_CUDA) cudaGetLastError();
     return set_err(ctx, e.code, e.msg);
   } catch (const std::bad_alloc&) {
     return set_err(ctx, TNX_ERR_OOM, "host out of memory");
@@ -152,6 +180,10 @@ extern "C" tnx_status tnx_ctx_create(int device, void* stream, tnx_alloc_fn allo
   c->alloc = alloc;
   c->fre = fre;
   c->user = user;
+  {
+    const char* ng = getenv("TNX_NO_GRAPHS");
+    c->use_graphs = !(ng && *ng && *ng != '0');
+  }
   tnx_status s = tnx_guard(c, [&] {
     c->scratch = new DevBuf(c, 64 * 1024);
     c->d_status = (int32_t*)((char*)c->scratch->p + 63 * 1024);

@@ -40,6 +40,7 @@ struct tnx_ctx {
   DevBuf* scratch = nullptr;   // small device scratch (norm partials)
   void* pinned = nullptr;      // small pinned host buffer
   int32_t* d_status = nullptr; // device status word written by bounded waits (0 = ok)
+  bool use_graphs = true;      // capture applies / Lanczos solves in CUDA graphs (needs a non-default stream)
   // profiler (CUDA events around kernel classes)
   bool prof = false;
   std::vector<ProfRec> prof_pending;
@@ -47,6 +48,7 @@ struct tnx_ctx {
   double prof_ms[TNX_KC_COUNT] = {};
   int64_t prof_n[TNX_KC_COUNT] = {};
   double prof_work[TNX_KC_COUNT] = {};
+  std::vector<ProfRec>* capture_recs = nullptr;   // set while a graph is being captured
   cudaEvent_t get_event();
   void* dalloc(size_t n);
   void dfree(void* p, size_t n);
@@ -112,6 +114,8 @@ struct tnx_tensor {
 };
 
 tnx_status tnx_guard(tnx_ctx* ctx, const std::function<void()>& f);
+// add the timings of events recorded inside a graph (after the graph ran)
+void prof_accumulate(tnx_ctx* ctx, const std::vector<ProfRec>& recs);
 // after a stream sync: fail with TNX_ERR_TIMEOUT if a device wait ran out (and clear it)
 void check_device_status(tnx_ctx* ctx);
 void check_contractible(const BondD& a, const BondD& b, const std::string& label);

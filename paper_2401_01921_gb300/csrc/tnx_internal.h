@@ -20,7 +20,7 @@
 // the one contiguous in the destination.  src_slot < 0 writes zeros.
 struct CopyTask {
   int32_t src_slot, dst_slot;
-  int32_t rank, pad0;
+  int32_t rank, tleg;         // tleg >= 0: transposing task, source contiguous along leg tleg
   int64_t src_off, dst_off;
   int64_t nelem;
   int32_t shape[TNX_MAXR];
@@ -105,10 +105,16 @@ void tnx_note_launch(int n);
 // Kernel launchers (defined in the .cu files).  All enqueue on `st`.
 // ---------------------------------------------------------------------------
 cudaError_t tnx_launch_match(const MatchArgs& a, cudaStream_t st);
-cudaError_t tnx_launch_copy(const CopyTask* tasks, const int64_t* elem_start, int ntasks, int64_t total,
-                            double* const* slots, cudaStream_t st);
+#define TNX_COPY_CHUNK 1024    // elements per relayout CTA
+// chunks[i] = (task index, first element); a task of n elements has ceil(n / TNX_COPY_CHUNK) chunks;
+// a transposing task has one chunk per 32 x 32 tile: (task index, tile index)
+cudaError_t tnx_launch_copy(const CopyTask* tasks, const int2* chunks, int nchunks, double* const* slots,
+                            cudaStream_t st);
 cudaError_t tnx_launch_gemm_f64(const GemmGroup* groups, const GemmTile* tiles, int ntiles,
                                 double* const* slots, cudaStream_t st);
+// K <= 16 products, tiles of 128 rows x 64 columns (FP64)
+cudaError_t tnx_launch_gemm_skinny(const GemmGroup* groups, const GemmTile* tiles, int ntiles, double* const* slots,
+                                   cudaStream_t st);
 cudaError_t tnx_launch_gemm_f32(const GemmGroup* groups, const GemmTile* tiles, int ntiles,
                                 double* const* slots, cudaStream_t st);
 cudaError_t tnx_launch_row_exponents(const SliceJob* jobs, const int64_t* row_start, int njobs,

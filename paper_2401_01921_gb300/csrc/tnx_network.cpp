@@ -312,6 +312,14 @@ void finish_task(CopyTask& t, std::vector<int64_t> shape, std::vector<int64_t> s
     t.dstride[l] = d2[l];
     t.nelem *= sh2[l];
   }
+  // transposing task: the source's unit-stride leg is not the destination's
+  t.tleg = -1;
+  if (t.src_slot >= 0 && t.rank >= 2) {
+    int S = -1;
+    for (int l = 0; l < t.rank; ++l)
+      if (t.sstride[l] == 1 && t.shape[l] > 1) S = l;
+    if (S >= 0 && S != t.rank - 1 && t.shape[S] >= 8 && t.dstride[t.rank - 1] == 1) t.tleg = S;
+  }
 }
 
 // Every element a task touches must lie inside its slot's buffer: checked on
@@ -334,12 +342,24 @@ void validate_tasks(const Plan& p, const std::vector<CopyTask>& tasks) {
 TaskList upload_tasks(Plan& p, const std::vector<CopyTask>& tasks) {
   validate_tasks(p, tasks);
   TaskList tl;
-  std::vector<int64_t> start(tasks.size() + 1, 0);
-  for (size_t i = 0; i < tasks.size(); ++i) start[i + 1] = start[i] + tasks[i].nelem;
+  std::vector<int2> chunks;
+  tl.total = 0;
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    if (tasks[i].nelem > INT32_MAX) fail(TNX_ERR_UNSUPPORTED, "block above 2^31 elements");
+    if (tasks[i].tleg >= 0) {
+      const int64_t ncols = tasks[i].shape[tasks[i].tleg], nrows = tasks[i].nelem / ncols;
+      const int64_t ntiles = ((nrows + 31) / 32) * ((ncols + 31) / 32);
+      for (int64_t k = 0; k < ntiles; ++k) chunks.push_back(make_int2((int)i, (int)k));
+    } else {
+      for (int64_t e = 0; e < tasks[i].nelem; e += TNX_COPY_CHUNK) chunks.push_back(make_int2((int)i, (int)e));
+    }
+    tl.total += tasks[i].nelem;
+  }
+  if (chunks.size() > INT32_MAX) fail(TNX_ERR_UNSUPPORTED, "too many relayout chunks");
   tl.n = (int)tasks.size();
-  tl.total = start.back();
+  tl.nchunks = (int)chunks.size();
   tl.d = p.upload(tasks);
-  tl.start = p.upload(start);
+  tl.chunks = p.upload(chunks);
   return tl;
 }
 
@@ -557,7 +577,8 @@ void build_step(Plan& p, StepPlan& s) {
 
   // grouped GEMM
   std::vector<GemmGroup> gg(G);
-  std::vector<GemmTile> tiles;
+  std::vector<GemmTile> tiles, stiles;
+  s.skinny.assign(G, 0);
   for (int g = 0; g < G; ++g) {
     GemmGroup& x = gg[g];
     memset(&x, 0, sizeof(x));
@@ -572,12 +593,20 @@ void build_step(Plan& p, StepPlan& s) {
     x.N = (int32_t)s.mkn[3 * g + 2];
     x.lda = x.ldb = (int32_t)s.ldK[g];
     x.ldc = x.N;
-    for (int m0 = 0; m0 < x.M; m0 += 64)
-      for (int n0 = 0; n0 < x.N; n0 += 64) tiles.push_back(GemmTile{g, m0, n0, 0});
+    if (x.K <= 16) {
+      s.skinny[g] = 1;
+      for (int m0 = 0; m0 < x.M; m0 += 128)
+        for (int n0 = 0; n0 < x.N; n0 += 64) stiles.push_back(GemmTile{g, m0, n0, 0});
+    } else {
+      for (int m0 = 0; m0 < x.M; m0 += 64)
+        for (int n0 = 0; n0 < x.N; n0 += 64) tiles.push_back(GemmTile{g, m0, n0, 0});
+    }
   }
   s.dG = p.upload(gg);
   s.dT = p.upload(tiles);
   s.ntiles = (int)tiles.size();
+  s.dTs = p.upload(stiles);
+  s.nstiles_skinny = (int)stiles.size();
 
   // useful flops: matched block pairs share (group, K offset)
   std::map<std::pair<int64_t, int64_t>, std::pair<double, double>> acc;
@@ -593,7 +622,12 @@ void build_step(Plan& p, StepPlan& s) {
     acc[std::make_pair(s.bmap[3 * b], s.bmap[3 * b + 1])].second += (double)block_dim(B, b, s.fb);
   }
   s.flops = 0;
-  for (auto& kv : acc) s.flops += 2.0 * kv.second.first * kd[kv.first] * kv.second.second;
+  s.flops_skinny = 0;
+  for (auto& kv : acc) {
+    const double f = 2.0 * kv.second.first * kd[kv.first] * kv.second.second;
+    s.flops += f;
+    if (s.skinny[kv.first.first]) s.flops_skinny += f;
+  }
 
   // output view: the fused matrices C_g, one block per (row tuple, column tuple)
   OpView& C = s.C;
@@ -736,6 +770,8 @@ Plan* ensure_plan(tnx_network* net) {
   if (net->plan && net->plan->key == key) return net->plan.get();
   net->plan.reset();
   std::unique_ptr<Plan> p(new Plan());
+  static uint64_t serial = 0;
+  p->serial = ++serial;
   p->ctx = net->ctx;
   p->prec = net->prec;
   p->key = key;
@@ -764,6 +800,11 @@ Plan* ensure_plan(tnx_network* net) {
     p->out_slot = p->new_slot(nullptr, ne);
   }
   p->d_status = (int32_t*)p->alloc_zero(64);
+  if (p->nin > 64) fail(TNX_ERR_UNSUPPORTED, "at most 64 tensors per network");
+  std::function<uint64_t(int)> leaves = [&](int node) -> uint64_t {
+    const TreeNode& n = net->tree[node];
+    return n.leaf >= 0 ? (uint64_t)1 << n.leaf : leaves(n.l) | leaves(n.r);
+  };
   std::function<OpView(int)> walk = [&](int node) -> OpView {
     const TreeNode& n = net->tree[node];
     if (n.leaf >= 0) return input_view(net->ts[n.leaf], n.leaf);
@@ -771,6 +812,8 @@ Plan* ensure_plan(tnx_network* net) {
     OpView B = walk(n.r);
     p->steps.emplace_back();
     StepPlan& s = p->steps.back();
+    s.leavesA = leaves(n.l);
+    s.leavesB = leaves(n.r);
     s.A = std::move(A);
     s.B = std::move(B);
     build_step(*p, s);
@@ -794,33 +837,70 @@ void sync_slots(Plan& p) {
   p.h_slots_dev = p.h_slots;
 }
 
-void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st);
+void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB);
 
-void enqueue_plan(Plan& p, cudaStream_t st) {
+// Enqueue one apply.  `fixed`: network tensors whose data has not changed since
+// the previous apply of this plan (a Lanczos solve marks every tensor but the
+// vector).  Operands built only from fixed tensors keep their packed and sliced
+// forms from that previous apply, and a step whose two operands are both fixed
+// keeps its product: neither is recomputed.
+void enqueue_plan(Plan& p, cudaStream_t st, uint64_t fixed = 0) {
   tnx_ctx* c = p.ctx;
   for (auto& s : p.steps) {
+    const bool needA = (s.leavesA & ~fixed) != 0;
+    const bool needB = (s.leavesB & ~fixed) != 0;
+    if (!needA && !needB) continue;
     {
-      ProfScope ps(c, st, TNX_KC_RELAYOUT, 16.0 * (double)(s.copyA.total + s.copyB.total));
-      CUDA_CHECK(tnx_launch_copy(s.copyA.d, s.copyA.start, s.copyA.n, s.copyA.total, p.d_slots, st));
-      CUDA_CHECK(tnx_launch_copy(s.copyB.d, s.copyB.start, s.copyB.n, s.copyB.total, p.d_slots, st));
+      ProfScope ps(c, st, TNX_KC_RELAYOUT,
+                   16.0 * (double)((needA ? s.copyA.total : 0) + (needB ? s.copyB.total : 0)));
+      if (needA) CUDA_CHECK(tnx_launch_copy(s.copyA.d, s.copyA.chunks, s.copyA.nchunks, p.d_slots, st));
+      if (needB) CUDA_CHECK(tnx_launch_copy(s.copyB.d, s.copyB.chunks, s.copyB.nchunks, p.d_slots, st));
+    }
+    if (s.nstiles_skinny) {
+      ProfScope ps(c, st, TNX_KC_GEMM, s.flops_skinny);
+      CUDA_CHECK(tnx_launch_gemm_skinny(s.dG, s.dTs, s.nstiles_skinny, p.d_slots, st));
     }
     switch (p.prec) {
       case TNX_PREC_F64: {
-        ProfScope ps(c, st, TNX_KC_GEMM, s.flops);
+        ProfScope ps(c, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
         CUDA_CHECK(tnx_launch_gemm_f64(s.dG, s.dT, s.ntiles, p.d_slots, st));
         break;
       }
       case TNX_PREC_F32: {
-        ProfScope ps(c, st, TNX_KC_GEMM, s.flops);
+        ProfScope ps(c, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
         CUDA_CHECK(tnx_launch_gemm_f32(s.dG, s.dT, s.ntiles, p.d_slots, st));
         break;
       }
-      default: enqueue_split(p, s, st); break;
+      default: enqueue_split(p, s, st, needA, needB); break;
     }
   }
   ProfScope ps(c, st, TNX_KC_FINAL, 16.0 * (double)p.fin.total);
-  CUDA_CHECK(tnx_launch_copy(p.fin.d, p.fin.start, p.fin.n, p.fin.total, p.d_slots, st));
+  CUDA_CHECK(tnx_launch_copy(p.fin.d, p.fin.chunks, p.fin.nchunks, p.d_slots, st));
 }
+
+// Stream capture of `body` into g (graphs need a non-default stream).
+void capture_graph(tnx_ctx* c, cudaStream_t st, GraphRec& g, const std::function<void()>& body) {
+  g.prof = c->prof;
+  c->capture_recs = &g.recs;
+  CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  try {
+    body();
+  } catch (...) {
+    cudaGraph_t gr = nullptr;
+    cudaStreamEndCapture(st, &gr);
+    if (gr) cudaGraphDestroy(gr);
+    c->capture_recs = nullptr;
+    throw;
+  }
+  c->capture_recs = nullptr;
+  cudaGraph_t gr = nullptr;
+  CUDA_CHECK(cudaStreamEndCapture(st, &gr));
+  cudaError_t e = cudaGraphInstantiate(&g.exec, gr, 0);
+  cudaGraphDestroy(gr);
+  CUDA_CHECK(e);
+}
+
+bool graphs_enabled(tnx_ctx* c) { return c->stream != nullptr && c->use_graphs; }
 
 void bind_inputs(tnx_network* net, Plan& p) {
   for (int i = 0; i < p.nin; ++i) p.h_slots[i] = net->ts[i].t->data;
@@ -836,7 +916,9 @@ void check_out_bonds(const Plan& p, const tnx_tensor* out) {
 
 namespace {
 void build_split_parts(Plan& p, StepPlan& s) { tnx_build_split_parts(p, s); }
-void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st) { tnx_enqueue_split(p, s, st); }
+void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB) {
+  tnx_enqueue_split(p, s, st, needA, needB);
+}
 }  // namespace
 
 // ------------------------------------------------------------------ C-ABI
@@ -983,7 +1065,20 @@ extern "C" tnx_status tnx_network_launch_into(tnx_network* net, tnx_tensor* out)
     bind_inputs(net, *p);
     p->h_slots[p->out_slot] = out->data;
     sync_slots(*p);
-    enqueue_plan(*p, net->ctx->stream);
+    tnx_ctx* c = net->ctx;
+    if (graphs_enabled(c)) {
+      if (!p->apply_graph || p->apply_graph->prof != c->prof) {
+        p->apply_graph.reset(new GraphRec());
+        capture_graph(c, c->stream, *p->apply_graph, [&] { enqueue_plan(*p, c->stream); });
+      }
+      CUDA_CHECK(cudaGraphLaunch(p->apply_graph->exec, c->stream));
+      if (c->prof) {
+        CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        prof_accumulate(c, p->apply_graph->recs);
+      }
+    } else {
+      enqueue_plan(*p, c->stream);
+    }
   });
 }
 
@@ -1043,6 +1138,21 @@ extern "C" tnx_status tnx_network_step_tables(tnx_network* net, int step, int32_
 }
 
 // ---------------------------------------------------------------- Lanczos
+// Workspace and captured graph of a Lanczos solve, reused while the plan, the
+// step count and the bound buffers stay the same.
+struct LanczosCache {
+  uint64_t plan_serial = 0;
+  int nsteps = 0, slot = -1;
+  int64_t n = 0;
+  const double* v0 = nullptr;
+  double* evec = nullptr;
+  std::vector<std::unique_ptr<DevBuf>> bufs;
+  LanczosDev L;
+  std::unique_ptr<GraphRec> graph;
+};
+
+tnx_network::~tnx_network() = default;
+
 extern "C" tnx_status tnx_lanczos(tnx_network* net, const char* vec_slot, tnx_tensor* v0, int nsteps, double* eval,
                                   tnx_tensor* evec, int* nmatvec) {
   if (!net) return TNX_ERR_ARG;
@@ -1066,53 +1176,76 @@ extern "C" tnx_status tnx_lanczos(tnx_network* net, const char* vec_slot, tnx_te
     if (p->out_bonds != v0->bonds) fail(TNX_ERR_BOND_MISMATCH, "the operator's output bonds differ from the vector's");
     if (evec) check_out_bonds(*p, evec);
     const int64_t n = v0->nelem;
-    LanczosDev L;
-    memset(&L, 0, sizeof(L));
-    L.n = n;
-    L.nmax = nsteps;
-    L.nblocks = tnx_reduce_blocks(n);
-    std::vector<std::unique_ptr<DevBuf>> bufs;
-    auto dev = [&](size_t bytes) {
-      bufs.emplace_back(new DevBuf(ctx, std::max<size_t>(bytes, 256)));
-      CUDA_CHECK(cudaMemsetAsync(bufs.back()->p, 0, std::max<size_t>(bytes, 256), ctx->stream));
-      return bufs.back()->p;
-    };
-    L.V = (double*)dev((size_t)(nsteps + 1) * n * 8);
-    L.w = (double*)dev((size_t)n * 8);
-    L.alpha = (double*)dev((size_t)(nsteps + 1) * 8);
-    L.beta = (double*)dev((size_t)(nsteps + 2) * 8);
-    L.coef = (double*)dev((size_t)(nsteps + 2) * 8);
-    L.partial = (double*)dev((size_t)std::max<int64_t>(1216, (int64_t)L.nblocks * (nsteps + 2)) * 8);
-    L.y = (double*)dev((size_t)(nsteps + 1) * 8);
-    L.scratch = (double*)dev((size_t)(4 * (nsteps + 1)) * 8);
-    L.state = (int32_t*)dev(64);
-    L.eval = (double*)dev(64);
+    std::unique_ptr<LanczosCache>& lc = net->lanczos;
+    if (!lc || lc->plan_serial != p->serial || lc->nsteps != nsteps || lc->n != n || lc->slot != slot) {
+      lc.reset(new LanczosCache());
+      lc->plan_serial = p->serial;
+      lc->nsteps = nsteps;
+      lc->n = n;
+      lc->slot = slot;
+      LanczosDev& L = lc->L;
+      memset(&L, 0, sizeof(L));
+      L.n = n;
+      L.nmax = nsteps;
+      L.nblocks = tnx_reduce_blocks(n);
+      auto dev = [&](size_t bytes) {
+        lc->bufs.emplace_back(new DevBuf(ctx, std::max<size_t>(bytes, 256)));
+        CUDA_CHECK(cudaMemsetAsync(lc->bufs.back()->p, 0, std::max<size_t>(bytes, 256), ctx->stream));
+        return lc->bufs.back()->p;
+      };
+      L.V = (double*)dev((size_t)(nsteps + 1) * n * 8);
+      L.w = (double*)dev((size_t)n * 8);
+      L.alpha = (double*)dev((size_t)(nsteps + 1) * 8);
+      L.beta = (double*)dev((size_t)(nsteps + 2) * 8);
+      L.coef = (double*)dev((size_t)(nsteps + 2) * 8);
+      L.partial = (double*)dev((size_t)std::max<int64_t>(1216, (int64_t)152 * (nsteps + 2)) * 8);
+      L.y = (double*)dev((size_t)(nsteps + 1) * 8);
+      L.scratch = (double*)dev((size_t)(4 * (nsteps + 1)) * 8);
+      L.state = (int32_t*)dev(64);
+      L.eval = (double*)dev(64);
+    }
+    LanczosDev& L = lc->L;
     bind_inputs(net, *p);
     p->h_slots[p->out_slot] = L.w;
     sync_slots(*p);
     cudaStream_t st = ctx->stream;
-    {
-      ProfScope ps(ctx, st, TNX_KC_VECTOR, 24.0 * (double)n);
-      CUDA_CHECK(tnx_launch_lanczos_init(L, v0->data, st));
+    double* evp = evec ? evec->data : nullptr;
+    // apply 0 prepares every operand; later applies only those fed by the vector
+    const uint64_t fixed = ~((uint64_t)1 << slot);
+    auto body = [&] {
+      {
+        ProfScope ps(ctx, st, TNX_KC_VECTOR, 24.0 * (double)n);
+        CUDA_CHECK(tnx_launch_lanczos_init(L, v0->data, st));
+      }
+      for (int j = 0; j < nsteps; ++j) {
+        CUDA_CHECK(tnx_launch_lanczos_set_input(p->d_slots + slot, L, j, st));
+        enqueue_plan(*p, st, j == 0 ? 0 : fixed);
+        // bytes of one step: alpha dot (2n), axpy (3n+n), 2 x Gram-Schmidt over
+        // j+1 vectors (dots (j+1)n + n, update (j+1)n + 2n), norm (n), scale (2n)
+        ProfScope ps(ctx, st, TNX_KC_VECTOR, 8.0 * (double)n * (2 + 4 + 2 * (2.0 * (j + 1) + 3) + 1 + 2));
+        CUDA_CHECK(tnx_launch_lanczos_step(L, j, st));
+      }
+      ProfScope ps(ctx, st, TNX_KC_VECTOR, evp ? 8.0 * (double)n * (nsteps + 2) : 0.0);
+      CUDA_CHECK(tnx_launch_lanczos_finish(L, evp, st));
+    };
+    if (graphs_enabled(ctx)) {
+      if (!lc->graph || lc->v0 != v0->data || lc->evec != evp || lc->graph->prof != ctx->prof) {
+        lc->graph.reset(new GraphRec());
+        lc->v0 = v0->data;
+        lc->evec = evp;
+        capture_graph(ctx, st, *lc->graph, body);
+      }
+      CUDA_CHECK(cudaGraphLaunch(lc->graph->exec, st));
+    } else {
+      body();
     }
-    for (int j = 0; j < nsteps; ++j) {
-      CUDA_CHECK(tnx_launch_lanczos_set_input(p->d_slots + slot, L, j, st));
-      enqueue_plan(*p, st);
-      // bytes of one step: alpha dot (2n), axpy (3n+n), 2 x Gram-Schmidt over
-      // j+1 vectors (dots (j+1)n + n, update (j+1)n + 2n), norm (n), scale (2n)
-      ProfScope ps(ctx, st, TNX_KC_VECTOR, 8.0 * (double)n * (2 + 4 + 2 * (2.0 * (j + 1) + 3) + 1 + 2));
-      CUDA_CHECK(tnx_launch_lanczos_step(L, j, st));
-    }
-    {
-      ProfScope ps(ctx, st, TNX_KC_VECTOR, evec ? 8.0 * (double)n * (nsteps + 2) : 0.0);
-      CUDA_CHECK(tnx_launch_lanczos_finish(L, evec ? evec->data : nullptr, st));
-    }
-    // the device slot of the vector now points into L.V: restore the table
+    // the device slot of the vector now points into L.V: restore the table next time
     p->h_slots_dev.assign(p->h_slots.size(), nullptr);
     double* hp = (double*)ctx->pinned;
     CUDA_CHECK(cudaMemcpyAsync(hp, L.eval, 8, cudaMemcpyDeviceToHost, st));
     CUDA_CHECK(cudaMemcpyAsync(hp + 1, L.state, 8, cudaMemcpyDeviceToHost, st));
     CUDA_CHECK(cudaStreamSynchronize(st));
+    if (graphs_enabled(ctx) && ctx->prof) prof_accumulate(ctx, lc->graph->recs);
     check_device_status(ctx);
     *eval = hp[0];
     if (nmatvec) *nmatvec = ((int32_t*)(hp + 1))[0];

@@ -31,13 +31,15 @@ struct OpView {
 
 struct TaskList {
   CopyTask* d = nullptr;
-  int64_t* start = nullptr;
+  int2* chunks = nullptr;
+  int nchunks = 0;
   int n = 0;
   int64_t total = 0;
 };
 
 struct StepPlan {
   OpView A, B, C;
+  uint64_t leavesA = 0, leavesB = 0;   // network tensors feeding each operand (bit i = tensor i)
   std::vector<int> ka, kb, fa, fb;
   int G = 0;
   std::vector<int32_t> charges;
@@ -50,21 +52,45 @@ struct StepPlan {
   GemmGroup* dG = nullptr;
   GemmTile* dT = nullptr;
   int ntiles = 0;
+  GemmTile* dTs = nullptr;      // skinny (K <= 16) tiles, FP64 in every precision
+  int nstiles_skinny = 0;
+  std::vector<char> skinny;     // per group
+  double flops_skinny = 0;      // useful flops of the skinny groups
   // split precision
   int slotSA = -1, slotSB = -1, slotEA = -1, slotEB = -1;
-  SliceJob* dJobs = nullptr;
-  int njobs = 0;
-  int64_t* dRowStart = nullptr;
-  int64_t totRows = 0;
-  int64_t* dTileStart = nullptr;
-  int64_t totTiles = 0;
+  struct Jobs {             // one list of slicing jobs with its prefix arrays
+    SliceJob* d = nullptr;
+    int n = 0;
+    int64_t* row_start = nullptr;
+    int64_t rows = 0;
+    int64_t* warp_start = nullptr;
+    int64_t warps = 0;
+    int64_t elems = 0;
+  } jobsAll, jobsA, jobsB;
+  int64_t slice_elems = 0;      // packed elements that get sliced (split precision)
   SplitGroup* dSG = nullptr;
   GemmTile* dST = nullptr;
   int nstiles = 0;
 };
 
+// A captured CUDA graph plus the profiler events recorded inside it.
+struct GraphRec {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<ProfRec> recs;
+  bool prof = false;
+  ~GraphRec() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (auto& r : recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+  }
+};
+
 struct Plan {
   tnx_ctx* ctx = nullptr;
+  uint64_t serial = 0;            // unique per plan (cache key of dependent graphs)
+  std::unique_ptr<GraphRec> apply_graph;
   std::vector<std::unique_ptr<DevBuf>> bufs;
   std::vector<double*> h_slots, h_slots_dev;   // wanted / last uploaded
   double** d_slots = nullptr;
@@ -110,9 +136,11 @@ struct tnx_network {
   int prec = TNX_PREC_F64;
   std::string order_dims_key;      // dims for which the optimal tree was computed
   std::unique_ptr<Plan> plan;
+  std::unique_ptr<struct LanczosCache> lanczos;
+  ~tnx_network();
 };
 
 
 // split-precision planning and launch (tnx_split.cpp)
 void tnx_build_split_parts(Plan& p, StepPlan& s);
-void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st);
+void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB);

@@ -14,12 +14,20 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
   if (p.prec == TNX_PREC_TF32) fail(TNX_ERR_UNSUPPORTED, "TF32 products are not available in this build");
   const int G = s.G;
   const int n = p.nslice;
-  std::vector<SliceJob> jobs;
-  std::vector<int64_t> row_start(1, 0), warp_start(1, 0);
+  std::vector<SliceJob> jobs[2];
+  std::vector<int64_t> row_start[2], warp_start[2];
+  int64_t elems[2] = {0, 0};
   std::vector<int64_t> offSA(G), offSB(G), offEA(G), offEB(G);
   int64_t sa = 0, sb = 0, ea = 0, eb = 0;
   for (int g = 0; g < G; ++g) {
     const int64_t M = s.mkn[3 * g], K = s.mkn[3 * g + 1], N = s.mkn[3 * g + 2];
+    if (s.skinny[g]) {
+      offSA[g] = sa;
+      offSB[g] = sb;
+      offEA[g] = ea;
+      offEB[g] = eb;
+      continue;
+    }
     if (K > KMAX) fail(TNX_ERR_UNSUPPORTED, "split precision supports K <= 8192 per charge sector");
     const int64_t KT = (K + TK - 1) / TK, MT = (M + TM - 1) / TM, NT = (N + TN - 1) / TN;
     offSA[g] = sa;
@@ -37,6 +45,7 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
   s.slotEB = p.new_slot(p.alloc_zero((size_t)std::max<int64_t>(eb, 1) * 4), eb / 2);
   for (int side = 0; side < 2; ++side) {
     for (int g = 0; g < G; ++g) {
+      if (s.skinny[g]) continue;
       const int64_t M = s.mkn[3 * g], K = s.mkn[3 * g + 1], N = s.mkn[3 * g + 2];
       SliceJob j;
       memset(&j, 0, sizeof(j));
@@ -54,17 +63,38 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
       j.tile_rows = tr;
       const int64_t KT = (K + TK - 1) / TK;
       const int64_t padded = (rows + tr - 1) / tr * tr;
-      jobs.push_back(j);
-      row_start.push_back(row_start.back() + rows);
-      warp_start.push_back(warp_start.back() + padded / 8 * KT);
+      jobs[side].push_back(j);
+      elems[side] += rows * K;
+      row_start[side].push_back(rows);
+      warp_start[side].push_back(padded / 8 * KT);
     }
   }
-  s.njobs = (int)jobs.size();
-  s.totRows = row_start.back();
-  s.totTiles = warp_start.back();
-  s.dJobs = p.upload(jobs);
-  s.dRowStart = p.upload(row_start);
-  s.dTileStart = p.upload(warp_start);
+  auto make = [&](const std::vector<SliceJob>& js, const std::vector<int64_t>& rc, const std::vector<int64_t>& wc,
+                  int64_t el) {
+    StepPlan::Jobs J;
+    std::vector<int64_t> rs(1, 0), ws(1, 0);
+    for (size_t i = 0; i < js.size(); ++i) {
+      rs.push_back(rs.back() + rc[i]);
+      ws.push_back(ws.back() + wc[i]);
+    }
+    J.n = (int)js.size();
+    J.rows = rs.back();
+    J.warps = ws.back();
+    J.elems = el;
+    J.d = p.upload(js);
+    J.row_start = p.upload(rs);
+    J.warp_start = p.upload(ws);
+    return J;
+  };
+  std::vector<SliceJob> all = jobs[0];
+  all.insert(all.end(), jobs[1].begin(), jobs[1].end());
+  std::vector<int64_t> rall = row_start[0], wall = warp_start[0];
+  rall.insert(rall.end(), row_start[1].begin(), row_start[1].end());
+  wall.insert(wall.end(), warp_start[1].begin(), warp_start[1].end());
+  s.jobsA = make(jobs[0], row_start[0], warp_start[0], elems[0]);
+  s.jobsB = make(jobs[1], row_start[1], warp_start[1], elems[1]);
+  s.jobsAll = make(all, rall, wall, elems[0] + elems[1]);
+  s.slice_elems = elems[0] + elems[1];
   std::vector<SplitGroup> sg(G);
   std::vector<GemmTile> tiles;
   for (int g = 0; g < G; ++g) {
@@ -84,6 +114,7 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
     x.K = (int32_t)s.mkn[3 * g + 1];
     x.N = (int32_t)s.mkn[3 * g + 2];
     x.ldc = x.N;
+    if (s.skinny[g]) continue;
     for (int m0 = 0; m0 < x.M; m0 += TM)
       for (int n0 = 0; n0 < x.N; n0 += TN) tiles.push_back(GemmTile{g, m0, n0, 0});
   }
@@ -92,14 +123,14 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
   s.nstiles = (int)tiles.size();
 }
 
-void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st) {
+void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB) {
   const int f16 = p.prec == TNX_PREC_SPLIT_F16 ? 1 : 0;
-  const double elems = (double)(s.copyA.total + s.copyB.total);
-  {
-    ProfScope ps(p.ctx, st, TNX_KC_SLICE, elems * (8.0 + 8.0 + 2.0 * p.nslice));
-    CUDA_CHECK(tnx_launch_row_exponents(s.dJobs, s.dRowStart, s.njobs, s.totRows, p.d_slots, st));
-    CUDA_CHECK(tnx_launch_slices(s.dJobs, s.dTileStart, s.njobs, s.totTiles, p.nslice, p.beta, f16, p.d_slots, st));
+  const StepPlan::Jobs* J = (needA && needB) ? &s.jobsAll : needA ? &s.jobsA : needB ? &s.jobsB : nullptr;
+  if (J && J->n) {
+    ProfScope ps(p.ctx, st, TNX_KC_SLICE, (double)J->elems * (8.0 + 8.0 + 2.0 * p.nslice));
+    CUDA_CHECK(tnx_launch_row_exponents(J->d, J->row_start, J->n, J->rows, p.d_slots, st));
+    CUDA_CHECK(tnx_launch_slices(J->d, J->warp_start, J->n, J->warps, p.nslice, p.beta, f16, p.d_slots, st));
   }
-  ProfScope ps(p.ctx, st, TNX_KC_GEMM, s.flops);
+  ProfScope ps(p.ctx, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
   CUDA_CHECK(tnx_launch_gemm_split(s.dSG, s.dST, s.nstiles, p.nslice, p.beta, f16, p.d_slots, p.ctx->d_status, st));
 }

@@ -285,3 +285,24 @@ def test_tensor_without_blocks(ctx):
     net.put("B", Bt)
     out = net.launch([i, o])
     assert out.nblocks == 0
+
+
+def test_graph_and_profiler_leave_no_stale_cuda_error(ctx):
+    """Profiled, graph-captured launches and Lanczos solves: figures come back and torch keeps working."""
+    import torch
+    import paper_2401_01921_gb300 as tnx
+    wl = I.heisenberg_workload(40, 9)
+    net, T, B = lib_heff(ctx, wl, symmetric=True)
+    out = tnx.Tensor(ctx, B["psi"])
+    ctx.profile(True)
+    net.launch_into(out)
+    net.launch_into(out)
+    lam, k = tnx.lanczos(net, "psi", T["psi"], 8)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    assert prof["gemm"][1] > 0 and prof["gemm"][0] > 0
+    assert prof["vector"][1] > 0
+    x = torch.zeros(1024, device="cuda")
+    x.add_(1.0)
+    torch.cuda.synchronize()
+    assert float(x.sum()) == 1024.0
