@@ -223,6 +223,29 @@ tnx_status tnx_network_step_tables(tnx_network* net, int step, int32_t* charges,
 tnx_status tnx_lanczos(tnx_network* net, const char* vec_slot, tnx_tensor* v0, int nsteps,
                        double* eval, tnx_tensor* evec, int* nmatvec);
 
+/* ---------------------------------------------------------------- batches */
+
+/* A batch of nnet networks with the same number of pairwise contractions and
+ * the same precision (typically one blueprint over many independent
+ * instances: the batched H_eff*psi of many DMRG problems).  Every pairwise
+ * step of all instances runs as one relayout launch and one grouped-GEMM
+ * launch over all their charge sectors; a launch of the batch is one CUDA
+ * graph.  Each network must be fully put; its plan is built now and the batch
+ * keeps references (a network must outlive the batch; re-planning a network
+ * invalidates the batch: TNX_ERR_ARG at launch).  No counterpart in the paper,
+ * which contracts one network per call (Sec. 8). */
+typedef struct tnx_batch tnx_batch;
+tnx_status tnx_batch_create(tnx_ctx* ctx, int nnet, tnx_network* const* nets, tnx_batch** out);
+tnx_status tnx_batch_destroy(tnx_batch* b);
+/* Launch every network into outs[i] (bonds equal to network i's TOUT bonds). Asynchronous. */
+tnx_status tnx_batch_launch_into(tnx_batch* b, tnx_tensor* const* outs);
+/* Useful flops of one batch launch (sum over the instances). */
+tnx_status tnx_batch_flops(tnx_batch* b, double* flops);
+/* Times the split-GEMM launch schedules (one CTA per tile; persistent grids of
+ * 152, 304, 456 CTAs) on this batch (writing into outs) and keeps the fastest;
+ * *choice (may be NULL) gets the grid size (0 = one CTA per tile). */
+tnx_status tnx_batch_autotune(tnx_batch* b, tnx_tensor* const* outs, int* choice);
+
 /* ------------------------------------------------------------ diagnostics */
 
 /* Kernel classes timed by the profiler. */

@@ -87,6 +87,11 @@ _SIGS = {
     "tnx_network_step_sizes": (C.c_int, [_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _i64p, _i64p]),
     "tnx_network_step_tables": (C.c_int, [_p, C.c_int, _i32p, _i64p, _i64p, _i64p]),
     "tnx_lanczos": (C.c_int, [_p, C.c_char_p, _p, C.c_int, C.POINTER(C.c_double), _p, C.POINTER(C.c_int)]),
+    "tnx_batch_create": (C.c_int, [_p, C.c_int, C.POINTER(_p), C.POINTER(_p)]),
+    "tnx_batch_destroy": (C.c_int, [_p]),
+    "tnx_batch_launch_into": (C.c_int, [_p, C.POINTER(_p)]),
+    "tnx_batch_flops": (C.c_int, [_p, C.POINTER(C.c_double)]),
+    "tnx_batch_autotune": (C.c_int, [_p, C.POINTER(_p), C.POINTER(C.c_int)]),
     "tnx_profile_enable": (C.c_int, [_p, C.c_int]),
     "tnx_profile_read": (C.c_int, [_p, C.POINTER(C.c_double), _i64p, C.POINTER(C.c_double)]),
     "tnx_kernel_launches": (C.c_int, [_i64p]),
@@ -285,21 +290,30 @@ class Tensor:
         self.ctx.check(lib().tnx_tensor_norm(self.h, C.byref(x)))
         return x.value
 
+    def dense_coords(self):
+        """Dense (full-bond) coordinates of every stored element, in buffer order."""
+        qn, sh, off = self.blocks()
+        if self.rank == 0 or self.nelem == 0:
+            return []
+        sizes = np.prod(sh, axis=1)
+        blk = np.repeat(np.arange(self.nblocks), sizes)
+        local = np.arange(self.nelem, dtype=np.int64) - off[blk]
+        coords = [None] * self.rank
+        for l in range(self.rank - 1, -1, -1):
+            ext = sh[blk, l]
+            start = np.asarray(self.bonds[l].offsets())[qn[blk, l]]
+            coords[l] = start + local % ext
+            local = local // ext
+        return coords
+
     def fill(self, value_at):
         """Fill every block from value_at(list of dense-coordinate arrays) and upload."""
-        qn, sh, off = self.blocks()
-        out = np.zeros(self.nelem)
-        offs = [b.offsets() for b in self.bonds]
-        for b in range(self.nblocks):
-            grids = [np.arange(offs[l][qn[b, l]], offs[l][qn[b, l]] + sh[b, l]) for l in range(self.rank)]
-            if grids:
-                mesh = np.meshgrid(*grids, indexing="ij")
-                vals = value_at([m.reshape(-1) for m in mesh])
-            else:
-                vals = value_at([])
-            n = int(np.prod(sh[b])) if self.rank else 1
-            out[off[b]:off[b] + n] = np.asarray(vals, dtype=np.float64).reshape(-1)
-        self.upload(out)
+        if self.rank == 0:
+            self.upload(np.asarray(value_at([]), dtype=np.float64).reshape(1))
+            return self
+        if self.nelem == 0:
+            return self
+        self.upload(np.asarray(value_at(self.dense_coords()), dtype=np.float64).reshape(-1))
         return self
 
     def block_dict(self, flat=None):
@@ -389,6 +403,41 @@ class Network:
         try:
             if self.h:
                 lib().tnx_network_destroy(self.h)
+        except Exception:
+            pass
+
+
+class Batch:
+    """tnx_batch: many networks launched together (one launch per kernel class and step)."""
+
+    def __init__(self, ctx: Context, nets):
+        self.ctx = ctx
+        self.nets = list(nets)
+        arr = (C.c_void_p * len(self.nets))(*[n.h for n in self.nets])
+        h = C.c_void_p()
+        ctx.check(lib().tnx_batch_create(ctx.h, len(self.nets), arr, C.byref(h)))
+        self.h = h
+
+    def _outs(self, outs):
+        return (C.c_void_p * len(outs))(*[o.h for o in outs])
+
+    def launch_into(self, outs):
+        self.ctx.check(lib().tnx_batch_launch_into(self.h, self._outs(outs)))
+
+    def autotune(self, outs) -> int:
+        c = C.c_int()
+        self.ctx.check(lib().tnx_batch_autotune(self.h, self._outs(outs), C.byref(c)))
+        return c.value
+
+    def flops(self) -> float:
+        x = C.c_double()
+        self.ctx.check(lib().tnx_batch_flops(self.h, C.byref(x)))
+        return x.value
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().tnx_batch_destroy(self.h)
         except Exception:
             pass
 

@@ -26,7 +26,7 @@
 // row / column maximum and the dropped levels: about 2^-40 relative to
 // max|row| * max|col| * K.
 //
-// Kernel layout: one CTA per 128 x 64 output tile, 6 warps: warp 0 issues the
+// Kernel layout: 128 x 64 output tiles, 6 warps per CTA: warp 0 issues the
 // bulk copies (the TMA engine, cp.async.bulk) of pre-tiled slices into a
 // 3-stage shared-memory ring, warp 1 issues tcgen05.mma (one elected lane),
 // warps 2-5 drain tensor memory (tcgen05.ld) into the integer accumulators
@@ -286,23 +286,22 @@ struct SplitShared {
   int abort_flag;
 };
 
+// Persistent over tiles: CTA b takes tiles b, b + gridDim.x, ... of the list
+// (the host orders it longest-K first).  Tensor memory and the barriers are set
+// up once per CTA; the stage ring and the chunk hand-off between the MMA warp
+// and the epilogue warps continue across tiles, so the producer streams the
+// next tile's slices while the epilogue drains the current one.
 template <int NS>
 __global__ void __launch_bounds__(192, 1) split_gemm_kernel(const SplitGroup* __restrict__ groups,
-                                                             const GemmTile* __restrict__ tiles, int beta, int f16,
-                                                             double* const* __restrict__ slots, int32_t* status) {
+                                                             const GemmTile* __restrict__ tiles, int ntiles, int beta,
+                                                             int f16, double* const* __restrict__ slots,
+                                                             int32_t* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // stage ring: STAGES x (NS A tiles + NS B tiles), 1024-byte aligned
   unsigned char* ring = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int STAGE_BYTES = NS * (ATILE + BTILE);
   SplitShared* sh = (SplitShared*)(ring + STAGES * STAGE_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  const GemmTile tl = tiles[blockIdx.x];
-  const SplitGroup g = groups[tl.group];
-  const int KT = (g.K + TK - 1) / TK;
-  const int KTPC = KC / TK;                      // K tiles per exact chunk
-  const int nchunks = (KT + KTPC - 1) / KTPC;
-  const int mt = tl.m0 / TM, nt = tl.n0 / TN;
+  constexpr int KTPC = KC / TK;   // K tiles per exact chunk
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -329,64 +328,79 @@ __global__ void __launch_bounds__(192, 1) split_gemm_kernel(const SplitGroup* __
   if (warp == 0) {
     // ---------------- producer: bulk copies of pre-tiled slices
     if (lane == 0) {
-      const char* Ab = (const char*)slots[g.a_slot] + g.a_off_bytes;
-      const char* Bb = (const char*)slots[g.b_slot] + g.b_off_bytes;
-      int issued = 0;
-      for (int kt = 0; kt < KT && !*abort_flag; ++kt) {
-        const int s = kt % STAGES;
-        const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
-        if (kt >= STAGES && !mbar_wait(&sh->empty[s], ph ^ 1u, status, 11, abort_flag)) break;
-        unsigned char* sa = ring + s * STAGE_BYTES;
-        unsigned char* sb = sa + NS * ATILE;
-        mbar_expect_tx(&sh->full[s], NS * (ATILE + BTILE));
-        bulk_g2s(sa, Ab + ((int64_t)mt * KT + kt) * NS * ATILE, NS * ATILE, &sh->full[s]);
-        bulk_g2s(sb, Bb + ((int64_t)nt * KT + kt) * NS * BTILE, NS * BTILE, &sh->full[s]);
-        issued = kt + 1;
+      int g = 0;   // global K-tile counter of this CTA
+      for (int ti = blockIdx.x; ti < ntiles && !*abort_flag; ti += gridDim.x) {
+        const GemmTile tl = tiles[ti];
+        const SplitGroup gr = groups[tl.group];
+        const int KT = (gr.K + TK - 1) / TK;
+        const char* Ab = (const char*)slots[gr.a_slot] + gr.a_off_bytes + ((int64_t)(tl.m0 / TM) * KT) * NS * ATILE;
+        const char* Bb = (const char*)slots[gr.b_slot] + gr.b_off_bytes + ((int64_t)(tl.n0 / TN) * KT) * NS * BTILE;
+        for (int kt = 0; kt < KT; ++kt, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          if (g >= STAGES && !mbar_wait(&sh->empty[s], ph ^ 1u, status, 11, abort_flag)) break;
+          unsigned char* sa = ring + s * STAGE_BYTES;
+          mbar_expect_tx(&sh->full[s], NS * (ATILE + BTILE));
+          bulk_g2s(sa, Ab + (int64_t)kt * NS * ATILE, NS * ATILE, &sh->full[s]);
+          bulk_g2s(sa + NS * ATILE, Bb + (int64_t)kt * NS * BTILE, NS * BTILE, &sh->full[s]);
+        }
       }
-      // never leave copies in flight: wait (bounded) for every issued stage to land
-      for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt) {
-        const int s = kt % STAGES;
+      // never leave copies in flight: wait (bounded) for the last issued stages to land
+      for (int q = (g > STAGES ? g - STAGES : 0); q < g; ++q) {
         const long long t0 = clock64();
-        while (!mbar_try(&sh->full[s], (uint32_t)(kt / STAGES) & 1u) && clock64() - t0 < WAIT_LIMIT) {
+        while (!mbar_try(&sh->full[q % STAGES], (uint32_t)(q / STAGES) & 1u) && clock64() - t0 < WAIT_LIMIT) {
         }
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      for (int kt = 0; kt < KT; ++kt) {
-        const int s = kt % STAGES;
-        const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
-        const int chunk = kt / KTPC;
-        const bool first_in_chunk = (kt % KTPC) == 0;
-        const bool last_in_chunk = ((kt + 1) % KTPC) == 0 || kt == KT - 1;
-        if (first_in_chunk && chunk > 0 && !mbar_wait(&sh->accempty, (uint32_t)(chunk - 1) & 1u, status, 12, abort_flag))
-          break;
-        if (!mbar_wait(&sh->full[s], ph, status, 13, abort_flag)) break;
-        tc_fence_after();
-        const uint32_t sa = smem_u32(ring + s * STAGE_BYTES);
-        const uint32_t sb = sa + NS * ATILE;
-        // A slice i meets the B slices j = 0 .. NS-1-i stacked along N (they are
-        // consecutive 64-row tiles, so the stack is one taller K-major operand);
-        // its output columns are the accumulators of levels i .. NS-1, also
-        // consecutive: one MMA (N <= 256, else two) per A slice and K step.
+      int g = 0, chunk = 0;
+      bool ok = true;
+      for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+        const SplitGroup gr = groups[tiles[ti].group];
+        const int KT = (gr.K + TK - 1) / TK;
+        for (int kt = 0; kt < KT; ++kt, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          const bool first_in_chunk = (kt % KTPC) == 0;
+          const bool last_in_chunk = ((kt + 1) % KTPC) == 0 || kt == KT - 1;
+          if (first_in_chunk && chunk > 0 && !mbar_wait(&sh->accempty, (uint32_t)(chunk - 1) & 1u, status, 12, abort_flag)) {
+            ok = false;
+            break;
+          }
+          if (!mbar_wait(&sh->full[s], ph, status, 13, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(ring + s * STAGE_BYTES);
+          const uint32_t sb = sa + NS * ATILE;
+          // A slice i meets the B slices j = 0 .. NS-1-i stacked along N (they are
+          // consecutive 64-row tiles, so the stack is one taller K-major operand);
+          // its output columns are the accumulators of levels i .. NS-1, also
+          // consecutive: one MMA (N <= 256, else two) per A slice and K step.
 #pragma unroll
-        for (int ks = 0; ks < TK / 16; ++ks) {
+          for (int ks = 0; ks < TK / 16; ++ks) {
 #pragma unroll
-          for (int i = 0; i < NS; ++i) {
-            const uint64_t ad = smem_desc(sa + i * ATILE + ks * 256);
-            const uint32_t acc = (first_in_chunk && ks == 0 && i == 0) ? 0u : 1u;
-            const int nj = NS - i;
+            for (int i = 0; i < NS; ++i) {
+              const uint64_t ad = smem_desc(sa + i * ATILE + ks * 256);
+              const uint32_t acc = (first_in_chunk && ks == 0 && i == 0) ? 0u : 1u;
+              const int nj = NS - i;
 #pragma unroll
-            for (int j0 = 0; j0 < nj; j0 += 4) {
-              const int cnt = (nj - j0) < 4 ? (nj - j0) : 4;
-              const uint64_t bd = smem_desc(sb + j0 * BTILE + ks * 256);
-              mma_f16(tmem + (uint32_t)((i + j0) * TN), ad, bd, instr_desc(f16, cnt * TN), acc);
+              for (int j0 = 0; j0 < nj; j0 += 4) {
+                const int cnt = (nj - j0) < 4 ? (nj - j0) : 4;
+                const uint64_t bd = smem_desc(sb + j0 * BTILE + ks * 256);
+                mma_f16(tmem + (uint32_t)((i + j0) * TN), ad, bd, instr_desc(f16, cnt * TN), acc);
+              }
             }
           }
+          mma_commit(&sh->empty[s]);
+          if (last_in_chunk) {
+            mma_commit(&sh->accfull);
+            ++chunk;
+          }
         }
-        mma_commit(&sh->empty[s]);
-        if (last_in_chunk) mma_commit(&sh->accfull);
       }
       // all MMAs issued by this thread have completed before tensor memory is freed
       mma_commit(&sh->done);
@@ -397,39 +411,49 @@ __global__ void __launch_bounds__(192, 1) split_gemm_kernel(const SplitGroup* __
   } else {
     // ---------------- epilogue: warps 2..5, TMEM lanes 32*(warp%4) ..
     const int sub = warp & 3;
-    const int row = tl.m0 + sub * 32 + lane;
-    long long acc[TN];
-#pragma unroll
-    for (int c = 0; c < TN; ++c) acc[c] = 0;
+    int chunk = 0;
     bool ok = true;
-    for (int ch = 0; ch < nchunks; ++ch) {
-      if (!mbar_wait(&sh->accfull, (uint32_t)ch & 1u, status, 14, abort_flag)) { ok = false; break; }
-      tc_fence_after();
+    for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+      const GemmTile tl = tiles[ti];
+      const SplitGroup gr = groups[tl.group];
+      const int KT = (gr.K + TK - 1) / TK;
+      const int nchunks = (KT + KTPC - 1) / KTPC;
+      const int row = tl.m0 + sub * 32 + lane;
+      long long acc[TN];
 #pragma unroll
-      for (int cg = 0; cg < TN / 16; ++cg) {
-#pragma unroll
-        for (int t = 0; t < NS; ++t) {
-          uint32_t v[16];
-          tmem_ld16(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(t * TN + cg * 16), v);
-          tmem_wait_ld();
-          const long long scale_t = 1LL << (beta * (NS - 1 - t));
-#pragma unroll
-          for (int c = 0; c < 16; ++c) acc[cg * 16 + c] += (long long)__float2int_rn(__uint_as_float(v[c])) * scale_t;
+      for (int c = 0; c < TN; ++c) acc[c] = 0;
+      for (int ch = 0; ch < nchunks; ++ch, ++chunk) {
+        if (!mbar_wait(&sh->accfull, (uint32_t)chunk & 1u, status, 14, abort_flag)) {
+          ok = false;
+          break;
         }
-      }
-      tc_fence_before();
-      if (lane == 0) mbar_arrive(&sh->accempty);
-    }
-    if (ok && row < g.M) {
-      const int eb_r = ((const int32_t*)slots[g.ea_slot])[g.ea_off + row];
-      double* crow = slots[g.c_slot] + g.c_off + (int64_t)row * g.ldc;
-      const int32_t* eb_c = (const int32_t*)slots[g.eb_slot] + g.eb_off;
+        tc_fence_after();
 #pragma unroll
-      for (int c = 0; c < TN; ++c) {
-        const int col = tl.n0 + c;
-        if (col < g.N) {
-          const int e = eb_r + eb_c[col] - 2046 + 2 - beta * (NS + 1);
-          crow[col] = i64_scaled_to_double(acc[c], e);
+        for (int cg = 0; cg < TN / 16; ++cg) {
+#pragma unroll
+          for (int t = 0; t < NS; ++t) {
+            uint32_t v[16];
+            tmem_ld16(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(t * TN + cg * 16), v);
+            tmem_wait_ld();
+            const long long scale_t = 1LL << (beta * (NS - 1 - t));
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[cg * 16 + c] += (long long)__float2int_rn(__uint_as_float(v[c])) * scale_t;
+          }
+        }
+        tc_fence_before();
+        if (lane == 0) mbar_arrive(&sh->accempty);
+      }
+      if (ok && row < gr.M) {
+        const int eb_r = ((const int32_t*)slots[gr.ea_slot])[gr.ea_off + row];
+        double* crow = slots[gr.c_slot] + gr.c_off + (int64_t)row * gr.ldc;
+        const int32_t* eb_c = (const int32_t*)slots[gr.eb_slot] + gr.eb_off;
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+          const int col = tl.n0 + c;
+          if (col < gr.N) {
+            const int e = eb_r + eb_c[col] - 2046 + 2 - beta * (NS + 1);
+            crow[col] = i64_scaled_to_double(acc[c], e);
+          }
         }
       }
     }
@@ -468,8 +492,9 @@ size_t tnx_split_smem_bytes(int nslice) {
 }
 
 cudaError_t tnx_launch_gemm_split(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int nslice, int beta,
-                                  int f16, double* const* slots, int32_t* status, cudaStream_t st) {
+                                  int f16, double* const* slots, int32_t* status, cudaStream_t st, int grid) {
   if (ntiles <= 0) return cudaSuccess;
+  if (grid <= 0 || grid > ntiles) grid = ntiles;
   if (nslice != MAXN || beta != 7) return cudaErrorInvalidValue;
   const size_t smem = tnx_split_smem_bytes(nslice);
   static bool attr = false;
@@ -478,7 +503,7 @@ cudaError_t tnx_launch_gemm_split(const SplitGroup* groups, const GemmTile* tile
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  split_gemm_kernel<MAXN><<<ntiles, 192, smem, st>>>(groups, tiles, beta, f16, slots, status);
+  split_gemm_kernel<MAXN><<<grid, 192, smem, st>>>(groups, tiles, ntiles, beta, f16, slots, status);
   tnx_note_launch(1);
   return cudaGetLastError();
 }

@@ -1,0 +1,326 @@
+// Batched contraction: many networks with the same blueprint and contraction
+// tree run as one sequence of launches (one relayout launch and one grouped
+// GEMM launch per pairwise step for all instances together), captured in one
+// CUDA graph.  The split GEMM's launch schedule (one CTA per tile, or a
+// persistent grid of 1x / 2x / 3x the SM count over a longest-K-first tile
+// list) is picked by timing each candidate on the batch itself.
+//
+// Each instance keeps its own plan (tables, packed operands, intermediates);
+// the batch only merges the task tables, shifting every slot index by the
+// instance's offset in the merged slot table.
+#include <algorithm>
+#include <cstring>
+
+#include "tnx_plan.h"
+
+Plan* tnx_ensure_plan(tnx_network* net);
+void tnx_bind_inputs(tnx_network* net, Plan& p);
+void tnx_check_out_bonds(const Plan& p, const tnx_tensor* out);
+void tnx_capture_graph(tnx_ctx* c, cudaStream_t st, GraphRec& g, const std::function<void()>& body);
+
+struct BStep {
+  TaskList A, B;
+  GemmGroup* dG = nullptr;
+  GemmTile *dT = nullptr, *dTs = nullptr;
+  int nt = 0, nts = 0;
+  StepPlan::Jobs jobs;
+  SplitGroup* dSG = nullptr;
+  GemmTile* dST = nullptr;
+  int nst = 0;
+  double flops = 0, flops_skinny = 0;
+};
+
+struct tnx_batch {
+  tnx_ctx* ctx = nullptr;
+  std::vector<tnx_network*> nets;
+  std::vector<uint64_t> serials;
+  std::vector<Plan*> plans;
+  std::vector<int> base;      // slot offset per instance
+  int prec = TNX_PREC_F64, nslice = 6, beta = 7;
+  std::vector<std::unique_ptr<DevBuf>> bufs;
+  std::vector<double*> h_slots;
+  double** d_slots = nullptr;
+  std::vector<BStep> steps;
+  TaskList fin;
+  int split_grid = 0;
+  std::unique_ptr<GraphRec> graph;
+
+  template <class T>
+  T* upload(const std::vector<T>& v) {
+    size_t n = std::max<size_t>(v.size(), 1) * sizeof(T);
+    bufs.emplace_back(new DevBuf(ctx, n));
+    if (!v.empty())
+      CUDA_CHECK(cudaMemcpyAsync(bufs.back()->p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    return (T*)bufs.back()->p;
+  }
+};
+
+namespace {
+
+int shift_slot(int s, int b) { return s < 0 ? s : s + b; }
+
+TaskList merge_tasks(tnx_batch& B, const std::vector<const TaskList*>& parts) {
+  std::vector<CopyTask> tasks;
+  std::vector<int2> chunks;
+  TaskList out;
+  for (size_t i = 0; i < parts.size(); ++i) {
+    const int off = (int)tasks.size();
+    for (CopyTask t : parts[i]->h) {
+      t.src_slot = shift_slot(t.src_slot, B.base[i]);
+      t.dst_slot = shift_slot(t.dst_slot, B.base[i]);
+      tasks.push_back(t);
+    }
+    for (int2 c : parts[i]->hchunks) chunks.push_back(make_int2(c.x + off, c.y));
+    out.total += parts[i]->total;
+  }
+  if (chunks.size() > INT32_MAX) fail(TNX_ERR_UNSUPPORTED, "too many relayout chunks in the batch");
+  out.n = (int)tasks.size();
+  out.nchunks = (int)chunks.size();
+  out.d = B.upload(tasks);
+  out.chunks = B.upload(chunks);
+  return out;
+}
+
+void enqueue_batch(tnx_batch& B, cudaStream_t st) {
+  tnx_ctx* c = B.ctx;
+  const int f16 = B.prec == TNX_PREC_SPLIT_F16 ? 1 : 0;
+  for (auto& s : B.steps) {
+    {
+      ProfScope ps(c, st, TNX_KC_RELAYOUT, 16.0 * (double)(s.A.total + s.B.total));
+      CUDA_CHECK(tnx_launch_copy(s.A.d, s.A.chunks, s.A.nchunks, B.d_slots, st));
+      CUDA_CHECK(tnx_launch_copy(s.B.d, s.B.chunks, s.B.nchunks, B.d_slots, st));
+    }
+    if (s.nts) {
+      ProfScope ps(c, st, TNX_KC_GEMM, s.flops_skinny);
+      CUDA_CHECK(tnx_launch_gemm_skinny(s.dG, s.dTs, s.nts, B.d_slots, st));
+    }
+    if (B.prec == TNX_PREC_F64 || B.prec == TNX_PREC_F32) {
+      ProfScope ps(c, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
+      if (B.prec == TNX_PREC_F64) CUDA_CHECK(tnx_launch_gemm_f64(s.dG, s.dT, s.nt, B.d_slots, st));
+      else CUDA_CHECK(tnx_launch_gemm_f32(s.dG, s.dT, s.nt, B.d_slots, st));
+    } else {
+      if (s.jobs.n) {
+        ProfScope ps(c, st, TNX_KC_SLICE, (double)s.jobs.elems * (16.0 + 2.0 * B.nslice));
+        CUDA_CHECK(tnx_launch_row_exponents(s.jobs.d, s.jobs.row_start, s.jobs.n, s.jobs.rows, B.d_slots, st));
+        CUDA_CHECK(tnx_launch_slices(s.jobs.d, s.jobs.warp_start, s.jobs.n, s.jobs.warps, B.nslice, B.beta, f16,
+                                     B.d_slots, st));
+      }
+      ProfScope ps(c, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
+      CUDA_CHECK(tnx_launch_gemm_split(s.dSG, s.dST, s.nst, B.nslice, B.beta, f16, B.d_slots, c->d_status, st,
+                                       B.split_grid));
+    }
+  }
+  ProfScope ps(c, st, TNX_KC_FINAL, 16.0 * (double)B.fin.total);
+  CUDA_CHECK(tnx_launch_copy(B.fin.d, B.fin.chunks, B.fin.nchunks, B.d_slots, st));
+}
+
+void check_fresh(const tnx_batch& B) {
+  for (size_t i = 0; i < B.nets.size(); ++i)
+    if (!B.nets[i]->plan || B.nets[i]->plan->serial != B.serials[i])
+      fail(TNX_ERR_ARG, "a network of the batch was re-planned since the batch was created; create a new batch");
+}
+
+void bind(tnx_batch& B, tnx_tensor* const* outs) {
+  for (size_t i = 0; i < B.nets.size(); ++i) {
+    Plan& p = *B.plans[i];
+    tnx_check_out_bonds(p, outs[i]);
+    tnx_bind_inputs(B.nets[i], p);
+    p.h_slots[p.out_slot] = outs[i]->data;
+    for (size_t k = 0; k < p.h_slots.size(); ++k) B.h_slots[B.base[i] + k] = p.h_slots[k];
+  }
+  CUDA_CHECK(cudaMemcpyAsync(B.d_slots, B.h_slots.data(), B.h_slots.size() * sizeof(double*), cudaMemcpyHostToDevice,
+                             B.ctx->stream));
+}
+
+}  // namespace
+
+extern "C" tnx_status tnx_batch_create(tnx_ctx* ctx, int n, tnx_network* const* nets, tnx_batch** out) {
+  return tnx_guard(ctx, [&] {
+    if (!ctx || n < 1 || !nets || !out) fail(TNX_ERR_ARG, "bad batch arguments");
+    std::unique_ptr<tnx_batch> B(new tnx_batch());
+    B->ctx = ctx;
+    int slots = 0;
+    for (int i = 0; i < n; ++i) {
+      if (!nets[i] || nets[i]->ctx != ctx) fail(TNX_ERR_ARG, "every network must belong to the context");
+      for (int j = 0; j < i; ++j)
+        if (nets[j] == nets[i]) fail(TNX_ERR_ARG, "a network appears twice in the batch");
+      Plan* p = tnx_ensure_plan(nets[i]);
+      if (i > 0 && (p->steps.size() != B->plans[0]->steps.size() || p->prec != B->prec))
+        fail(TNX_ERR_ARG, "batched networks need the same number of contractions and the same precision");
+      B->nets.push_back(nets[i]);
+      B->plans.push_back(p);
+      B->serials.push_back(p->serial);
+      B->prec = p->prec;
+      B->nslice = p->nslice;
+      B->beta = p->beta;
+      B->base.push_back(slots);
+      slots += (int)p->h_slots.size();
+    }
+    B->h_slots.assign(slots, nullptr);
+    B->bufs.emplace_back(new DevBuf(ctx, (size_t)slots * sizeof(double*)));
+    B->d_slots = (double**)B->bufs.back()->p;
+    const size_t nst = B->plans[0]->steps.size();
+    B->steps.resize(nst);
+    const bool split = B->prec == TNX_PREC_SPLIT_BF16 || B->prec == TNX_PREC_SPLIT_F16;
+    for (size_t s = 0; s < nst; ++s) {
+      BStep& bs = B->steps[s];
+      std::vector<const TaskList*> pa, pb;
+      for (auto* p : B->plans) {
+        pa.push_back(&p->steps[s].copyA);
+        pb.push_back(&p->steps[s].copyB);
+      }
+      bs.A = merge_tasks(*B, pa);
+      bs.B = merge_tasks(*B, pb);
+      std::vector<GemmGroup> gg;
+      std::vector<GemmTile> tt, ts;
+      std::vector<SliceJob> jobs;
+      std::vector<int64_t> rs(1, 0), ws(1, 0);
+      std::vector<SplitGroup> sg;
+      std::vector<GemmTile> st;
+      for (size_t i = 0; i < B->plans.size(); ++i) {
+        const StepPlan& sp = B->plans[i]->steps[s];
+        const int b = B->base[i];
+        const int goff = (int)gg.size();
+        for (GemmGroup g : sp.hG) {
+          g.a_slot = shift_slot(g.a_slot, b);
+          g.b_slot = shift_slot(g.b_slot, b);
+          g.c_slot = shift_slot(g.c_slot, b);
+          gg.push_back(g);
+        }
+        for (GemmTile t : sp.hT) { t.group += goff; tt.push_back(t); }
+        for (GemmTile t : sp.hTs) { t.group += goff; ts.push_back(t); }
+        bs.flops += sp.flops;
+        bs.flops_skinny += sp.flops_skinny;
+        if (split) {
+          const int soff = (int)sg.size();
+          for (size_t q = 0; q < sp.jobsAll.h.size(); ++q) {
+            SliceJob j = sp.jobsAll.h[q];
+            j.src_slot = shift_slot(j.src_slot, b);
+            j.dst_slot = shift_slot(j.dst_slot, b);
+            j.exp_slot = shift_slot(j.exp_slot, b);
+            jobs.push_back(j);
+            rs.push_back(rs.back() + sp.jobsAll.hrows[q]);
+            ws.push_back(ws.back() + sp.jobsAll.hwarps[q]);
+          }
+          bs.jobs.elems += sp.jobsAll.elems;
+          for (SplitGroup g : sp.hSG) {
+            g.a_slot = shift_slot(g.a_slot, b);
+            g.b_slot = shift_slot(g.b_slot, b);
+            g.c_slot = shift_slot(g.c_slot, b);
+            g.ea_slot = shift_slot(g.ea_slot, b);
+            g.eb_slot = shift_slot(g.eb_slot, b);
+            sg.push_back(g);
+          }
+          for (GemmTile t : sp.hST) { t.group += soff; st.push_back(t); }
+        }
+      }
+      bs.dG = B->upload(gg);
+      bs.dT = B->upload(tt);
+      bs.nt = (int)tt.size();
+      bs.dTs = B->upload(ts);
+      bs.nts = (int)ts.size();
+      if (split) {
+        // longest K first, so a persistent grid ends with short tiles
+        std::stable_sort(st.begin(), st.end(), [&](const GemmTile& x, const GemmTile& y) {
+          return sg[x.group].K > sg[y.group].K;
+        });
+        bs.jobs.n = (int)jobs.size();
+        bs.jobs.rows = rs.back();
+        bs.jobs.warps = ws.back();
+        bs.jobs.d = B->upload(jobs);
+        bs.jobs.row_start = B->upload(rs);
+        bs.jobs.warp_start = B->upload(ws);
+        bs.dSG = B->upload(sg);
+        bs.dST = B->upload(st);
+        bs.nst = (int)st.size();
+      }
+    }
+    std::vector<const TaskList*> pf;
+    for (auto* p : B->plans) pf.push_back(&p->fin);
+    B->fin = merge_tasks(*B, pf);
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    *out = B.release();
+  });
+}
+
+extern "C" tnx_status tnx_batch_destroy(tnx_batch* b) {
+  if (!b) return TNX_ERR_ARG;
+  cudaStreamSynchronize(b->ctx->stream);
+  delete b;
+  return TNX_OK;
+}
+
+extern "C" tnx_status tnx_batch_flops(tnx_batch* b, double* flops) {
+  if (!b || !flops) return TNX_ERR_ARG;
+  double f = 0;
+  for (auto& s : b->steps) f += s.flops;
+  *flops = f;
+  return TNX_OK;
+}
+
+extern "C" tnx_status tnx_batch_launch_into(tnx_batch* b, tnx_tensor* const* outs) {
+  if (!b) return TNX_ERR_ARG;
+  return tnx_guard(b->ctx, [&] {
+    if (!outs) fail(TNX_ERR_ARG, "null outputs");
+    for (size_t i = 0; i < b->nets.size(); ++i)
+      if (!outs[i]) fail(TNX_ERR_ARG, "null output tensor");
+    check_fresh(*b);
+    bind(*b, outs);
+    tnx_ctx* c = b->ctx;
+    if (c->stream && c->use_graphs) {
+      if (!b->graph || b->graph->prof != c->prof) {
+        b->graph.reset(new GraphRec());
+        tnx_capture_graph(c, c->stream, *b->graph, [&] { enqueue_batch(*b, c->stream); });
+      }
+      CUDA_CHECK(cudaGraphLaunch(b->graph->exec, c->stream));
+      if (c->prof) {
+        CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        prof_accumulate(c, b->graph->recs);
+      }
+    } else {
+      enqueue_batch(*b, c->stream);
+    }
+  });
+}
+
+extern "C" tnx_status tnx_batch_autotune(tnx_batch* b, tnx_tensor* const* outs, int* choice) {
+  if (!b) return TNX_ERR_ARG;
+  return tnx_guard(b->ctx, [&] {
+    if (!outs) fail(TNX_ERR_ARG, "null outputs");
+    check_fresh(*b);
+    bind(*b, outs);
+    tnx_ctx* c = b->ctx;
+    const bool prof = c->prof;
+    c->prof = false;
+    const int cands[] = {0, 152, 304, 456};
+    float best = 1e30f;
+    int pick = 0;
+    cudaEvent_t e0, e1;
+    CUDA_CHECK(cudaEventCreate(&e0));
+    CUDA_CHECK(cudaEventCreate(&e1));
+    for (int cand : cands) {
+      b->split_grid = cand;
+      enqueue_batch(*b, c->stream);   // warm
+      float t = 1e30f;
+      for (int r = 0; r < 3; ++r) {
+        CUDA_CHECK(cudaEventRecord(e0, c->stream));
+        enqueue_batch(*b, c->stream);
+        CUDA_CHECK(cudaEventRecord(e1, c->stream));
+        CUDA_CHECK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+        t = std::min(t, ms);
+      }
+      if (t < best) {
+        best = t;
+        pick = cand;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->prof = prof;
+    b->split_grid = pick;
+    b->graph.reset();
+    if (choice) *choice = pick;
+  });
+}

@@ -121,8 +121,10 @@ cudaError_t tnx_launch_row_exponents(const SliceJob* jobs, const int64_t* row_st
                                      int64_t total_rows, double* const* slots, cudaStream_t st);
 cudaError_t tnx_launch_slices(const SliceJob* jobs, const int64_t* tile_start, int njobs, int64_t total_tiles,
                               int nslice, int beta, int f16, double* const* slots, cudaStream_t st);
+// grid <= 0 or >= ntiles: one CTA per tile; otherwise a persistent grid of `grid` CTAs
 cudaError_t tnx_launch_gemm_split(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int nslice,
-                                  int beta, int f16, double* const* slots, int32_t* status, cudaStream_t st);
+                                  int beta, int f16, double* const* slots, int32_t* status, cudaStream_t st,
+                                  int grid = 0);
 cudaError_t tnx_launch_gemm_tf32(const SplitGroup* groups, const GemmTile* tiles, int ntiles,
                                  double* const* slots, int32_t* status, cudaStream_t st);
 

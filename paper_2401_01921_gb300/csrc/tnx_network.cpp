@@ -360,6 +360,8 @@ TaskList upload_tasks(Plan& p, const std::vector<CopyTask>& tasks) {
   tl.nchunks = (int)chunks.size();
   tl.d = p.upload(tasks);
   tl.chunks = p.upload(chunks);
+  tl.h = tasks;
+  tl.hchunks = chunks;
   return tl;
 }
 
@@ -607,6 +609,9 @@ void build_step(Plan& p, StepPlan& s) {
   s.ntiles = (int)tiles.size();
   s.dTs = p.upload(stiles);
   s.nstiles_skinny = (int)stiles.size();
+  s.hG = gg;
+  s.hT = tiles;
+  s.hTs = stiles;
 
   // useful flops: matched block pairs share (group, K offset)
   std::map<std::pair<int64_t, int64_t>, std::pair<double, double>> acc;
@@ -920,6 +925,14 @@ void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB
   tnx_enqueue_split(p, s, st, needA, needB);
 }
 }  // namespace
+
+// shared with the batch module
+Plan* tnx_ensure_plan(tnx_network* net) { return ensure_plan(net); }
+void tnx_bind_inputs(tnx_network* net, Plan& p) { bind_inputs(net, p); }
+void tnx_check_out_bonds(const Plan& p, const tnx_tensor* out) { check_out_bonds(p, out); }
+void tnx_capture_graph(tnx_ctx* c, cudaStream_t st, GraphRec& g, const std::function<void()>& body) {
+  capture_graph(c, st, g, body);
+}
 
 // ------------------------------------------------------------------ C-ABI
 static bool all_put(const tnx_network* net);

@@ -35,6 +35,8 @@ struct TaskList {
   int nchunks = 0;
   int n = 0;
   int64_t total = 0;
+  std::vector<CopyTask> h;      // host copies (batched plans merge them)
+  std::vector<int2> hchunks;
 };
 
 struct StepPlan {
@@ -54,6 +56,8 @@ struct StepPlan {
   int ntiles = 0;
   GemmTile* dTs = nullptr;      // skinny (K <= 16) tiles, FP64 in every precision
   int nstiles_skinny = 0;
+  std::vector<GemmGroup> hG;    // host copies
+  std::vector<GemmTile> hT, hTs;
   std::vector<char> skinny;     // per group
   double flops_skinny = 0;      // useful flops of the skinny groups
   // split precision
@@ -66,11 +70,15 @@ struct StepPlan {
     int64_t* warp_start = nullptr;
     int64_t warps = 0;
     int64_t elems = 0;
+    std::vector<SliceJob> h;    // host copies
+    std::vector<int64_t> hrows, hwarps;   // per-job row and warp counts
   } jobsAll, jobsA, jobsB;
   int64_t slice_elems = 0;      // packed elements that get sliced (split precision)
   SplitGroup* dSG = nullptr;
   GemmTile* dST = nullptr;
   int nstiles = 0;
+  std::vector<SplitGroup> hSG;  // host copies
+  std::vector<GemmTile> hST;
 };
 
 // A captured CUDA graph plus the profiler events recorded inside it.

@@ -1,6 +1,8 @@
 // Split-precision planning: per pairwise step, the row-exponent and slicing
 // jobs that turn the packed FP64 operands into tiles of integer-valued 16-bit
 // slices, and the tile list of the tcgen05 split GEMM (k_split.cu).
+#include <algorithm>
+
 #include "tnx_plan.h"
 
 size_t tnx_split_smem_bytes(int nslice);
@@ -84,6 +86,9 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
     J.d = p.upload(js);
     J.row_start = p.upload(rs);
     J.warp_start = p.upload(ws);
+    J.h = js;
+    J.hrows = rc;
+    J.hwarps = wc;
     return J;
   };
   std::vector<SliceJob> all = jobs[0];
@@ -118,9 +123,13 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
     for (int m0 = 0; m0 < x.M; m0 += TM)
       for (int n0 = 0; n0 < x.N; n0 += TN) tiles.push_back(GemmTile{g, m0, n0, 0});
   }
+  std::stable_sort(tiles.begin(), tiles.end(),
+                   [&](const GemmTile& x, const GemmTile& y) { return sg[x.group].K > sg[y.group].K; });
   s.dSG = p.upload(sg);
   s.dST = p.upload(tiles);
   s.nstiles = (int)tiles.size();
+  s.hSG = sg;
+  s.hST = tiles;
 }
 
 void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB) {
