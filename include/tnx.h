@@ -246,6 +246,48 @@ tnx_status tnx_batch_flops(tnx_batch* b, double* flops);
  * *choice (may be NULL) gets the grid size (0 = one CTA per tile). */
 tnx_status tnx_batch_autotune(tnx_batch* b, tnx_tensor* const* outs, int* choice);
 
+/* ------------------------------------------------- no-allocation variant */
+
+/* The fused charge-sector tables of ONE pairwise contraction (what
+ * tnx_network_step_tables reports for a step), computed by the device matching
+ * kernel WITHOUT allocating any memory.  The paper has no counterpart: this is
+ * for callers that cannot call cudaMalloc (or any allocator) where they need
+ * the tables - a latency-critical loop whose memory was sized up front, a
+ * process whose device memory belongs to another framework's pool, a plugin
+ * that only receives pre-sized buffers.  No tnx_ctx is needed (creating one
+ * allocates).
+ *
+ * The kernel's working memory is a fixed 16 MiB array in device memory that
+ * every GPU loading the library holds until the process exits; contractions
+ * that need more are refused (TNX_ERR_UNSUPPORTED, with the byte count in err).
+ * Every call shares that array: calls that overlap on the GPU race and must be
+ * serialised by the caller.  The first call on a device looks up the array's
+ * device address (with that device current); make that first call before any
+ * stream capture.  The call enqueues on `stream` (a cudaStream_t, NULL = legacy
+ * default stream) and waits for it before returning.
+ *
+ * Arguments (host = host memory, dev = device memory):
+ *  nsym, zn[nsym] (host): symmetries; zn[c] = 0 for U(1), n for Z_n.
+ *  nk, nfa, nfb: contracted legs, free legs of A, free legs of B.
+ *  nsec[nk+nfa+nfb] (host): sectors per leg, K legs (in A's leg order) first.
+ *  degs (host): degeneracies of every sector of those legs, concatenated.
+ *  kcharges (host): [K-leg sector][nsym] charges as they enter A's flux
+ *      (negated on OUT legs, reduced mod n for Z_n).
+ *  nA, rA, qA (dev, int32 [nA*rA]): A's blocks (sector indices, lexicographic;
+ *      every entry must be a valid sector index of its leg: not checked);
+ *  kposA[nk], fposA[nfa] (host): A's legs holding the K / free legs; same for B.
+ *  gmax: capacity of the group outputs.
+ *  Outputs (dev): ngroups[1], charges[gmax*nsym], mkn[gmax*3],
+ *      amap[nA*3], bmap[nB*3] - the same conventions as tnx_network_step_tables.
+ *  err[errlen] (host, may be NULL): message on failure, empty on success. */
+tnx_status tnx_match_tables_noalloc(void* stream, int nsym, const int32_t* zn, int nk, int nfa, int nfb,
+                                    const int32_t* nsec, const int64_t* degs, const int32_t* kcharges,
+                                    int64_t nA, int rA, const int32_t* qA, const int32_t* kposA,
+                                    const int32_t* fposA, int64_t nB, int rB, const int32_t* qB,
+                                    const int32_t* kposB, const int32_t* fposB, int gmax, int32_t* ngroups,
+                                    int32_t* charges, int64_t* mkn, int64_t* amap, int64_t* bmap, char* err,
+                                    size_t errlen);
+
 /* ------------------------------------------------------------ diagnostics */
 
 /* Kernel classes timed by the profiler. */
