@@ -9,8 +9,9 @@
 //
 // A task copies one block: per leg a shape, a source stride and a destination
 // stride (elements); the legs are ordered so that the last one is contiguous
-// in the destination.  The planner cuts every task into chunks of at most
-// CHUNK elements; one CTA takes one chunk (one descriptor load, no search),
+// in the destination.  The planner cuts large tasks into chunks of at most
+// CHUNK elements and packs runs of small tasks (up to PACK of them, CHUNK
+// elements in all) into one chunk; one CTA takes one chunk,
 // its threads walk destination order so stores coalesce, and loads coalesce
 // whenever the source is contiguous along the same leg.  When the source is
 // contiguous along another leg, the task is moved in 32 x 32 tiles staged
@@ -73,49 +74,78 @@ __device__ void copy_transpose(const CopyTask& t, int tile, double* const* __res
   }
 }
 
-__global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ tasks, const int2* __restrict__ chunks,
+// Element e of a task: decompose the in-task index over the legs (last leg
+// fastest) into source and destination offsets.
+__device__ __forceinline__ void copy_one(const CopyTask& t, const double* src, double* dst, int i) {
+  int64_t so = 0, dof = 0;
+#pragma unroll
+  for (int l = TNX_MAXR - 1; l >= 0; --l) {
+    if (l < t.rank) {
+      const int sh = t.shape[l];
+      const int q = i / sh;
+      const int rem = i - q * sh;
+      i = q;
+      so += rem * t.sstride[l];
+      dof += rem * t.dstride[l];
+    }
+  }
+  dst[dof] = src ? __ldg(src + so) : 0.0;
+}
+
+// chunk = (first task, first element, number of tasks, number of elements).
+// One task: its elements [first, first + count).  Several (small) tasks: all
+// their elements, back to back; the chunk's descriptors are staged in shared
+// memory and each thread finds its task by binary search over their starts.
+// A negative task count marks one 32 x 32 tile of a transposing task.
+__global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ tasks, const int4* __restrict__ chunks,
                                                   double* const* __restrict__ slots) {
-  const int2 ch = chunks[blockIdx.x];           // (task, first element of the chunk, or tile index)
-  const CopyTask& t = tasks[ch.x];
-  if (t.tleg >= 0) {
-    copy_transpose(t, ch.y, slots);
+  __shared__ CopyTask st[TNX_COPY_PACK];
+  __shared__ int sstart[TNX_COPY_PACK + 1];
+  const int4 ch = chunks[blockIdx.x];
+  if (ch.z < 0) {
+    copy_transpose(tasks[ch.x], ch.y, slots);
     return;
   }
-  const int r = t.rank;
-  int shape[TNX_MAXR];
-  int64_t ss[TNX_MAXR], ds[TNX_MAXR];
-#pragma unroll
-  for (int l = 0; l < TNX_MAXR; ++l) {
-    if (l < r) {
-      shape[l] = t.shape[l];
-      ss[l] = t.sstride[l];
-      ds[l] = t.dstride[l];
-    }
+  if (ch.z == 1) {
+    const CopyTask& t = tasks[ch.x];
+    const double* src = t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr;
+    double* dst = slots[t.dst_slot] + t.dst_off;
+    for (int e = ch.y + threadIdx.x; e < ch.y + ch.w; e += CT) copy_one(t, src, dst, e);
+    return;
   }
-  const double* src = t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr;
-  double* dst = slots[t.dst_slot] + t.dst_off;
-  const int64_t lim = (int64_t)ch.y + TNX_COPY_CHUNK;
-  const int end = (int)(t.nelem < lim ? t.nelem : lim);
-  for (int e = ch.y + threadIdx.x; e < end; e += CT) {
-    int i = e;
-    int64_t so = 0, dof = 0;
-#pragma unroll
-    for (int l = TNX_MAXR - 1; l >= 0; --l) {
-      if (l < r) {
-        const int q = i / shape[l];
-        const int rem = i - q * shape[l];
-        i = q;
-        so += rem * ss[l];
-        dof += rem * ds[l];
-      }
+  // several small tasks
+  const int nt = ch.z;
+  {
+    const int words = (int)(sizeof(CopyTask) / 4) * nt;
+    const int* g = (const int*)(tasks + ch.x);
+    int* sm = (int*)st;
+    for (int i = threadIdx.x; i < words; i += CT) sm[i] = g[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int k = 0; k < nt; ++k) {
+      sstart[k] = acc;
+      acc += (int)st[k].nelem;
     }
-    dst[dof] = src ? __ldg(src + so) : 0.0;
+    sstart[nt] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < ch.w; e += CT) {
+    int lo = 0, hi = nt;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (sstart[mid] <= e) lo = mid; else hi = mid;
+    }
+    const CopyTask& t = st[lo];
+    const double* src = t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr;
+    copy_one(t, src, slots[t.dst_slot] + t.dst_off, e - sstart[lo]);
   }
 }
 
 }  // namespace
 
-cudaError_t tnx_launch_copy(const CopyTask* tasks, const int2* chunks, int nchunks, double* const* slots,
+cudaError_t tnx_launch_copy(const CopyTask* tasks, const int4* chunks, int nchunks, double* const* slots,
                             cudaStream_t st) {
   if (nchunks <= 0) return cudaSuccess;
   copy_kernel<<<nchunks, CT, 0, st>>>(tasks, chunks, slots);

@@ -61,19 +61,17 @@ int shift_slot(int s, int b) { return s < 0 ? s : s + b; }
 
 TaskList merge_tasks(tnx_batch& B, const std::vector<const TaskList*>& parts) {
   std::vector<CopyTask> tasks;
-  std::vector<int2> chunks;
+  std::vector<int4> chunks;
   TaskList out;
   for (size_t i = 0; i < parts.size(); ++i) {
-    const int off = (int)tasks.size();
     for (CopyTask t : parts[i]->h) {
       t.src_slot = shift_slot(t.src_slot, B.base[i]);
       t.dst_slot = shift_slot(t.dst_slot, B.base[i]);
       tasks.push_back(t);
     }
-    for (int2 c : parts[i]->hchunks) chunks.push_back(make_int2(c.x + off, c.y));
     out.total += parts[i]->total;
   }
-  if (chunks.size() > INT32_MAX) fail(TNX_ERR_UNSUPPORTED, "too many relayout chunks in the batch");
+  tnx_make_copy_chunks(tasks, chunks);   // small tasks of different instances pack together
   out.n = (int)tasks.size();
   out.nchunks = (int)chunks.size();
   out.d = B.upload(tasks);

@@ -106,9 +106,12 @@ void tnx_note_launch(int n);
 // ---------------------------------------------------------------------------
 cudaError_t tnx_launch_match(const MatchArgs& a, cudaStream_t st);
 #define TNX_COPY_CHUNK 1024    // elements per relayout CTA
-// chunks[i] = (task index, first element); a task of n elements has ceil(n / TNX_COPY_CHUNK) chunks;
-// a transposing task has one chunk per 32 x 32 tile: (task index, tile index)
-cudaError_t tnx_launch_copy(const CopyTask* tasks, const int2* chunks, int nchunks, double* const* slots,
+#define TNX_COPY_PACK 64       // small tasks per relayout CTA at most
+// chunks[i] = (first task, first element, task count, element count): a large
+// task is cut into chunks of TNX_COPY_CHUNK elements (task count 1), runs of
+// small tasks are packed (task count > 1, first element 0), and a transposing
+// task has one chunk per 32 x 32 tile: (task, tile index, -1, 0).
+cudaError_t tnx_launch_copy(const CopyTask* tasks, const int4* chunks, int nchunks, double* const* slots,
                             cudaStream_t st);
 cudaError_t tnx_launch_gemm_f64(const GemmGroup* groups, const GemmTile* tiles, int ntiles,
                                 double* const* slots, cudaStream_t st);

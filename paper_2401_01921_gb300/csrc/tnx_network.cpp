@@ -322,6 +322,41 @@ void finish_task(CopyTask& t, std::vector<int64_t> shape, std::vector<int64_t> s
   }
 }
 
+}  // namespace
+
+// Chunks of the relayout kernel (see k_copy.cu): large tasks cut into pieces of
+// TNX_COPY_CHUNK elements, consecutive small tasks packed together, transposing
+// tasks cut into 32 x 32 tiles.
+void tnx_make_copy_chunks(const std::vector<CopyTask>& tasks, std::vector<int4>& chunks) {
+  chunks.clear();
+  size_t i = 0;
+  while (i < tasks.size()) {
+    const CopyTask& t = tasks[i];
+    if (t.nelem > INT32_MAX) fail(TNX_ERR_UNSUPPORTED, "block above 2^31 elements");
+    if (t.tleg >= 0) {
+      const int64_t ncols = t.shape[t.tleg], nrows = t.nelem / ncols;
+      const int64_t ntiles = ((nrows + 31) / 32) * ((ncols + 31) / 32);
+      for (int64_t k = 0; k < ntiles; ++k) chunks.push_back(make_int4((int)i, (int)k, -1, 0));
+      ++i;
+    } else if (t.nelem >= TNX_COPY_CHUNK / 2) {
+      for (int64_t e = 0; e < t.nelem; e += TNX_COPY_CHUNK)
+        chunks.push_back(make_int4((int)i, (int)e, 1, (int)std::min<int64_t>(TNX_COPY_CHUNK, t.nelem - e)));
+      ++i;
+    } else {
+      size_t j = i;
+      int64_t tot = 0;
+      while (j < tasks.size() && j - i < TNX_COPY_PACK && tasks[j].tleg < 0 && tasks[j].nelem < TNX_COPY_CHUNK / 2 &&
+             tot + tasks[j].nelem <= TNX_COPY_CHUNK)
+        tot += tasks[j++].nelem;
+      chunks.push_back(make_int4((int)i, 0, (int)(j - i), (int)tot));
+      i = j;
+    }
+  }
+  if (chunks.size() > INT32_MAX) fail(TNX_ERR_UNSUPPORTED, "too many relayout chunks");
+}
+
+namespace {
+
 // Every element a task touches must lie inside its slot's buffer: checked on
 // the host before anything is launched.
 void validate_tasks(const Plan& p, const std::vector<CopyTask>& tasks) {
@@ -342,19 +377,10 @@ void validate_tasks(const Plan& p, const std::vector<CopyTask>& tasks) {
 TaskList upload_tasks(Plan& p, const std::vector<CopyTask>& tasks) {
   validate_tasks(p, tasks);
   TaskList tl;
-  std::vector<int2> chunks;
+  std::vector<int4> chunks;
   tl.total = 0;
-  for (size_t i = 0; i < tasks.size(); ++i) {
-    if (tasks[i].nelem > INT32_MAX) fail(TNX_ERR_UNSUPPORTED, "block above 2^31 elements");
-    if (tasks[i].tleg >= 0) {
-      const int64_t ncols = tasks[i].shape[tasks[i].tleg], nrows = tasks[i].nelem / ncols;
-      const int64_t ntiles = ((nrows + 31) / 32) * ((ncols + 31) / 32);
-      for (int64_t k = 0; k < ntiles; ++k) chunks.push_back(make_int2((int)i, (int)k));
-    } else {
-      for (int64_t e = 0; e < tasks[i].nelem; e += TNX_COPY_CHUNK) chunks.push_back(make_int2((int)i, (int)e));
-    }
-    tl.total += tasks[i].nelem;
-  }
+  tnx_make_copy_chunks(tasks, chunks);
+  for (size_t i = 0; i < tasks.size(); ++i) tl.total += tasks[i].nelem;
   if (chunks.size() > INT32_MAX) fail(TNX_ERR_UNSUPPORTED, "too many relayout chunks");
   tl.n = (int)tasks.size();
   tl.nchunks = (int)chunks.size();

@@ -31,12 +31,12 @@ struct OpView {
 
 struct TaskList {
   CopyTask* d = nullptr;
-  int2* chunks = nullptr;
+  int4* chunks = nullptr;
   int nchunks = 0;
   int n = 0;
   int64_t total = 0;
   std::vector<CopyTask> h;      // host copies (batched plans merge them)
-  std::vector<int2> hchunks;
+  std::vector<int4> hchunks;
 };
 
 struct StepPlan {
@@ -152,3 +152,6 @@ struct tnx_network {
 // split-precision planning and launch (tnx_split.cpp)
 void tnx_build_split_parts(Plan& p, StepPlan& s);
 void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB);
+
+// relayout chunks (tnx_network.cpp)
+void tnx_make_copy_chunks(const std::vector<CopyTask>& tasks, std::vector<int4>& chunks);
