@@ -9,7 +9,7 @@ vector work in FP64 on the device.  Useful flops are 2*m*k*n over the matched
 block pairs of every pairwise contraction, times the number of matvecs.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl tnx|reference]
-                  [--workload chi512|chi2048|dense32|batch256] [--prec split_bf16|f64|...]
+                  [--workload chi512|chi2048|dense32|batch256|serve] [--prec split_bf16|f64|...]
 
 --impl reference times the plain CPU FP64 oracle on the host cores (bounded
 sample) on the same metric.  With N > 1 (torchrun, NCCL) every rank runs an
@@ -241,6 +241,86 @@ def run_batch(args, torch, dev, tnx, I, build_network, dist, world, rank, local)
         print(json.dumps(line))
 
 
+def run_serve(args, torch, dev, tnx, I, build_network, rank, local):
+    """C5: Poisson stream of H_eff*psi applies and 30-step Lanczos solves over resident networks
+    (70% Heisenberg U(1), 30% Hubbard U(1)xU(1), chi log-uniform in [128, 4096]) through the
+    continuous-batching server (split precision, 8 slots, 150 GB budget), against the same trace
+    served one request at a time in plain FP64."""
+    import numpy as np
+    rng = np.random.default_rng(5)
+    npool = 12
+    u = I.uniform_at(5, 0, np.arange(npool))
+    chis = [int(round(2.0 ** (7.0 + 5.0 * x))) for x in u]
+    kinds = ["hubbard" if i % 10 in (3, 6, 9) else "heisenberg" for i in range(npool)]
+    ctx = tnx.Context(local)
+
+    def make_pool(prec):
+        pool = []
+        for i, (chi, kind) in enumerate(zip(chis, kinds)):
+            if kind == "heisenberg":
+                wl = I.heisenberg_workload(chi, max(6, int(round(20 * (chi / 512) ** 0.5))))
+            else:
+                wl = I.hubbard_workload(chi, seed_base=5000 + 4 * i)
+            bonds = I.heff_bonds(wl)
+            tensors = {n: (bonds[n], I.heff_value_fn(wl, n, symmetric=True)) for n in I.HEFF_NAMES}
+            net, T, B = build_network(ctx, I.HEFF_SPEC, tensors, wl.nsym, prec=prec)
+            pool.append((net, T, B, tnx.Tensor(ctx, B["psi"]), net.flops()))
+        return pool
+
+    nreq = args.steps * 12
+    which = rng.integers(0, npool, nreq)
+    isl = rng.random(nreq) < 0.5
+    gaps = rng.exponential(1.0, nreq)
+
+    def run(pool, slots, rate):
+        srv = tnx.Server(ctx, max_slots=slots, hbm_budget_bytes=150 * 10**9)
+        # warm every network once (plans, graphs) outside the measurement
+        for i in range(npool):
+            net, T, B, out, fl = pool[i]
+            srv.wait(srv.submit(net, "psi", T["psi"], tnx.REQ_LANCZOS, 30))
+            srv.wait(srv.submit(net, "psi", T["psi"], tnx.REQ_APPLY, 0, out))
+        t0 = time.perf_counter()
+        ids, useful = [], 0.0
+        at = 0.0
+        for k in range(nreq):
+            at += gaps[k] / rate
+            while time.perf_counter() - t0 < at:
+                time.sleep(0.0002)
+            net, T, B, out, fl = pool[which[k]]
+            if isl[k]:
+                ids.append(srv.submit(net, "psi", T["psi"], tnx.REQ_LANCZOS, 30))
+                useful += 30 * fl
+            else:
+                ids.append(srv.submit(net, "psi", T["psi"], tnx.REQ_APPLY, 0, out))
+                useful += fl
+        lat = [srv.wait(i)[2] for i in ids]
+        span = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return {"rate_req_s": rate, "requests": nreq, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "throughput_req_s": nreq / span,
+                "useful_tflops": useful / span / 1e12, "peak_resident_gb": st["peak_bytes"] / 1e9,
+                "evictions": st["evictions"]}
+
+    split_pool = make_pool("split_bf16")
+    sweep = [run(split_pool, 8, r) for r in (20.0, 80.0, 320.0)]
+    del split_pool
+    f64_pool = make_pool("f64")
+    base = run(f64_pool, 1, 80.0)
+    best = max(sweep, key=lambda x: x["throughput_req_s"])
+    line = {"metric": "serving: H_eff*psi / Lanczos requests, p50/p99 latency (ms) and throughput",
+            "value": best["throughput_req_s"], "unit": "requests/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 via split_bf16 slices", "data": "synthetic",
+            "config": {"workload": "serving_heisenberg70_hubbard30_chi128to4096_poisson",
+                       "pool_chis": chis, "pool_kinds": kinds, "requests_per_rate": nreq,
+                       "request_mix": "50% one apply, 50% 30-step Lanczos", "slots": 8, "hbm_budget_gb": 150,
+                       "sweep": sweep, "baseline_f64_one_at_a_time": base},
+            "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"]}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,6 +353,9 @@ def main():
     import tnx_inputs as I
     from paper_2401_01921_gb300.heff import build_network
 
+    if args.workload == "serve":
+        run_serve(args, torch, dev, tnx, I, build_network, rank, local)
+        return
     if args.workload == "batch256":
         run_batch(args, torch, dev, tnx, I, build_network, dist, world, rank, local)
         if dist:

@@ -246,6 +246,38 @@ tnx_status tnx_batch_flops(tnx_batch* b, double* flops);
  * *choice (may be NULL) gets the grid size (0 = one CTA per tile). */
 tnx_status tnx_batch_autotune(tnx_batch* b, tnx_tensor* const* outs, int* choice);
 
+/* ---------------------------------------------------------------- serving */
+
+/* A serving loop with continuous batching (no counterpart in the paper).  A
+ * request is one H_eff*psi-style apply (TNX_REQ_APPLY: out = the network
+ * applied with `vec` in slot `vec_slot`) or a Lanczos solve (TNX_REQ_LANCZOS:
+ * nsteps steps from `vec`; out, optional, receives the Ritz vector).  The
+ * networks stay resident (plans, packed constant operands, Lanczos workspace)
+ * between requests.  A worker thread admits queued requests, first fit in
+ * arrival order, whenever one of max_slots stream slots is free, the request's
+ * network is idle (one request per network at a time) and its resident memory
+ * fits hbm_budget_bytes (idle networks are evicted least recently used first);
+ * admitted requests run concurrently on their own CUDA streams.  While a
+ * server runs, the networks it serves must not be launched or modified through
+ * other calls, and the context's allocator must be callable from the worker
+ * thread. */
+enum { TNX_REQ_APPLY = 0, TNX_REQ_LANCZOS = 1 };
+typedef struct tnx_server tnx_server;
+tnx_status tnx_server_create(tnx_ctx* ctx, int max_slots, size_t hbm_budget_bytes, tnx_server** out);
+/* Stops the worker (requests not yet started are dropped), waits for running ones. */
+tnx_status tnx_server_destroy(tnx_server* s);
+/* Queues a request; *id identifies it for tnx_server_wait.  Thread-safe. */
+tnx_status tnx_server_submit(tnx_server* s, tnx_network* net, const char* vec_slot, tnx_tensor* vec, int kind,
+                             int nsteps, tnx_tensor* out, int64_t* id);
+/* Blocks until request id finishes (timeout_ms < 0: no limit; TNX_ERR_TIMEOUT
+ * if it runs out) and returns its status; eval / matvecs (Lanczos) and the
+ * latency from submission to completion in milliseconds (any may be NULL).
+ * Each id can be waited for once. */
+tnx_status tnx_server_wait(tnx_server* s, int64_t id, int timeout_ms, double* eval, int* matvecs, double* latency_ms);
+/* Completed requests, evictions, bytes currently resident, peak resident bytes. */
+tnx_status tnx_server_stats(tnx_server* s, int64_t* completed, int64_t* evictions, size_t* used_bytes,
+                            size_t* peak_bytes);
+
 /* ------------------------------------------------- no-allocation variant */
 
 /* The fused charge-sector tables of ONE pairwise contraction (what

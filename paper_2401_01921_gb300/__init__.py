@@ -92,6 +92,12 @@ _SIGS = {
     "tnx_batch_launch_into": (C.c_int, [_p, C.POINTER(_p)]),
     "tnx_batch_flops": (C.c_int, [_p, C.POINTER(C.c_double)]),
     "tnx_batch_autotune": (C.c_int, [_p, C.POINTER(_p), C.POINTER(C.c_int)]),
+    "tnx_server_create": (C.c_int, [_p, C.c_int, C.c_size_t, C.POINTER(_p)]),
+    "tnx_server_destroy": (C.c_int, [_p]),
+    "tnx_server_submit": (C.c_int, [_p, _p, C.c_char_p, _p, C.c_int, C.c_int, _p, _i64p]),
+    "tnx_server_wait": (C.c_int, [_p, C.c_int64, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_double)]),
+    "tnx_server_stats": (C.c_int, [_p, _i64p, _i64p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "tnx_profile_enable": (C.c_int, [_p, C.c_int]),
     "tnx_profile_read": (C.c_int, [_p, C.POINTER(C.c_double), _i64p, C.POINTER(C.c_double)]),
     "tnx_kernel_launches": (C.c_int, [_i64p]),
@@ -438,6 +444,48 @@ class Batch:
         try:
             if self.h:
                 lib().tnx_batch_destroy(self.h)
+        except Exception:
+            pass
+
+
+REQ_APPLY, REQ_LANCZOS = 0, 1
+
+
+class Server:
+    """tnx_server: continuous-batching request loop over resident networks."""
+
+    def __init__(self, ctx: Context, max_slots: int = 8, hbm_budget_bytes: int = 150 * 10**9):
+        self.ctx = ctx
+        h = C.c_void_p()
+        ctx.check(lib().tnx_server_create(ctx.h, max_slots, hbm_budget_bytes, C.byref(h)))
+        self.h = h
+
+    def submit(self, net: Network, slot: str, vec: Tensor, kind: int, nsteps: int = 0, out: Tensor | None = None) -> int:
+        i = C.c_int64()
+        self.ctx.check(lib().tnx_server_submit(self.h, net.h, slot.encode(), vec.h, kind, nsteps,
+                                               out.h if out is not None else None, C.byref(i)))
+        return i.value
+
+    def wait(self, rid: int, timeout_ms: int = -1):
+        """(eigenvalue, matvecs, latency ms) of request rid."""
+        ev, mv, lat = C.c_double(), C.c_int(), C.c_double()
+        self.ctx.check(lib().tnx_server_wait(self.h, rid, timeout_ms, C.byref(ev), C.byref(mv), C.byref(lat)))
+        return ev.value, mv.value, lat.value
+
+    def stats(self) -> dict:
+        c, e = C.c_int64(), C.c_int64()
+        u, pk = C.c_size_t(), C.c_size_t()
+        self.ctx.check(lib().tnx_server_stats(self.h, C.byref(c), C.byref(e), C.byref(u), C.byref(pk)))
+        return {"completed": c.value, "evictions": e.value, "used_bytes": u.value, "peak_bytes": pk.value}
+
+    def close(self):
+        if self.h:
+            lib().tnx_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass
 

@@ -169,6 +169,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ------------------------------------------------------- exponent pass
@@ -428,16 +434,20 @@ __global__ void __launch_bounds__(192, 1) split_gemm_kernel(const SplitGroup* __
           break;
         }
         tc_fence_after();
+        // all levels of 8 columns in flight at once, one wait per column group
 #pragma unroll
-        for (int cg = 0; cg < TN / 16; ++cg) {
+        for (int cg = 0; cg < TN / 8; ++cg) {
+          uint32_t v[NS][8];
 #pragma unroll
-          for (int t = 0; t < NS; ++t) {
-            uint32_t v[16];
-            tmem_ld16(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(t * TN + cg * 16), v);
-            tmem_wait_ld();
-            const long long scale_t = 1LL << (beta * (NS - 1 - t));
+          for (int t = 0; t < NS; ++t) tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(t * TN + cg * 8), v[t]);
+          tmem_wait_ld();
 #pragma unroll
-            for (int c = 0; c < 16; ++c) acc[cg * 16 + c] += (long long)__float2int_rn(__uint_as_float(v[c])) * scale_t;
+          for (int c = 0; c < 8; ++c) {
+            long long x = 0;
+#pragma unroll
+            for (int t = 0; t < NS; ++t)
+              x += (long long)__float2int_rn(__uint_as_float(v[t][c])) * (1LL << (beta * (NS - 1 - t)));
+            acc[cg * 8 + c] += x;
           }
         }
         tc_fence_before();

@@ -91,11 +91,11 @@ __global__ void set_slot_kernel(double** slot, double* p) { *slot = p; }
 
 // partial[b*m + i] = <V_i, w> over this block's contiguous chunk, i < m.  A
 // fixed grid of MD_BLOCKS blocks keeps the number of partial sums (and so the
-// FP64 additions of the reduction tree) small; each thread keeps 16 running
+// FP64 additions of the reduction tree) bounded; each thread keeps 16 running
 // sums, w is read once per group of 16 vectors, and the block reduction goes
 // through shared memory: 16 rows of MD_T values, 8 threads per row.
 constexpr int MD_T = 128;
-constexpr int MD_BLOCKS = 152;
+constexpr int MD_BLOCKS = 608;   // 4 per SM: enough warps in flight to hide load latency
 
 __global__ void __launch_bounds__(MD_T) multidot_kernel(LanczosDev L, int m) {
   __shared__ double sh[16][MD_T + 1];

@@ -21,6 +21,8 @@
 #include <algorithm>
 #include <cstring>
 #include <numeric>
+#include <cstdio>
+#include <cstdlib>
 #include <set>
 
 #include "tnx_host.h"
@@ -854,6 +856,27 @@ Plan* ensure_plan(tnx_network* net) {
   };
   OpView root = walk(net->root);
   build_final(*p, root, net->tout);
+  if (const char* dbg = getenv("TNX_DEBUG_PLAN")) {
+    if (*dbg && *dbg != '0') {
+      auto stats = [](const TaskList& t) {
+        int tr = 0, packed = 0;
+        for (auto& c : t.hchunks) {
+          if (c.z < 0) ++tr;
+          else if (c.z > 1) ++packed;
+        }
+        return std::to_string(t.n) + " tasks, " + std::to_string(t.total) + " elems, " + std::to_string(t.nchunks) +
+               " chunks (" + std::to_string(tr) + " transpose tiles, " + std::to_string(packed) + " packed)";
+      };
+      fprintf(stderr, "[tnx plan] order %s prec %d\n", p->order.c_str(), p->prec);
+      for (size_t i = 0; i < p->steps.size(); ++i) {
+        const StepPlan& s = p->steps[i];
+        fprintf(stderr, "[tnx plan] step %zu: G=%d flops=%.3e skinny=%.3e tiles=%d skinny_tiles=%d split_tiles=%d\n", i,
+                s.G, s.flops, s.flops_skinny, s.ntiles, s.nstiles_skinny, s.nstiles);
+        fprintf(stderr, "[tnx plan]   A: %s\n[tnx plan]   B: %s\n", stats(s.copyA).c_str(), stats(s.copyB).c_str());
+      }
+      fprintf(stderr, "[tnx plan] final: %s\n", stats(p->fin).c_str());
+    }
+  }
   p->d_slots = (double**)p->alloc_zero(p->h_slots.size() * sizeof(double*));
   p->h_slots_dev.assign(p->h_slots.size(), nullptr);
   CUDA_CHECK(cudaStreamSynchronize(net->ctx->stream));
@@ -861,12 +884,13 @@ Plan* ensure_plan(tnx_network* net) {
   return net->plan.get();
 }
 
-void sync_slots(Plan& p) {
+void sync_slots(Plan& p, cudaStream_t st) {
   if (p.h_slots == p.h_slots_dev) return;
-  CUDA_CHECK(cudaMemcpyAsync(p.d_slots, p.h_slots.data(), p.h_slots.size() * sizeof(double*), cudaMemcpyHostToDevice,
-                             p.ctx->stream));
+  CUDA_CHECK(cudaMemcpyAsync(p.d_slots, p.h_slots.data(), p.h_slots.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
   p.h_slots_dev = p.h_slots;
 }
+
+void sync_slots(Plan& p) { sync_slots(p, p.ctx->stream); }
 
 void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB);
 
@@ -952,8 +976,32 @@ void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB
 }
 }  // namespace
 
-// shared with the batch module
+// shared with the batch and serving modules
 Plan* tnx_ensure_plan(tnx_network* net) { return ensure_plan(net); }
+
+// One apply of the network into `out`, enqueued on `st` (a CUDA graph when
+// graphs are on and st is not the legacy default stream).
+void tnx_apply_enqueue(tnx_network* net, tnx_tensor* out, cudaStream_t st) {
+  Plan* p = ensure_plan(net);
+  check_out_bonds(*p, out);
+  bind_inputs(net, *p);
+  p->h_slots[p->out_slot] = out->data;
+  sync_slots(*p, st);
+  tnx_ctx* c = net->ctx;
+  if (st != nullptr && c->use_graphs) {
+    if (!p->apply_graph || p->apply_graph->prof != c->prof) {
+      p->apply_graph.reset(new GraphRec());
+      capture_graph(c, st, *p->apply_graph, [&] { enqueue_plan(*p, st); });
+    }
+    CUDA_CHECK(cudaGraphLaunch(p->apply_graph->exec, st));
+    if (c->prof) {
+      CUDA_CHECK(cudaStreamSynchronize(st));
+      prof_accumulate(c, p->apply_graph->recs);
+    }
+  } else {
+    enqueue_plan(*p, st);
+  }
+}
 void tnx_bind_inputs(tnx_network* net, Plan& p) { bind_inputs(net, p); }
 void tnx_check_out_bonds(const Plan& p, const tnx_tensor* out) { check_out_bonds(p, out); }
 void tnx_capture_graph(tnx_ctx* c, cudaStream_t st, GraphRec& g, const std::function<void()>& body) {
@@ -1099,25 +1147,7 @@ extern "C" tnx_status tnx_network_launch_into(tnx_network* net, tnx_tensor* out)
   if (!net) return TNX_ERR_ARG;
   return tnx_guard(net->ctx, [&] {
     if (!out) fail(TNX_ERR_ARG, "null output");
-    Plan* p = ensure_plan(net);
-    check_out_bonds(*p, out);
-    bind_inputs(net, *p);
-    p->h_slots[p->out_slot] = out->data;
-    sync_slots(*p);
-    tnx_ctx* c = net->ctx;
-    if (graphs_enabled(c)) {
-      if (!p->apply_graph || p->apply_graph->prof != c->prof) {
-        p->apply_graph.reset(new GraphRec());
-        capture_graph(c, c->stream, *p->apply_graph, [&] { enqueue_plan(*p, c->stream); });
-      }
-      CUDA_CHECK(cudaGraphLaunch(p->apply_graph->exec, c->stream));
-      if (c->prof) {
-        CUDA_CHECK(cudaStreamSynchronize(c->stream));
-        prof_accumulate(c, p->apply_graph->recs);
-      }
-    } else {
-      enqueue_plan(*p, c->stream);
-    }
+    tnx_apply_enqueue(net, out, net->ctx->stream);
   });
 }
 
@@ -1192,99 +1222,128 @@ struct LanczosCache {
 
 tnx_network::~tnx_network() = default;
 
+// A whole Lanczos solve enqueued on `st`; at its end the eigenvalue and the
+// number of matvecs are copied to host_out[0] (double) and host_out[1] (int32
+// in its first four bytes), which must be pinned host memory.  No sync.
+void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps, tnx_tensor* evec, cudaStream_t st,
+                         double* host_out) {
+  tnx_ctx* ctx = net->ctx;
+  NetTensor& vt = net->ts[slot];
+  if (!vt.t) {
+    vt.t = v0;
+    vt.perm.assign(v0->rank, 0);
+    std::iota(vt.perm.begin(), vt.perm.end(), 0);
+  }
+  for (int j = 0; j < (int)vt.perm.size(); ++j)
+    if (vt.perm[j] != j) fail(TNX_ERR_NETWORK, "the vector slot must be put in blueprint leg order");
+  if (v0->bonds != vt.t->bonds) fail(TNX_ERR_BOND_MISMATCH, "v0 bonds differ from the vector slot's bonds");
+  Plan* p = ensure_plan(net);
+  if (p->out_bonds != v0->bonds) fail(TNX_ERR_BOND_MISMATCH, "the operator's output bonds differ from the vector's");
+  if (evec) check_out_bonds(*p, evec);
+  const int64_t n = v0->nelem;
+  std::unique_ptr<LanczosCache>& lc = net->lanczos;
+  if (!lc || lc->plan_serial != p->serial || lc->nsteps != nsteps || lc->n != n || lc->slot != slot) {
+    lc.reset(new LanczosCache());
+    lc->plan_serial = p->serial;
+    lc->nsteps = nsteps;
+    lc->n = n;
+    lc->slot = slot;
+    LanczosDev& L = lc->L;
+    memset(&L, 0, sizeof(L));
+    L.n = n;
+    L.nmax = nsteps;
+    L.nblocks = tnx_reduce_blocks(n);
+    auto dev = [&](size_t bytes) {
+      lc->bufs.emplace_back(new DevBuf(ctx, std::max<size_t>(bytes, 256)));
+      CUDA_CHECK(cudaMemsetAsync(lc->bufs.back()->p, 0, std::max<size_t>(bytes, 256), st));
+      return lc->bufs.back()->p;
+    };
+    L.V = (double*)dev((size_t)(nsteps + 1) * n * 8);
+    L.w = (double*)dev((size_t)n * 8);
+    L.alpha = (double*)dev((size_t)(nsteps + 1) * 8);
+    L.beta = (double*)dev((size_t)(nsteps + 2) * 8);
+    L.coef = (double*)dev((size_t)(nsteps + 2) * 8);
+    L.partial = (double*)dev((size_t)std::max<int64_t>(1216, (int64_t)608 * (nsteps + 2)) * 8);
+    L.y = (double*)dev((size_t)(nsteps + 1) * 8);
+    L.scratch = (double*)dev((size_t)(4 * (nsteps + 1)) * 8);
+    L.state = (int32_t*)dev(64);
+    L.eval = (double*)dev(64);
+  }
+  LanczosDev& L = lc->L;
+  bind_inputs(net, *p);
+  p->h_slots[p->out_slot] = L.w;
+  sync_slots(*p, st);
+  double* evp = evec ? evec->data : nullptr;
+  // apply 0 prepares every operand; later applies only those fed by the vector
+  const uint64_t fixed = ~((uint64_t)1 << slot);
+  auto body = [&] {
+    {
+      ProfScope ps(ctx, st, TNX_KC_VECTOR, 24.0 * (double)n);
+      CUDA_CHECK(tnx_launch_lanczos_init(L, v0->data, st));
+    }
+    for (int j = 0; j < nsteps; ++j) {
+      CUDA_CHECK(tnx_launch_lanczos_set_input(p->d_slots + slot, L, j, st));
+      enqueue_plan(*p, st, j == 0 ? 0 : fixed);
+      // bytes of one step: two Gram-Schmidt passes over j+1 vectors (dots
+      // (j+1)n + n, update (j+1)n + 2n), norm folded in, scale (2n)
+      ProfScope ps(ctx, st, TNX_KC_VECTOR, 8.0 * (double)n * (2 * (2.0 * (j + 1) + 3) + 2));
+      CUDA_CHECK(tnx_launch_lanczos_step(L, j, st));
+    }
+    ProfScope ps(ctx, st, TNX_KC_VECTOR, evp ? 8.0 * (double)n * (nsteps + 2) : 0.0);
+    CUDA_CHECK(tnx_launch_lanczos_finish(L, evp, st));
+  };
+  if (st != nullptr && ctx->use_graphs) {
+    if (!lc->graph || lc->v0 != v0->data || lc->evec != evp || lc->graph->prof != ctx->prof) {
+      lc->graph.reset(new GraphRec());
+      lc->v0 = v0->data;
+      lc->evec = evp;
+      capture_graph(ctx, st, *lc->graph, body);
+    }
+    CUDA_CHECK(cudaGraphLaunch(lc->graph->exec, st));
+  } else {
+    body();
+  }
+  // the device slot of the vector now points into L.V: restore the table next time
+  p->h_slots_dev.assign(p->h_slots.size(), nullptr);
+  CUDA_CHECK(cudaMemcpyAsync(host_out, L.eval, 8, cudaMemcpyDeviceToHost, st));
+  CUDA_CHECK(cudaMemcpyAsync(host_out + 1, L.state, 8, cudaMemcpyDeviceToHost, st));
+}
+
+// Device bytes held by the network's plan and Lanczos workspace.
+size_t tnx_network_resident_bytes(tnx_network* net) {
+  size_t b = 0;
+  if (net->plan)
+    for (auto& d : net->plan->bufs) b += d->bytes;
+  if (net->lanczos)
+    for (auto& d : net->lanczos->bufs) b += d->bytes;
+  return b;
+}
+
+// Frees the plan and the Lanczos workspace (rebuilt on the next use).  The
+// caller guarantees nothing of this network is in flight.
+void tnx_network_evict(tnx_network* net) {
+  net->lanczos.reset();
+  net->plan.reset();
+}
+
+int tnx_network_slot(tnx_network* net, const char* name) {
+  for (size_t i = 0; i < net->ts.size(); ++i)
+    if (net->ts[i].name == name) return (int)i;
+  return -1;
+}
+
 extern "C" tnx_status tnx_lanczos(tnx_network* net, const char* vec_slot, tnx_tensor* v0, int nsteps, double* eval,
                                   tnx_tensor* evec, int* nmatvec) {
   if (!net) return TNX_ERR_ARG;
   return tnx_guard(net->ctx, [&] {
     tnx_ctx* ctx = net->ctx;
     if (!vec_slot || !v0 || !eval || nsteps < 1 || nsteps > 500) fail(TNX_ERR_ARG, "bad Lanczos arguments");
-    int slot = -1;
-    for (size_t i = 0; i < net->ts.size(); ++i)
-      if (net->ts[i].name == vec_slot) slot = (int)i;
+    const int slot = tnx_network_slot(net, vec_slot);
     if (slot < 0) fail(TNX_ERR_NETWORK, std::string("no tensor named '") + vec_slot + "'");
-    NetTensor& vt = net->ts[slot];
-    if (!vt.t) {
-      vt.t = v0;
-      vt.perm.assign(v0->rank, 0);
-      std::iota(vt.perm.begin(), vt.perm.end(), 0);
-    }
-    for (int j = 0; j < (int)vt.perm.size(); ++j)
-      if (vt.perm[j] != j) fail(TNX_ERR_NETWORK, "the vector slot must be put in blueprint leg order");
-    if (v0->bonds != vt.t->bonds) fail(TNX_ERR_BOND_MISMATCH, "v0 bonds differ from the vector slot's bonds");
-    Plan* p = ensure_plan(net);
-    if (p->out_bonds != v0->bonds) fail(TNX_ERR_BOND_MISMATCH, "the operator's output bonds differ from the vector's");
-    if (evec) check_out_bonds(*p, evec);
-    const int64_t n = v0->nelem;
-    std::unique_ptr<LanczosCache>& lc = net->lanczos;
-    if (!lc || lc->plan_serial != p->serial || lc->nsteps != nsteps || lc->n != n || lc->slot != slot) {
-      lc.reset(new LanczosCache());
-      lc->plan_serial = p->serial;
-      lc->nsteps = nsteps;
-      lc->n = n;
-      lc->slot = slot;
-      LanczosDev& L = lc->L;
-      memset(&L, 0, sizeof(L));
-      L.n = n;
-      L.nmax = nsteps;
-      L.nblocks = tnx_reduce_blocks(n);
-      auto dev = [&](size_t bytes) {
-        lc->bufs.emplace_back(new DevBuf(ctx, std::max<size_t>(bytes, 256)));
-        CUDA_CHECK(cudaMemsetAsync(lc->bufs.back()->p, 0, std::max<size_t>(bytes, 256), ctx->stream));
-        return lc->bufs.back()->p;
-      };
-      L.V = (double*)dev((size_t)(nsteps + 1) * n * 8);
-      L.w = (double*)dev((size_t)n * 8);
-      L.alpha = (double*)dev((size_t)(nsteps + 1) * 8);
-      L.beta = (double*)dev((size_t)(nsteps + 2) * 8);
-      L.coef = (double*)dev((size_t)(nsteps + 2) * 8);
-      L.partial = (double*)dev((size_t)std::max<int64_t>(1216, (int64_t)152 * (nsteps + 2)) * 8);
-      L.y = (double*)dev((size_t)(nsteps + 1) * 8);
-      L.scratch = (double*)dev((size_t)(4 * (nsteps + 1)) * 8);
-      L.state = (int32_t*)dev(64);
-      L.eval = (double*)dev(64);
-    }
-    LanczosDev& L = lc->L;
-    bind_inputs(net, *p);
-    p->h_slots[p->out_slot] = L.w;
-    sync_slots(*p);
-    cudaStream_t st = ctx->stream;
-    double* evp = evec ? evec->data : nullptr;
-    // apply 0 prepares every operand; later applies only those fed by the vector
-    const uint64_t fixed = ~((uint64_t)1 << slot);
-    auto body = [&] {
-      {
-        ProfScope ps(ctx, st, TNX_KC_VECTOR, 24.0 * (double)n);
-        CUDA_CHECK(tnx_launch_lanczos_init(L, v0->data, st));
-      }
-      for (int j = 0; j < nsteps; ++j) {
-        CUDA_CHECK(tnx_launch_lanczos_set_input(p->d_slots + slot, L, j, st));
-        enqueue_plan(*p, st, j == 0 ? 0 : fixed);
-        // bytes of one step: alpha dot (2n), axpy (3n+n), 2 x Gram-Schmidt over
-        // j+1 vectors (dots (j+1)n + n, update (j+1)n + 2n), norm (n), scale (2n)
-        ProfScope ps(ctx, st, TNX_KC_VECTOR, 8.0 * (double)n * (2 + 4 + 2 * (2.0 * (j + 1) + 3) + 1 + 2));
-        CUDA_CHECK(tnx_launch_lanczos_step(L, j, st));
-      }
-      ProfScope ps(ctx, st, TNX_KC_VECTOR, evp ? 8.0 * (double)n * (nsteps + 2) : 0.0);
-      CUDA_CHECK(tnx_launch_lanczos_finish(L, evp, st));
-    };
-    if (graphs_enabled(ctx)) {
-      if (!lc->graph || lc->v0 != v0->data || lc->evec != evp || lc->graph->prof != ctx->prof) {
-        lc->graph.reset(new GraphRec());
-        lc->v0 = v0->data;
-        lc->evec = evp;
-        capture_graph(ctx, st, *lc->graph, body);
-      }
-      CUDA_CHECK(cudaGraphLaunch(lc->graph->exec, st));
-    } else {
-      body();
-    }
-    // the device slot of the vector now points into L.V: restore the table next time
-    p->h_slots_dev.assign(p->h_slots.size(), nullptr);
     double* hp = (double*)ctx->pinned;
-    CUDA_CHECK(cudaMemcpyAsync(hp, L.eval, 8, cudaMemcpyDeviceToHost, st));
-    CUDA_CHECK(cudaMemcpyAsync(hp + 1, L.state, 8, cudaMemcpyDeviceToHost, st));
-    CUDA_CHECK(cudaStreamSynchronize(st));
-    if (graphs_enabled(ctx) && ctx->prof) prof_accumulate(ctx, lc->graph->recs);
+    tnx_lanczos_enqueue(net, slot, v0, nsteps, evec, ctx->stream, hp);
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->stream && ctx->use_graphs && ctx->prof) prof_accumulate(ctx, net->lanczos->graph->recs);
     check_device_status(ctx);
     *eval = hp[0];
     if (nmatvec) *nmatvec = ((int32_t*)(hp + 1))[0];

@@ -155,3 +155,12 @@ void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool n
 
 // relayout chunks (tnx_network.cpp)
 void tnx_make_copy_chunks(const std::vector<CopyTask>& tasks, std::vector<int4>& chunks);
+
+// enqueue helpers shared by the C-ABI, the batch and the serving modules (tnx_network.cpp)
+Plan* tnx_ensure_plan(tnx_network* net);
+void tnx_apply_enqueue(tnx_network* net, tnx_tensor* out, cudaStream_t st);
+void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps, tnx_tensor* evec, cudaStream_t st,
+                         double* host_out);
+int tnx_network_slot(tnx_network* net, const char* name);
+size_t tnx_network_resident_bytes(tnx_network* net);
+void tnx_network_evict(tnx_network* net);
