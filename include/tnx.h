@@ -324,7 +324,7 @@ tnx_status tnx_match_tables_noalloc(void* stream, int nsym, const int32_t* zn, i
 
 /* Kernel classes timed by the profiler. */
 enum { TNX_KC_MATCH = 0, TNX_KC_RELAYOUT = 1, TNX_KC_GEMM = 2, TNX_KC_SLICE = 3, TNX_KC_VECTOR = 4,
-       TNX_KC_FINAL = 5, TNX_KC_COUNT = 6 };
+       TNX_KC_FINAL = 5, TNX_KC_SKINNY = 6, TNX_KC_COUNT = 7 };
 
 /* enable != 0: bracket every kernel class a launch enqueues on the context
  * stream with CUDA events (adds two event records per launch); 0 stops.
@@ -333,8 +333,10 @@ tnx_status tnx_profile_enable(tnx_ctx* ctx, int enable);
 /* Synchronises the stream and returns, per kernel class (arrays of
  * TNX_KC_COUNT entries, any may be NULL): summed device milliseconds, number
  * of launches, and the algorithmic work of those launches (useful flops for
- * TNX_KC_GEMM: 2*m*k*n over matched block pairs; bytes read + written for the
- * relayout and slice classes, each element counted once per direction). */
+ * TNX_KC_GEMM (the main grouped product: split tensor-core or FP64) and
+ * TNX_KC_SKINNY (the K <= 16 FP64 products): 2*m*k*n over matched block pairs;
+ * bytes read + written for the relayout and slice classes, each element counted
+ * once per direction). */
 tnx_status tnx_profile_read(tnx_ctx* ctx, double* ms, int64_t* launches, double* work);
 /* Number of CUDA kernels this library has launched in the process so far. */
 tnx_status tnx_kernel_launches(int64_t* n);

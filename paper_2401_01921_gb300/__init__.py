@@ -102,7 +102,7 @@ _SIGS = {
     "tnx_profile_read": (C.c_int, [_p, C.POINTER(C.c_double), _i64p, C.POINTER(C.c_double)]),
     "tnx_kernel_launches": (C.c_int, [_i64p]),
 }
-KERNEL_CLASSES = ["match", "relayout", "gemm", "slice", "vector", "final"]
+KERNEL_CLASSES = ["match", "relayout", "gemm", "slice", "vector", "final", "skinny"]
 
 
 def lib() -> C.CDLL:

@@ -74,10 +74,11 @@ __device__ void copy_transpose(const CopyTask& t, int tile, double* const* __res
   }
 }
 
-// Element e of a task: decompose the in-task index over the legs (last leg
-// fastest) into source and destination offsets.
-__device__ __forceinline__ void copy_one(const CopyTask& t, const double* src, double* dst, int i) {
-  int64_t so = 0, dof = 0;
+// Source / destination offsets of in-task element i: decompose i over the
+// legs (last leg fastest).
+__device__ __forceinline__ void offsets(const CopyTask& t, int i, int64_t& so, int64_t& dof) {
+  so = 0;
+  dof = 0;
 #pragma unroll
   for (int l = TNX_MAXR - 1; l >= 0; --l) {
     if (l < t.rank) {
@@ -89,14 +90,46 @@ __device__ __forceinline__ void copy_one(const CopyTask& t, const double* src, d
       dof += rem * t.dstride[l];
     }
   }
-  dst[dof] = src ? __ldg(src + so) : 0.0;
+}
+
+// Elements [e0, e0 + n) of one task (n <= EPT): one decomposition, then steps
+// along the innermost leg; a carry into the next leg re-decomposes.
+constexpr int EPT = 4;
+
+__device__ __forceinline__ void copy_run(const CopyTask& t, const double* src, double* dst, int e0, int n) {
+  int64_t so, dof;
+  offsets(t, e0, so, dof);
+  const int last = t.rank - 1;
+  const int ext = t.shape[last];
+  int pos = e0 % ext;
+  const int64_t ss = t.sstride[last], ds = t.dstride[last];
+  double v[EPT];
+  int64_t d[EPT];
+#pragma unroll
+  for (int j = 0; j < EPT; ++j) {
+    if (j < n) {
+      v[j] = src ? __ldg(src + so) : 0.0;
+      d[j] = dof;
+      if (++pos == ext) {
+        pos = 0;
+        offsets(t, e0 + j + 1, so, dof);
+      } else {
+        so += ss;
+        dof += ds;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < EPT; ++j)
+    if (j < n) dst[d[j]] = v[j];
 }
 
 // chunk = (first task, first element, number of tasks, number of elements).
-// One task: its elements [first, first + count).  Several (small) tasks: all
-// their elements, back to back; the chunk's descriptors are staged in shared
-// memory and each thread finds its task by binary search over their starts.
-// A negative task count marks one 32 x 32 tile of a transposing task.
+// One task: its elements [first, first + count), EPT consecutive ones per
+// thread.  Several (small) tasks: all their elements, back to back; the
+// chunk's descriptors are staged in shared memory and each thread finds its
+// task by binary search over their starts.  A negative task count marks one
+// 32 x 32 tile of a transposing task.
 __global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ tasks, const int4* __restrict__ chunks,
                                                   double* const* __restrict__ slots) {
   __shared__ CopyTask st[TNX_COPY_PACK];
@@ -110,7 +143,8 @@ __global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ t
     const CopyTask& t = tasks[ch.x];
     const double* src = t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr;
     double* dst = slots[t.dst_slot] + t.dst_off;
-    for (int e = ch.y + threadIdx.x; e < ch.y + ch.w; e += CT) copy_one(t, src, dst, e);
+    const int end = ch.y + ch.w;
+    for (int e = ch.y + threadIdx.x * EPT; e < end; e += CT * EPT) copy_run(t, src, dst, e, min(EPT, end - e));
     return;
   }
   // several small tasks
@@ -139,7 +173,9 @@ __global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ t
     }
     const CopyTask& t = st[lo];
     const double* src = t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr;
-    copy_one(t, src, slots[t.dst_slot] + t.dst_off, e - sstart[lo]);
+    int64_t so, dof;
+    offsets(t, e - sstart[lo], so, dof);
+    slots[t.dst_slot][t.dst_off + dof] = src ? __ldg(src + so) : 0.0;
   }
 }
 

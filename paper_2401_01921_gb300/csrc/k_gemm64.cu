@@ -77,6 +77,25 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmGroup* __restrict__
 // MPO steps of H_eff (K, N ~ 10), where a square tile would be mostly padding.
 constexpr int SK_MAXK = 16;
 
+// KB = K rounded up to a multiple of 4: the FMA loop runs over KB entries only
+// (the MPO steps have K of 1..10, and FP64 FMAs are the scarce resource).
+template <int KB>
+__device__ __forceinline__ void skinny_rows(const GemmGroup& g, const GemmTile& tl, const double* A, double* C,
+                                            const double (*Bs)[SK_MAXK], int nn) {
+  const int m = tl.m0 + threadIdx.x;
+  if (m >= g.M) return;
+  double a[KB];
+#pragma unroll
+  for (int k = 0; k < KB; ++k) a[k] = k < g.K ? A[(int64_t)m * g.lda + k] : 0.0;
+  double* crow = C + (int64_t)m * g.ldc + tl.n0;
+  for (int n = 0; n < nn; ++n) {
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < KB; ++k) acc = fma(a[k], Bs[n][k], acc);
+    crow[n] = acc;
+  }
+}
+
 __global__ void __launch_bounds__(128) gemm_skinny_kernel(const GemmGroup* __restrict__ groups,
                                                           const GemmTile* __restrict__ tiles,
                                                           double* const* __restrict__ slots) {
@@ -92,17 +111,11 @@ __global__ void __launch_bounds__(128) gemm_skinny_kernel(const GemmGroup* __res
     Bs[n][k] = (n < nn && k < g.K) ? B[(int64_t)(tl.n0 + n) * g.ldb + k] : 0.0;
   }
   __syncthreads();
-  const int m = tl.m0 + threadIdx.x;
-  if (m >= g.M) return;
-  double a[SK_MAXK];
-#pragma unroll
-  for (int k = 0; k < SK_MAXK; ++k) a[k] = k < g.K ? A[(int64_t)m * g.lda + k] : 0.0;
-  double* crow = C + (int64_t)m * g.ldc + tl.n0;
-  for (int n = 0; n < nn; ++n) {
-    double acc = 0.0;
-#pragma unroll
-    for (int k = 0; k < SK_MAXK; ++k) acc = fma(a[k], Bs[n][k], acc);
-    crow[n] = acc;
+  switch ((g.K + 3) >> 2) {
+    case 1: skinny_rows<4>(g, tl, A, C, Bs, nn); break;
+    case 2: skinny_rows<8>(g, tl, A, C, Bs, nn); break;
+    case 3: skinny_rows<12>(g, tl, A, C, Bs, nn); break;
+    default: skinny_rows<16>(g, tl, A, C, Bs, nn); break;
   }
 }
 

@@ -89,7 +89,7 @@ void enqueue_batch(tnx_batch& B, cudaStream_t st) {
       CUDA_CHECK(tnx_launch_copy(s.B.d, s.B.chunks, s.B.nchunks, B.d_slots, st));
     }
     if (s.nts) {
-      ProfScope ps(c, st, TNX_KC_GEMM, s.flops_skinny);
+      ProfScope ps(c, st, TNX_KC_SKINNY, s.flops_skinny);
       CUDA_CHECK(tnx_launch_gemm_skinny(s.dG, s.dTs, s.nts, B.d_slots, st));
     }
     if (B.prec == TNX_PREC_F64 || B.prec == TNX_PREC_F32) {

@@ -912,7 +912,7 @@ void enqueue_plan(Plan& p, cudaStream_t st, uint64_t fixed = 0) {
       if (needB) CUDA_CHECK(tnx_launch_copy(s.copyB.d, s.copyB.chunks, s.copyB.nchunks, p.d_slots, st));
     }
     if (s.nstiles_skinny) {
-      ProfScope ps(c, st, TNX_KC_GEMM, s.flops_skinny);
+      ProfScope ps(c, st, TNX_KC_SKINNY, s.flops_skinny);
       CUDA_CHECK(tnx_launch_gemm_skinny(s.dG, s.dTs, s.nstiles_skinny, p.d_slots, st));
     }
     switch (p.prec) {
