@@ -16,12 +16,19 @@
 // whenever the source is contiguous along the same leg.  When the source is
 // contiguous along another leg, the task is moved in 32 x 32 tiles staged
 // through shared memory instead, so both sides coalesce.  Index arithmetic is
-// 32-bit inside a task.
+// 32-bit inside a task, and an index is split over the legs with
+// multiply-high divisions by the leg extents (constants the planner
+// precomputes) instead of hardware integer divisions.
 #include "tnx_internal.h"
 
 namespace {
 
 constexpr int CT = 256;
+
+// floor(n / shape[l]) for 0 <= n < 2^31 from the task's precomputed constants
+__device__ __forceinline__ int fdiv(int n, uint32_t magic, uint32_t shift) {
+  return magic ? (int)(__umulhi((uint32_t)n, magic) >> shift) : n;
+}
 
 // Transposing task: the source is contiguous along leg S = t.tleg, the
 // destination along the last leg.  View the block as a matrix with one column
@@ -39,12 +46,12 @@ __device__ void copy_transpose(const CopyTask& t, int tile, double* const* __res
   const double* src = t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr;
   double* dst = slots[t.dst_slot] + t.dst_off;
   // row index -> (source offset, destination offset) over the legs other than S
-  auto bases = [&](int row, int64_t& so, int64_t& dof) {
+  auto bases = [&](int row, int& so, int& dof) {
     so = 0;
     dof = 0;
     for (int l = r - 1; l >= 0; --l) {
       if (l == S) continue;
-      const int q = row / t.shape[l];
+      const int q = fdiv(row, t.magic[l], t.shift[l]);
       const int rem = row - q * t.shape[l];
       row = q;
       so += rem * t.sstride[l];
@@ -56,35 +63,34 @@ __device__ void copy_transpose(const CopyTask& t, int tile, double* const* __res
   for (int i = 0; i < 4; ++i) {
     const int rr = wid + 8 * i, row = r0 + rr;
     if (row < nrows && c < ncols) {
-      int64_t so, dof;
+      int so, dof;
       bases(row, so, dof);
-      sm[rr][lane] = src ? __ldg(src + so + (int64_t)c * t.sstride[S]) : 0.0;
+      sm[rr][lane] = src ? __ldg(src + so + c * t.sstride[S]) : 0.0;
     }
   }
   __syncthreads();
   const int row = r0 + lane;
   if (row < nrows) {
-    int64_t so, dof;
+    int so, dof;
     bases(row, so, dof);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int cc = wid + 8 * i, col = c0 + cc;
-      if (col < ncols) dst[dof + (int64_t)col * t.dstride[S]] = sm[lane][cc];
+      if (col < ncols) dst[dof + col * t.dstride[S]] = sm[lane][cc];
     }
   }
 }
 
 // Source / destination offsets of in-task element i: decompose i over the
 // legs (last leg fastest).
-__device__ __forceinline__ void offsets(const CopyTask& t, int i, int64_t& so, int64_t& dof) {
+__device__ __forceinline__ void offsets(const CopyTask& t, int i, int& so, int& dof) {
   so = 0;
   dof = 0;
 #pragma unroll
   for (int l = TNX_MAXR - 1; l >= 0; --l) {
     if (l < t.rank) {
-      const int sh = t.shape[l];
-      const int q = i / sh;
-      const int rem = i - q * sh;
+      const int q = fdiv(i, t.magic[l], t.shift[l]);
+      const int rem = i - q * t.shape[l];
       i = q;
       so += rem * t.sstride[l];
       dof += rem * t.dstride[l];
@@ -97,14 +103,14 @@ __device__ __forceinline__ void offsets(const CopyTask& t, int i, int64_t& so, i
 constexpr int EPT = 4;
 
 __device__ __forceinline__ void copy_run(const CopyTask& t, const double* src, double* dst, int e0, int n) {
-  int64_t so, dof;
+  int so, dof;
   offsets(t, e0, so, dof);
   const int last = t.rank - 1;
   const int ext = t.shape[last];
-  int pos = e0 % ext;
-  const int64_t ss = t.sstride[last], ds = t.dstride[last];
+  int pos = e0 - fdiv(e0, t.magic[last], t.shift[last]) * ext;
+  const int ss = t.sstride[last], ds = t.dstride[last];
   double v[EPT];
-  int64_t d[EPT];
+  int d[EPT];
 #pragma unroll
   for (int j = 0; j < EPT; ++j) {
     if (j < n) {
@@ -140,7 +146,13 @@ __global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ t
     return;
   }
   if (ch.z == 1) {
-    const CopyTask& t = tasks[ch.x];
+    {
+      const int* g = (const int*)(tasks + ch.x);
+      int* sm = (int*)st;
+      for (int i = threadIdx.x; i < (int)(sizeof(CopyTask) / 4); i += CT) sm[i] = g[i];
+    }
+    __syncthreads();
+    const CopyTask& t = st[0];
     const double* src = t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr;
     double* dst = slots[t.dst_slot] + t.dst_off;
     const int end = ch.y + ch.w;
@@ -173,7 +185,7 @@ __global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ t
     }
     const CopyTask& t = st[lo];
     const double* src = t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr;
-    int64_t so, dof;
+    int so, dof;
     offsets(t, e - sstart[lo], so, dof);
     slots[t.dst_slot][t.dst_off + dof] = src ? __ldg(src + so) : 0.0;
   }

@@ -26,10 +26,11 @@
 // row / column maximum and the dropped levels: about 2^-40 relative to
 // max|row| * max|col| * K.
 //
-// Kernel layout: 128 x 64 output tiles, 6 warps per CTA: warp 0 issues the
+// Kernel layout: 128 x 64 output tiles, 10 warps per CTA: warp 0 issues the
 // bulk copies (the TMA engine, cp.async.bulk) of pre-tiled slices into a
 // 3-stage shared-memory ring, warp 1 issues tcgen05.mma (one elected lane),
-// warps 2-5 drain tensor memory (tcgen05.ld) into the integer accumulators
+// warps 2-9 (two per quarter of the TMEM lanes, each taking half of the
+// tile's columns) drain tensor memory (tcgen05.ld) into the integer accumulators
 // and write FP64.  Operands sit in global memory already in the canonical
 // no-swizzle K-major core-matrix layout, so a stage is one contiguous copy.
 // Every wait on an mbarrier is bounded (about a second of clock); a wait that
@@ -50,6 +51,9 @@ constexpr int MAXN = 6;            // slices
 constexpr int ATILE = TM * TK * 2; // bytes of one A slice tile (8 KB)
 constexpr int BTILE = TN * TK * 2; // bytes of one B slice tile (4 KB)
 constexpr long long WAIT_LIMIT = 2000000000LL;   // clock cycles (~1 s)
+constexpr int EPI_WARPS = 8;       // epilogue warps: two per TMEM lane quarter
+constexpr int ECOLS = TN / 2;      // tile columns per epilogue warp
+constexpr int SPLIT_THREADS = 32 * (2 + EPI_WARPS);
 
 // ------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -159,14 +163,6 @@ __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
@@ -298,7 +294,7 @@ struct SplitShared {
 // and the epilogue warps continue across tiles, so the producer streams the
 // next tile's slices while the epilogue drains the current one.
 template <int NS>
-__global__ void __launch_bounds__(192, 1) split_gemm_kernel(const SplitGroup* __restrict__ groups,
+__global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const SplitGroup* __restrict__ groups,
                                                              const GemmTile* __restrict__ tiles, int ntiles, int beta,
                                                              int f16, double* const* __restrict__ slots,
                                                              int32_t* status) {
@@ -306,6 +302,8 @@ __global__ void __launch_bounds__(192, 1) split_gemm_kernel(const SplitGroup* __
   unsigned char* ring = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int STAGE_BYTES = NS * (ATILE + BTILE);
   SplitShared* sh = (SplitShared*)(ring + STAGES * STAGE_BYTES);
+  double (*sh_stage)[4] = (double (*)[4])(ring + STAGES * STAGE_BYTES + ((sizeof(SplitShared) + 15) & ~(size_t)15));
+  int* sh_ebc = (int*)(sh_stage + EPI_WARPS * 32);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int KTPC = KC / TK;   // K tiles per exact chunk
 
@@ -315,7 +313,7 @@ __global__ void __launch_bounds__(192, 1) split_gemm_kernel(const SplitGroup* __
       mbar_init(&sh->empty[s], 1);
     }
     mbar_init(&sh->accfull, 1);
-    mbar_init(&sh->accempty, 4);
+    mbar_init(&sh->accempty, EPI_WARPS);
     mbar_init(&sh->done, 1);
     sh->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -415,8 +413,10 @@ __global__ void __launch_bounds__(192, 1) split_gemm_kernel(const SplitGroup* __
       }
     }
   } else {
-    // ---------------- epilogue: warps 2..5, TMEM lanes 32*(warp%4) ..
+    // ---------------- epilogue: warps 2..9; warp w reads TMEM lanes 32*(w%4) ..
+    // (rows of the tile) and one half of the tile's columns
     const int sub = warp & 3;
+    const int cb = ((warp - 2) >> 2) * ECOLS;
     int chunk = 0;
     bool ok = true;
     for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
@@ -425,9 +425,19 @@ __global__ void __launch_bounds__(192, 1) split_gemm_kernel(const SplitGroup* __
       const int KT = (gr.K + TK - 1) / TK;
       const int nchunks = (KT + KTPC - 1) / KTPC;
       const int row = tl.m0 + sub * 32 + lane;
-      long long acc[TN];
+      // Row and column exponents are fetched before the first accumulator
+      // wait, so their global-load latency hides behind the MMAs.
+      double (*stg)[4] = sh_stage + (warp - 2) * 32;
+      int* ebc_s = sh_ebc + (warp - 2) * ECOLS;
+      const int eb_r = row < gr.M ? ((const int32_t*)slots[gr.ea_slot])[gr.ea_off + row] : 0;
+      {
+        const int32_t* eb_c = (const int32_t*)slots[gr.eb_slot] + gr.eb_off;
+        const int col = tl.n0 + cb + lane;
+        ebc_s[lane] = col < gr.N ? eb_c[col] : 0;
+      }
+      long long acc[ECOLS];
 #pragma unroll
-      for (int c = 0; c < TN; ++c) acc[c] = 0;
+      for (int c = 0; c < ECOLS; ++c) acc[c] = 0;
       for (int ch = 0; ch < nchunks; ++ch, ++chunk) {
         if (!mbar_wait(&sh->accfull, (uint32_t)chunk & 1u, status, 14, abort_flag)) {
           ok = false;
@@ -436,10 +446,11 @@ __global__ void __launch_bounds__(192, 1) split_gemm_kernel(const SplitGroup* __
         tc_fence_after();
         // all levels of 8 columns in flight at once, one wait per column group
 #pragma unroll
-        for (int cg = 0; cg < TN / 8; ++cg) {
+        for (int cg = 0; cg < ECOLS / 8; ++cg) {
           uint32_t v[NS][8];
 #pragma unroll
-          for (int t = 0; t < NS; ++t) tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(t * TN + cg * 8), v[t]);
+          for (int t = 0; t < NS; ++t)
+            tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(t * TN + cb + cg * 8), v[t]);
           tmem_wait_ld();
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
@@ -453,17 +464,30 @@ __global__ void __launch_bounds__(192, 1) split_gemm_kernel(const SplitGroup* __
         tc_fence_before();
         if (lane == 0) mbar_arrive(&sh->accempty);
       }
-      if (ok && row < gr.M) {
-        const int eb_r = ((const int32_t*)slots[gr.ea_slot])[gr.ea_off + row];
-        double* crow = slots[gr.c_slot] + gr.c_off + (int64_t)row * gr.ldc;
-        const int32_t* eb_c = (const int32_t*)slots[gr.eb_slot] + gr.eb_off;
+      if (ok) {
+        // Convert and write through a per-warp staging block of 32 rows x 4
+        // columns, so each store instruction covers whole 32-byte sectors of
+        // eight rows of C instead of one 8-byte word in each of 32 rows.
+        // Column c of row r sits at position c ^ ((r >> 2) & 3), which keeps
+        // the row-wise writes and the column-wise reads free of bank conflicts.
+        __syncwarp();
+        double* cbase = slots[gr.c_slot] + gr.c_off;
+        const int r0 = tl.m0 + sub * 32;
 #pragma unroll
-        for (int c = 0; c < TN; ++c) {
-          const int col = tl.n0 + c;
-          if (col < gr.N) {
-            const int e = eb_r + eb_c[col] - 2046 + 2 - beta * (NS + 1);
-            crow[col] = i64_scaled_to_double(acc[c], e);
+        for (int c4 = 0; c4 < ECOLS / 4; ++c4) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int e = eb_r + ebc_s[c4 * 4 + c] - 2046 + 2 - beta * (NS + 1);
+            stg[lane][c ^ ((lane >> 2) & 3)] = i64_scaled_to_double(acc[c4 * 4 + c], e);
           }
+          __syncwarp();
+          const int cc = lane & 3, col = tl.n0 + cb + c4 * 4 + cc;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int rr = q * 8 + (lane >> 2), r = r0 + rr;
+            if (r < gr.M && col < gr.N) cbase[(int64_t)r * gr.ldc + col] = stg[rr][cc ^ ((rr >> 2) & 3)];
+          }
+          __syncwarp();
         }
       }
     }
@@ -498,7 +522,10 @@ cudaError_t tnx_launch_slices(const SliceJob* jobs, const int64_t* warp_start, i
 }
 
 size_t tnx_split_smem_bytes(int nslice) {
-  return 1024 + (size_t)STAGES * nslice * (ATILE + BTILE) + sizeof(SplitShared) + 64;
+  // alignment slack + stage ring + barriers + epilogue staging (32 rows x 4 doubles
+  // per epilogue warp) + column exponents (ECOLS per epilogue warp)
+  return 1024 + (size_t)STAGES * nslice * (ATILE + BTILE) + ((sizeof(SplitShared) + 15) & ~(size_t)15) +
+         EPI_WARPS * 32 * 4 * sizeof(double) + EPI_WARPS * ECOLS * sizeof(int) + 64;
 }
 
 cudaError_t tnx_launch_gemm_split(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int nslice, int beta,
@@ -513,7 +540,7 @@ cudaError_t tnx_launch_gemm_split(const SplitGroup* groups, const GemmTile* tile
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  split_gemm_kernel<MAXN><<<grid, 192, smem, st>>>(groups, tiles, ntiles, beta, f16, slots, status);
+  split_gemm_kernel<MAXN><<<grid, SPLIT_THREADS, smem, st>>>(groups, tiles, ntiles, beta, f16, slots, status);
   tnx_note_launch(1);
   return cudaGetLastError();
 }

@@ -163,20 +163,29 @@ __global__ void __launch_bounds__(RT) gs_update_kernel(LanczosDev L, int m, int 
   }
 }
 
-// beta_{j+1} = sqrt(sum of the norm partials); decide stop; record k
-__global__ void __launch_bounds__(RT) lanczos_beta_decide_kernel(LanczosDev L, int j, int nb, int last) {
+// beta_{j+1} = sqrt(sum of the norm partials); decide stop; record k; point
+// the next apply's input slot at v_{j+1} (which the next kernel writes)
+__global__ void __launch_bounds__(RT) lanczos_beta_decide_kernel(LanczosDev L, int j, int nb, int last,
+                                                                 double** next_slot) {
   __shared__ double sh[32];
+  __shared__ double s_amax;
   if (stopped(L.state)) return;
   double acc = 0.0;
   for (int b = threadIdx.x; b < nb; b += RT) acc += L.partial[b];
+  if (threadIdx.x < 32) {
+    double amax = 0.0;
+    for (int i = threadIdx.x; i <= j; i += 32) amax = fmax(amax, fabs(L.alpha[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (threadIdx.x == 0) s_amax = amax;
+  }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) {
     const double beta = sqrt(acc);
     L.beta[j + 1] = beta;
-    double amax = 0.0;
-    for (int i = 0; i <= j; ++i) amax = fmax(amax, fabs(L.alpha[i]));
     L.state[0] = j + 1;
-    if (last || beta < 1e-14 * amax) L.state[1] = 1;
+    if (last || beta < 1e-14 * s_amax) L.state[1] = 1;
+    else *next_slot = L.V + (int64_t)(j + 1) * L.n;
   }
 }
 
@@ -342,7 +351,7 @@ cudaError_t tnx_launch_lanczos_set_input(double** slot_ptr, const LanczosDev& L,
 // alpha_j = <v_j, H v_j> and removes the three-term recurrence), the norm of
 // the result folded into the second update, then beta_{j+1}, the stopping
 // test and v_{j+1} = w / beta_{j+1}.
-cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, cudaStream_t st) {
+cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, double** next_slot, cudaStream_t st) {
   const int nb = grid_for(L.n);
   const int m = j + 1;
   for (int pass = 0; pass < 2; ++pass) {
@@ -353,7 +362,7 @@ cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, cudaStream_t st)
     gs_update_kernel<<<nb, RT, 0, st>>>(L, m, pass == 1);
     tnx_note_launch(1);
   }
-  lanczos_beta_decide_kernel<<<1, RT, 0, st>>>(L, j, nb, j == L.nmax - 1);
+  lanczos_beta_decide_kernel<<<1, RT, 0, st>>>(L, j, nb, j == L.nmax - 1, next_slot);
   tnx_note_launch(1);
   lanczos_normalize_kernel<<<nb, RT, 0, st>>>(L, j);
   tnx_note_launch(1);

@@ -18,14 +18,20 @@
 
 // One strided block copy.  Legs are ordered outer -> inner; the last leg is
 // the one contiguous in the destination.  src_slot < 0 writes zeros.
+// Offsets inside one task are 32-bit (the planner rejects blocks whose
+// element offsets reach 2^31); the slot offsets are 64-bit.  magic/shift
+// divide an index below 2^31 by shape[l] without a hardware division:
+// q = magic ? umulhi(n, magic) >> shift : n.
 struct CopyTask {
   int32_t src_slot, dst_slot;
   int32_t rank, tleg;         // tleg >= 0: transposing task, source contiguous along leg tleg
   int64_t src_off, dst_off;
   int64_t nelem;
   int32_t shape[TNX_MAXR];
-  int64_t sstride[TNX_MAXR];
-  int64_t dstride[TNX_MAXR];
+  uint32_t magic[TNX_MAXR];
+  int32_t sstride[TNX_MAXR];
+  int32_t dstride[TNX_MAXR];
+  uint8_t shift[TNX_MAXR];
 };
 
 // One dense product C[M,N] = A[M,K] * B[N,K]^T (both operands K-major, C row-major).
@@ -155,5 +161,5 @@ struct LanczosDev {
 };
 cudaError_t tnx_launch_lanczos_init(const LanczosDev& L, const double* v0, cudaStream_t st);
 cudaError_t tnx_launch_lanczos_set_input(double** slot_ptr, const LanczosDev& L, int j, cudaStream_t st);
-cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, cudaStream_t st);
+cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, double** next_slot, cudaStream_t st);
 cudaError_t tnx_launch_lanczos_finish(const LanczosDev& L, double* evec, cudaStream_t st);

@@ -307,12 +307,37 @@ void finish_task(CopyTask& t, std::vector<int64_t> shape, std::vector<int64_t> s
   if (sh2.size() > TNX_MAXR) fail(TNX_ERR_UNSUPPORTED, "block copy of rank above the limit");
   t.rank = (int)sh2.size();
   t.nelem = 1;
+  int64_t smax = 0, dmax = 0;
   for (size_t l = 0; l < sh2.size(); ++l) {
     if (sh2[l] > INT32_MAX) fail(TNX_ERR_UNSUPPORTED, "block extent above 2^31");
-    t.shape[l] = (int32_t)sh2[l];
-    t.sstride[l] = s2[l];
-    t.dstride[l] = d2[l];
+    smax += (sh2[l] - 1) * s2[l];
+    dmax += (sh2[l] - 1) * d2[l];
     t.nelem *= sh2[l];
+  }
+  if (t.nelem > INT32_MAX || smax > INT32_MAX || dmax > INT32_MAX)
+    fail(TNX_ERR_UNSUPPORTED, "block relayout with element offsets above 2^31");
+  for (int l = 0; l < TNX_MAXR; ++l) {
+    t.shape[l] = 1;
+    t.magic[l] = 0;
+    t.shift[l] = 0;
+    t.sstride[l] = t.dstride[l] = 0;
+  }
+  for (size_t l = 0; l < sh2.size(); ++l) {
+    const uint64_t d = (uint64_t)sh2[l];
+    t.shape[l] = (int32_t)d;
+    t.sstride[l] = (int32_t)s2[l];
+    t.dstride[l] = (int32_t)d2[l];
+    // Division by the invariant d for indices n < 2^31 (Granlund and
+    // Montgomery, PLDI 1994): with p = ceil(log2 d) and m = ceil(2^(31+p) / d),
+    // m < 2^32 and floor(n / d) = floor(n m / 2^(31+p)) = umulhi(n, m) >> (p - 1),
+    // because n m / 2^(31+p) exceeds n / d by less than 1 / d.
+    if (d > 1) {
+      int lg = 0;
+      while ((1ull << lg) < d) ++lg;
+      const uint64_t m = ((1ull << (31 + lg)) + d - 1) / d;
+      t.magic[l] = (uint32_t)m;
+      t.shift[l] = (uint8_t)(lg - 1);
+    }
   }
   // transposing task: the source's unit-stride leg is not the destination's
   t.tleg = -1;
@@ -890,7 +915,6 @@ void sync_slots(Plan& p, cudaStream_t st) {
   p.h_slots_dev = p.h_slots;
 }
 
-void sync_slots(Plan& p) { sync_slots(p, p.ctx->stream); }
 
 void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB);
 
@@ -955,7 +979,6 @@ void capture_graph(tnx_ctx* c, cudaStream_t st, GraphRec& g, const std::function
   CUDA_CHECK(e);
 }
 
-bool graphs_enabled(tnx_ctx* c) { return c->stream != nullptr && c->use_graphs; }
 
 void bind_inputs(tnx_network* net, Plan& p) {
   for (int i = 0; i < p.nin; ++i) p.h_slots[i] = net->ts[i].t->data;
@@ -1282,12 +1305,13 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
       CUDA_CHECK(tnx_launch_lanczos_init(L, v0->data, st));
     }
     for (int j = 0; j < nsteps; ++j) {
-      CUDA_CHECK(tnx_launch_lanczos_set_input(p->d_slots + slot, L, j, st));
+      // the input slot points at v_0 here; each step kernel points it at v_{j+1}
+      if (j == 0) CUDA_CHECK(tnx_launch_lanczos_set_input(p->d_slots + slot, L, 0, st));
       enqueue_plan(*p, st, j == 0 ? 0 : fixed);
       // bytes of one step: two Gram-Schmidt passes over j+1 vectors (dots
       // (j+1)n + n, update (j+1)n + 2n), norm folded in, scale (2n)
       ProfScope ps(ctx, st, TNX_KC_VECTOR, 8.0 * (double)n * (2 * (2.0 * (j + 1) + 3) + 2));
-      CUDA_CHECK(tnx_launch_lanczos_step(L, j, st));
+      CUDA_CHECK(tnx_launch_lanczos_step(L, j, p->d_slots + slot, st));
     }
     ProfScope ps(ctx, st, TNX_KC_VECTOR, evp ? 8.0 * (double)n * (nsteps + 2) : 0.0);
     CUDA_CHECK(tnx_launch_lanczos_finish(L, evp, st));
