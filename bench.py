@@ -330,6 +330,7 @@ def main():
     ap.add_argument("--workload", default="chi512")
     ap.add_argument("--prec", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--order", default=None, help="explicit contraction order (default: the library's optimum)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -371,14 +372,14 @@ def main():
     if prec == "auto":
         prec = "split_bf16"
         try:
-            net, T, B = build_network(ctx, I.HEFF_SPEC, tensors, wl.nsym, prec=prec)
+            net, T, B = build_network(ctx, I.HEFF_SPEC, tensors, wl.nsym, order=args.order, prec=prec)
             net.flops()
             tnx.lanczos(net, "psi", T["psi"], 2)
         except tnx.TnxError as e:
             if e.name != "TNX_ERR_UNSUPPORTED":
                 raise
             prec = "f64"
-    net, T, B = build_network(ctx, I.HEFF_SPEC, tensors, wl.nsym, prec=prec)
+    net, T, B = build_network(ctx, I.HEFF_SPEC, tensors, wl.nsym, order=args.order, prec=prec)
     apply_flops = net.flops()
     evec = tnx.Tensor(ctx, B["psi"])
     stream = ctx.stream          # the library's stream: events are recorded on it

@@ -7,22 +7,23 @@
 //
 //  * every row of A (and every column of B) gets a common power-of-two scale
 //    2^(E+1) from the exponent E of its largest entry; an entry x becomes the
-//    fixed-point integer fix = floor(|x| 2^(F-E-1)) < 2^F, F = n*beta, which is
-//    cut into n slices of beta bits, s_i in [0, 2^beta), so that
-//    |x| ~ sum_i s_i 2^(E+1-beta(i+1)); each slice (with the sign of x) is an
-//    integer, exact in BF16 or FP16;
-//  * the product sum_k a_k b_k becomes sum over slice pairs (i, j); pairs with
+//    signed fixed-point integer v = round(x 2^(F-E-2)), |v| <= 2^(F-1),
+//    F = n*beta, written in n balanced base-2^beta digits
+//    v = sum_i d_i 2^(beta(n-1-i)), d_i in [-2^(beta-1), 2^(beta-1)]; each
+//    digit is an integer, exact in BF16 or FP16;
+//  * the product sum_k a_k b_k becomes sum over digit pairs (i, j); pairs with
 //    the same level t = i + j share one FP32 accumulator in tensor memory; all
 //    pairs with t <= n-1 are formed (terms below 2^-(beta n) are dropped); the
 //    accumulators of consecutive levels sit in consecutive TMEM columns, so
 //    one MMA of A slice i against the stacked B slices 0..n-1-i feeds all of
 //    its levels at once;
-//  * the K loop runs in chunks of KC = 128: with beta = 7 a level sums at most
-//    n * KC * 127^2 < 2^24, so every FP32 accumulation is exact; after each
-//    chunk the levels are read out of tensor memory and added, exactly, into
-//    a 64-bit integer fixed-point accumulator I = sum_t L_t 2^(beta(n-1-t));
-//  * the result is rounded once: C = I * 2^(E_r + E_c + 2 - beta(n+1)).
-// The only error is the truncation of each operand to F bits below its
+//  * the K loop runs in chunks of KC = 640: with beta = 7 a level sums at
+//    most n * KC * 64^2 < 2^24, so every FP32 accumulation is exact; after
+//    each chunk the levels are read out of tensor memory and added, exactly,
+//    into a 64-bit integer fixed-point accumulator
+//    I = sum_t L_t 2^(beta(n-1-t));
+//  * the result is rounded once: C = I * 2^(E_r + E_c + 2 - 2(F-1) + beta(n-1)).
+// The only error is the rounding of each operand to F-1 bits below its
 // row / column maximum and the dropped levels: about 2^-40 relative to
 // max|row| * max|col| * K.
 //
@@ -45,7 +46,7 @@ namespace {
 constexpr int TM = 128;            // tile rows (A)
 constexpr int TN = 64;             // tile columns (B rows)
 constexpr int TK = 32;             // K per stage
-constexpr int KC = 128;            // K per exact chunk
+constexpr int KC = 640;            // K per exact chunk
 constexpr int STAGES = 3;
 constexpr int MAXN = 6;            // slices
 constexpr int ATILE = TM * TK * 2; // bytes of one A slice tile (8 KB)
@@ -150,6 +151,18 @@ __device__ __forceinline__ double i64_scaled_to_double(long long v, int e) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)biased << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
+// The same value through the hardware conversion: __ll2double_rn rounds v to
+// 53 bits (nearest-even) and adding e to the exponent field is the exact
+// scaling by 2^e while the result stays normal; outside that range the
+// integer routine above decides.
+__device__ __forceinline__ double i64_scaled_fast(long long v, int e) {
+  if (v == 0) return 0.0;
+  const long long bits = __double_as_longlong(__ll2double_rn(v));
+  const int ex = (int)((bits >> 52) & 0x7FF) + e;
+  if (ex >= 1 && ex <= 2046) return __longlong_as_double(bits + ((long long)e << 52));
+  return i64_scaled_to_double(v, e);
+}
+
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                         uint32_t accumulate) {
   asm volatile(
@@ -204,7 +217,7 @@ __global__ void row_exponent_kernel(const SliceJob* __restrict__ jobs, const int
 
 // ------------------------------------------------------------ slicing
 __device__ __forceinline__ uint16_t slice_bits(uint32_t s, uint32_t neg, int f16) {
-  // s < 2^beta <= 256: exact as float via the 2^23 magic, exact in bf16 / f16
+  // s <= 2^(beta-1) <= 128: exact as float via the 2^23 magic, exact in bf16 / f16
   const float f = __int_as_float(0x4B000000 | s) - 8388608.0f;
   uint16_t b;
   if (f16) b = __half_as_ushort(__float2half_rn(f));
@@ -221,6 +234,7 @@ __global__ void slice_kernel(const SliceJob* __restrict__ jobs, const int64_t* _
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int F = nslice * beta;
   const uint32_t mask = (1u << beta) - 1u;
+  const long long half = 1ll << (beta - 1);
   for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += warps) {
     int lo = 0, hi = njobs;
     while (hi - lo > 1) {
@@ -247,19 +261,34 @@ __global__ void slice_kernel(const SliceJob* __restrict__ jobs, const int64_t* _
       const int k = k0 + e;
       unsigned long long bits = 0;
       if (live && k < j.K) bits = __double_as_longlong(src[k]);
-      const uint32_t neg = (uint32_t)(bits >> 63);
       const int eb = (int)((bits >> 52) & 0x7FF);
+      // |x| 2^(F-E-2) rounded half up: m53 * 2^-rs with rs = 54 - F + E_r - E >= 12
       unsigned long long fix = 0;
       if (eb != 0 && eb_r != 0) {
         const unsigned long long m53 = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        const int rs = 53 - F + (eb_r - eb);
-        fix = rs >= 64 ? 0ull : (m53 >> rs);
+        const int rs = 54 - F + (eb_r - eb);
+        fix = rs >= 64 ? 0ull : ((m53 >> (rs - 1)) + 1ull) >> 1;
+      }
+      long long v = (bits >> 63) ? -(long long)fix : (long long)fix;
+      // balanced digits, least significant first; the top digit takes the rest
+      int dg[MAXN];
+#pragma unroll
+      for (int i = MAXN - 1; i >= 0; --i) {
+        if (i < nslice) {
+          if (i > 0) {
+            const long long r = ((v + half) & (long long)mask) - half;
+            dg[i] = (int)r;
+            v = (v - r) >> beta;
+          } else {
+            dg[0] = (int)v;
+          }
+        }
       }
 #pragma unroll
       for (int i = 0; i < MAXN; ++i) {
         if (i < nslice) {
-          const uint32_t s = (uint32_t)(fix >> (beta * (nslice - 1 - i))) & mask;
-          const uint32_t b = slice_bits(s, neg, f16);
+          const int d = dg[i];
+          const uint32_t b = slice_bits((uint32_t)(d < 0 ? -d : d), d < 0 ? 1u : 0u, f16);
           sl[i][e >> 1] |= (e & 1) ? (b << 16) : b;
         }
       }
@@ -477,8 +506,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
         for (int c4 = 0; c4 < ECOLS / 4; ++c4) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            const int e = eb_r + ebc_s[c4 * 4 + c] - 2046 + 2 - beta * (NS + 1);
-            stg[lane][c ^ ((lane >> 2) & 3)] = i64_scaled_to_double(acc[c4 * 4 + c], e);
+            const int e = eb_r + ebc_s[c4 * 4 + c] - 2044 - 2 * (NS * beta - 1) + beta * (NS - 1);
+            stg[lane][c ^ ((lane >> 2) & 3)] = i64_scaled_fast(acc[c4 * 4 + c], e);
           }
           __syncwarp();
           const int cc = lane & 3, col = tl.n0 + cb + c4 * 4 + cc;
