@@ -123,10 +123,25 @@ def fp64_peak_tflops(torch, dev):
     return 2 * n ** 3 / (best * 1e-3) / 1e12
 
 
-def cpu_oracle_sample(wl, seconds: float = 12.0):
+def oracle_order(wl, order_opt):
+    """The contraction order the oracle runs, matching the library arm's choice:
+    "dense" -> the oracle's dense-cost search, "sparse" -> its block-sparse-cost
+    search, anything else -> that explicit tree."""
+    if order_opt == "dense":
+        return None
+    if order_opt != "sparse":
+        return order_opt
+    from oracle import heff as oheff
+    from oracle.network import sparse_optimal_order, tree_str
+    net, _ = oheff.make_heff(wl, symmetric=True)
+    bonds = {n: list(net.tensors[n].bonds) for n in net.names}
+    return tree_str(sparse_optimal_order(net.names, net.labels, bonds)[0])
+
+
+def cpu_oracle_sample(wl, order=None, seconds: float = 12.0):
     """The oracle as it stands on the host cores: repeated H_eff applies for ~seconds."""
     from oracle import heff as oheff
-    net, T = oheff.make_heff(wl, symmetric=True)
+    net, T = oheff.make_heff(wl, symmetric=True, order=order)
     rec = []
     net.launch(record=rec)
     flops = sum(r["flops"] for r in rec)
@@ -149,7 +164,8 @@ def run_reference(args):
         return
     wl, wname = workload(args.workload)
     from oracle import heff as oheff
-    net, T = oheff.make_heff(wl, symmetric=True)
+    order = oracle_order(wl, args.order)
+    net, T = oheff.make_heff(wl, symmetric=True, order=order)
     rec = []
     net.launch(record=rec)
     flops = sum(r["flops"] for r in rec)
@@ -167,7 +183,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wname, "sample": "one H_eff*psi apply per step (oracle, numpy FP64)"},
+        "config": {"workload": wname, "order": net.get_order(),
+                   "sample": "one H_eff*psi apply per step (oracle, numpy FP64)"},
         "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} H_eff*psi applies of {wname} on the host"},
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -330,7 +347,9 @@ def main():
     ap.add_argument("--workload", default="chi512")
     ap.add_argument("--prec", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--order", default=None, help="explicit contraction order (default: the library's optimum)")
+    ap.add_argument("--order", default="sparse",
+                    help='contraction order: "sparse" (block-sparse-cost search, default), "dense" '
+                         '(dense-cost search of the paper) or an explicit tree')
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -368,18 +387,19 @@ def main():
     bonds = I.heff_bonds(wl)
     tensors = {n: (bonds[n], I.heff_value_fn(wl, n, symmetric=True)) for n in I.HEFF_NAMES}
 
+    order_arg = None if args.order == "dense" else args.order
     prec = args.prec
     if prec == "auto":
         prec = "split_bf16"
         try:
-            net, T, B = build_network(ctx, I.HEFF_SPEC, tensors, wl.nsym, order=args.order, prec=prec)
+            net, T, B = build_network(ctx, I.HEFF_SPEC, tensors, wl.nsym, order=order_arg, prec=prec)
             net.flops()
             tnx.lanczos(net, "psi", T["psi"], 2)
         except tnx.TnxError as e:
             if e.name != "TNX_ERR_UNSUPPORTED":
                 raise
             prec = "f64"
-    net, T, B = build_network(ctx, I.HEFF_SPEC, tensors, wl.nsym, order=args.order, prec=prec)
+    net, T, B = build_network(ctx, I.HEFF_SPEC, tensors, wl.nsym, order=order_arg, prec=prec)
     apply_flops = net.flops()
     evec = tnx.Tensor(ctx, B["psi"])
     stream = ctx.stream          # the library's stream: events are recorded on it
@@ -490,7 +510,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        v, n, dt, fl = cpu_oracle_sample(wl)
+        v, n, dt, fl = cpu_oracle_sample(wl, order=net.get_order())
         cpu = {"value": v, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{n} oracle H_eff*psi applies of {wname} ({dt:.1f} s, numpy FP64, default BLAS threads)"}
 

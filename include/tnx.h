@@ -176,10 +176,17 @@ tnx_status tnx_network_destroy(tnx_network* net);
  * The network keeps a reference to t.  Bond checks happen at launch. */
 tnx_status tnx_network_put(tnx_network* net, const char* name, tnx_tensor* t, int nlab,
                            const char* const* labels);
-/* Sec. 8.3 setOrder: optimal != 0 computes the min-cost order (dynamic
+/* Sec. 8.3 setOrder: optimal == 1 computes the min-cost order (dynamic
  * programming with cost capping, Pfeifer et al. 2014, cost = product of the
  * dimensions of all legs of each pairwise contraction) at launch, cached per
- * set of bond dimensions; optimal == 0 takes `order` ("(A,(B,C))"). */
+ * set of bond dimensions; optimal == 0 takes `order` ("(A,(B,C))").
+ * optimal == 2 (an addition to the paper's search, for block-sparse
+ * operands): the same subset dynamic programming with each pairwise cost
+ * counted over charge sectors, 2 * sum_g H_a(-g) H_k(g) H_b(g), H_S(c) = number
+ * of index combinations of the legs S with signed total charge c, assuming
+ * every intermediate holds all zero-flux blocks of its legs; at most 12
+ * tensors (else TNX_ERR_UNSUPPORTED); cached per set of bond sectors.
+ * Errors: TNX_ERR_ARG (optimal outside 0..2), TNX_ERR_NETWORK. */
 tnx_status tnx_network_set_order(tnx_network* net, int optimal, const char* order);
 /* Sec. 8.3 getOrder: writes the current tree ("(M2,(M1,M3))"), NUL-terminated,
  * into buf (TNX_ERR_ARG if len is too small). */

@@ -359,8 +359,11 @@ class Network:
         self.ctx.check(ctx_code)
         self._refs[name] = t
 
-    def set_order(self, optimal: bool, order: str | None = None):
-        self.ctx.check(lib().tnx_network_set_order(self.h, 1 if optimal else 0, order.encode() if order else None))
+    def set_order(self, optimal, order: str | None = None):
+        """optimal: False (explicit `order`), True (dense-cost search) or "sparse"
+        (block-sparse-cost search)."""
+        mode = 2 if optimal == "sparse" else (1 if optimal else 0)
+        self.ctx.check(lib().tnx_network_set_order(self.h, mode, order.encode() if order else None))
 
     def get_order(self) -> str:
         buf = C.create_string_buffer(4096)

@@ -141,6 +141,152 @@ u128 mul_sat(u128 a, u128 b) {
 // contraction: product of the dimensions of all distinct legs of both operands.
 // Ties keep the first split S1 (containing the lowest member) in increasing
 // bitmask order.
+// ------------------------------------------ block-sparse order search
+// Cost of a pairwise contraction counted over charge sectors instead of
+// dense dimensions: an operand made of the zero-flux blocks of its legs,
+// contracted over the legs K, costs 2 sum_g H_a(-g) H_k(g) H_b(g) flops, where
+// H_S(c) is the number of index combinations of the legs S whose signed charges
+// add up to c (a convolution of the legs' sector degeneracies), g the charge
+// of the contracted legs seen from the left operand, and the left / right free
+// legs must carry -g / +g for both operands to be zero-flux.  Intermediates
+// are assumed to hold every zero-flux block of their legs.  Subset dynamic
+// programming (no capping; at most 12 tensors) minimises the summed cost;
+// ties keep the first split, as in the dense search.
+namespace {
+typedef std::map<std::vector<int32_t>, double> Hist;
+
+struct SymInfo {
+  std::vector<int> kinds, zn;
+  std::vector<int32_t> add(const std::vector<int32_t>& a, const std::vector<int32_t>& b) const {
+    std::vector<int32_t> c(a.size());
+    for (size_t i = 0; i < a.size(); ++i) {
+      c[i] = a[i] + b[i];
+      if (kinds[i] == TNX_ZN) c[i] %= zn[i];
+    }
+    return c;
+  }
+  std::vector<int32_t> neg(const std::vector<int32_t>& a) const {
+    std::vector<int32_t> c(a.size());
+    for (size_t i = 0; i < a.size(); ++i) c[i] = kinds[i] == TNX_ZN ? (zn[i] - a[i]) % zn[i] : -a[i];
+    return c;
+  }
+};
+
+Hist hist_conv(const Hist& a, const Hist& b, const SymInfo& sy) {
+  Hist c;
+  for (auto& x : a)
+    for (auto& y : b) c[sy.add(x.first, y.first)] += x.second * y.second;
+  return c;
+}
+
+Hist leg_hist(const BondD& b) {
+  Hist h;
+  for (int s = 0; s < b.nsec; ++s) {
+    std::vector<int32_t> q(b.nsym);
+    for (int c = 0; c < b.nsym; ++c) q[c] = b.signed_q(s, c);
+    h[q] += (double)b.deg[s];
+  }
+  return h;
+}
+}  // namespace
+
+void sparse_optimal_tree(tnx_network* net) {
+  const int n = (int)net->ts.size();
+  if (n > 12) fail(TNX_ERR_UNSUPPORTED, "the block-sparse order search supports at most 12 tensors");
+  SymInfo sy;
+  const BondD& b0 = net->ts[0].t->bonds[0];
+  sy.kinds = b0.kinds;
+  sy.zn = b0.zn;
+  const int nsym = b0.nsym;
+  // label -> (tensor, bond) of each occurrence
+  std::map<std::string, std::vector<std::pair<int, const BondD*>>> occ;
+  for (int i = 0; i < n; ++i) {
+    const NetTensor& t = net->ts[i];
+    for (size_t j = 0; j < t.labels.size(); ++j) occ[t.labels[j]].push_back({i, &t.t->bonds[t.perm[j]]});
+  }
+  std::vector<std::string> labs;
+  for (auto& kv : occ) labs.push_back(kv.first);
+  const int nl = (int)labs.size();
+  std::vector<std::vector<int>> legs(n);
+  for (int i = 0; i < n; ++i)
+    for (auto& l : net->ts[i].labels) legs[i].push_back((int)(std::find(labs.begin(), labs.end(), l) - labs.begin()));
+  const uint32_t full = (1u << n) - 1;
+  std::vector<std::vector<int>> open(full + 1);
+  std::vector<int> cnt(nl);
+  for (uint32_t m = 1; m <= full; ++m) {
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (int i = 0; i < n; ++i)
+      if (m >> i & 1)
+        for (int l : legs[i]) cnt[l]++;
+    for (int l = 0; l < nl; ++l)
+      if (cnt[l] == 1) open[m].push_back(l);
+  }
+  // the bond of label l as it appears inside subset m
+  auto bond_in = [&](int l, uint32_t m) -> const BondD& {
+    for (auto& o : occ[labs[l]])
+      if (m >> o.first & 1) return *o.second;
+    fail(TNX_ERR_NETWORK, "internal: label outside its subset");
+    return *occ[labs[l]][0].second;
+  };
+  const Hist unit = {{std::vector<int32_t>(nsym, 0), 1.0}};
+  auto hist_of = [&](const std::vector<int>& ls, uint32_t m) {
+    Hist h = unit;
+    for (int l : ls) h = hist_conv(h, leg_hist(bond_in(l, m)), sy);
+    return h;
+  };
+  auto pair_cost = [&](uint32_t a, uint32_t b) {
+    std::vector<int> fa, fb, k;
+    for (int l : open[a]) (std::find(open[b].begin(), open[b].end(), l) != open[b].end() ? k : fa).push_back(l);
+    for (int l : open[b])
+      if (std::find(open[a].begin(), open[a].end(), l) == open[a].end()) fb.push_back(l);
+    const Hist ha = hist_of(fa, a), hk = hist_of(k, a), hb = hist_of(fb, b);
+    double c = 0.0;
+    for (auto& g : hk) {
+      auto ia = ha.find(sy.neg(g.first));
+      auto ib = hb.find(g.first);
+      if (ia != ha.end() && ib != hb.end()) c += 2.0 * ia->second * g.second * ib->second;
+    }
+    return c;
+  };
+  std::vector<double> best(full + 1, 0.0);
+  std::vector<uint32_t> split(full + 1, 0);
+  for (int size = 2; size <= n; ++size)
+    for (uint32_t m = 1; m <= full; ++m) {
+      if (__builtin_popcount(m) != size) continue;
+      uint32_t low = m & (~m + 1), rest = m ^ low, s = 0;
+      bool found = false;
+      double bc = 0.0;
+      while (true) {
+        uint32_t m1 = low | s, m2 = m ^ m1;
+        if (m2 != 0) {
+          const double c = best[m1] + best[m2] + pair_cost(m1, m2);
+          if (!found || c < bc) {
+            found = true;
+            bc = c;
+            split[m] = m1;
+          }
+        }
+        if (s == rest) break;
+        s = (s - rest) & rest;
+      }
+      best[m] = bc;
+    }
+  std::vector<TreeNode> nodes;
+  std::function<int(uint32_t)> build = [&](uint32_t m) -> int {
+    if (__builtin_popcount(m) == 1) {
+      nodes.push_back(TreeNode{__builtin_ctz(m), -1, -1});
+      return (int)nodes.size() - 1;
+    }
+    int l = build(split[m]);
+    int r = build(m ^ split[m]);
+    nodes.push_back(TreeNode{-1, l, r});
+    return (int)nodes.size() - 1;
+  };
+  int root = build(full);
+  net->tree = nodes;
+  net->root = root;
+}
+
 void optimal_tree(tnx_network* net) {
   const int n = (int)net->ts.size();
   if (n > 20) fail(TNX_ERR_UNSUPPORTED, "optimal order search supports at most 20 tensors");
@@ -811,9 +957,14 @@ void require_put(const tnx_network* net) {
 void ensure_order(tnx_network* net) {
   require_put(net);
   if (net->optimal) {
-    std::string dk = dims_key(net);
+    // the sparse search depends on the sectors, not only the dimensions
+    std::string dk = std::to_string(net->optimal) + ":" + dims_key(net);
+    if (net->optimal == 2)
+      for (auto& t : net->ts)
+        for (auto& b : t.t->bonds) dk += b.key();
     if (dk != net->order_dims_key) {
-      optimal_tree(net);
+      if (net->optimal == 2) sparse_optimal_tree(net);
+      else optimal_tree(net);
       net->order_dims_key = dk;
     }
   }
@@ -1129,13 +1280,14 @@ extern "C" tnx_status tnx_network_set_order(tnx_network* net, int optimal, const
   if (!net) return TNX_ERR_ARG;
   return tnx_guard(net->ctx, [&] {
     if (optimal) {
-      net->optimal = true;
+      if (optimal != 1 && optimal != 2) fail(TNX_ERR_ARG, "optimal must be 0, 1 or 2");
+      net->optimal = optimal;
       net->order_dims_key.clear();
       if (all_put(net)) ensure_order(net);
     } else {
       if (!order || !*order) fail(TNX_ERR_NETWORK, "an explicit order is required when optimal is off");
       set_tree_from_string(net, order);
-      net->optimal = false;
+      net->optimal = 0;
     }
   });
 }

@@ -140,7 +140,7 @@ struct tnx_network {
   std::vector<std::string> tout;
   std::vector<TreeNode> tree;
   int root = -1;
-  bool optimal = false;
+  int optimal = 0;                 // 0 explicit order, 1 dense-cost search, 2 block-sparse-cost search
   int prec = TNX_PREC_F64;
   std::string order_dims_key;      // dims for which the optimal tree was computed
   std::unique_ptr<Plan> plan;

@@ -24,7 +24,9 @@ def build_network(ctx: Context, spec: str, tensors: dict, nsym: int, order: str 
         B[name] = make_bonds(ctx, legs, nsym)
         T[name] = Tensor(ctx, B[name]).fill(value_at)
         net.put(name, T[name])
-    if order:
+    if order == "sparse":
+        net.set_order("sparse")
+    elif order:
         net.set_order(False, order)
     else:
         net.set_order(True)

@@ -306,3 +306,21 @@ def test_graph_and_profiler_leave_no_stale_cuda_error(ctx):
     x.add_(1.0)
     torch.cuda.synchronize()
     assert float(x.sum()) == 1024.0
+
+
+@pytest.mark.parametrize("name", ["u1_chi16", "u1_chi512", "dense_chi32", "hubbard_chi64"])
+def test_sparse_order_search(ctx, name):
+    """Block-sparse-cost search: the library's tree has the oracle's minimum sector
+    count over all 105 trees, and its result matches the oracle in that order."""
+    from oracle.network import parse_order, sparse_optimal_order, sparse_tree_cost
+    wl = WORKLOADS[name]()
+    net, T, B = lib_heff(ctx, wl, order="sparse")
+    got = net.get_order()
+    onet, _ = oracle_heff(wl)
+    bonds = {n: list(onet.tensors[n].bonds) for n in onet.names}
+    _, best = sparse_optimal_order(onet.names, onet.labels, bonds)
+    assert sparse_tree_cost(parse_order(got, onet.names), onet.labels, bonds) == best
+    if name == "u1_chi512":
+        assert got == "(L,((psi,R),(W1,W2)))"
+    onet.set_order(False, got)
+    assert rel_fro(net.launch(B["psi"]).block_dict(), onet.launch()) <= TOL_F64
