@@ -186,35 +186,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// ------------------------------------------------------- exponent pass
-// One warp per row of a packed operand: biased exponent of the row's largest |x|.
-__global__ void row_exponent_kernel(const SliceJob* __restrict__ jobs, const int64_t* __restrict__ row_start,
-                                    int njobs, int64_t total, double* const* __restrict__ slots) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < total; r += warps) {
-    int lo = 0, hi = njobs;
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      if (__ldg(row_start + mid) <= r) lo = mid; else hi = mid;
-    }
-    const SliceJob& j = jobs[lo];
-    const int64_t row = r - __ldg(row_start + lo);
-    const unsigned long long* x = (const unsigned long long*)(slots[j.src_slot] + j.src_off + row * j.ld);
-    unsigned long long m = 0;
-    for (int k = lane; k < j.K; k += 32) {
-      const unsigned long long b = x[k] & 0x7FFFFFFFFFFFFFFFull;
-      m = b > m ? b : m;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
-      m = v > m ? v : m;
-    }
-    if (lane == 0) ((int32_t*)slots[j.exp_slot])[j.exp_off + row] = (int32_t)(m >> 52);
-  }
-}
-
 // ------------------------------------------------------------ slicing
 __device__ __forceinline__ uint16_t slice_bits(uint32_t s, uint32_t neg, int f16) {
   // s <= 2^(beta-1) <= 128: exact as float via the 2^23 magic, exact in bf16 / f16
@@ -225,85 +196,115 @@ __device__ __forceinline__ uint16_t slice_bits(uint32_t s, uint32_t neg, int f16
   return (s != 0 && neg) ? (uint16_t)(b | 0x8000) : b;
 }
 
-// One warp per (8-row group, 32-wide K tile) of a padded operand; lane =
-// (row in group) * 4 + (8-column group).  Writes 16 bytes per slice per lane.
-__global__ void slice_kernel(const SliceJob* __restrict__ jobs, const int64_t* __restrict__ warp_start, int njobs,
-                             int64_t total, int nslice, int beta, int f16, double* const* __restrict__ slots) {
-  const int lane = threadIdx.x & 31;
+// Slices of the packed operands, one CTA (8 warps) per work item.  Rows are
+// taken in groups of 8 (rows past an operand's end give zero slices); in a
+// warp, lane = (row in group) * 4 + (8-column group).  A job with long rows
+// (SliceJob::cta_mode) gives one group per item and the 8 warps share the
+// group; otherwise an item is 8 groups, one per warp.  For a group, first the
+// biased exponent of each row's largest |x| (lanes of a row scan every 4th
+// entry, the lanes and then the sharing warps combine), stored for the GEMM
+// epilogue; then the group's 32-wide K tiles are sliced, 8 entries per lane,
+// 16 bytes per slice per lane written in the tiled core-matrix layout the
+// GEMM copies in.
+__global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restrict__ jobs,
+                                                         const int2* __restrict__ items, int64_t total, int nslice,
+                                                         int beta, int f16, double* const* __restrict__ slots) {
+  __shared__ unsigned long long s_max[8][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int r8 = lane >> 2, kq = lane & 3;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int F = nslice * beta;
   const uint32_t mask = (1u << beta) - 1u;
   const long long half = 1ll << (beta - 1);
-  for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += warps) {
-    int lo = 0, hi = njobs;
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      if (__ldg(warp_start + mid) <= w) lo = mid; else hi = mid;
-    }
-    const SliceJob& j = jobs[lo];
-    const int64_t wl = w - __ldg(warp_start + lo);
+  for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+    const int2 item = items[w];   // (job, first 8-row group)
+    const SliceJob& j = jobs[item.x];
+    const bool shared_group = j.cta_mode != 0;   // uniform over the CTA
+    const int64_t ngroups = ((int64_t)j.rows + j.tile_rows - 1) / j.tile_rows * (j.tile_rows / 8);
+    const int64_t rg = shared_group ? item.y : (int64_t)item.y + wid;
     const int KT = (j.K + TK - 1) / TK;
-    const int64_t rg = wl / KT;       // 8-row group in the padded operand
-    const int kt = (int)(wl % KT);
     const int64_t row = rg * 8 + r8;
-    const int k0 = kt * TK + kq * 8;
-    const double* src = slots[j.src_slot] + j.src_off + row * j.ld;
     const bool live = row < j.rows;
-    const int eb_r = live ? ((const int32_t*)slots[j.exp_slot])[j.exp_off + row] : 0;
-    uint32_t sl[MAXN][4];
-#pragma unroll
-    for (int i = 0; i < MAXN; ++i)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) sl[i][q] = 0;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int k = k0 + e;
-      unsigned long long bits = 0;
-      if (live && k < j.K) bits = __double_as_longlong(src[k]);
-      const int eb = (int)((bits >> 52) & 0x7FF);
-      // |x| 2^(F-E-2) rounded half up: m53 * 2^-rs with rs = 54 - F + E_r - E >= 12
-      unsigned long long fix = 0;
-      if (eb != 0 && eb_r != 0) {
-        const unsigned long long m53 = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        const int rs = 54 - F + (eb_r - eb);
-        fix = rs >= 64 ? 0ull : ((m53 >> (rs - 1)) + 1ull) >> 1;
-      }
-      long long v = (bits >> 63) ? -(long long)fix : (long long)fix;
-      // balanced digits, least significant first; the top digit takes the rest
-      int dg[MAXN];
-#pragma unroll
-      for (int i = MAXN - 1; i >= 0; --i) {
-        if (i < nslice) {
-          if (i > 0) {
-            const long long r = ((v + half) & (long long)mask) - half;
-            dg[i] = (int)r;
-            v = (v - r) >> beta;
-          } else {
-            dg[0] = (int)v;
-          }
-        }
+    const double* src = slots[j.src_slot] + j.src_off + row * j.ld;
+    // row exponent
+    const int kstart = shared_group ? wid * 4 + kq : kq, kstep = shared_group ? 32 : 4;
+    unsigned long long mx = 0;
+    if (live)
+      for (int k = kstart; k < j.K; k += kstep) {
+        const unsigned long long b = __double_as_longlong(src[k]) & 0x7FFFFFFFFFFFFFFFull;
+        mx = b > mx ? b : mx;
       }
 #pragma unroll
-      for (int i = 0; i < MAXN; ++i) {
-        if (i < nslice) {
-          const int d = dg[i];
-          const uint32_t b = slice_bits((uint32_t)(d < 0 ? -d : d), d < 0 ? 1u : 0u, f16);
-          sl[i][e >> 1] |= (e & 1) ? (b << 16) : b;
-        }
-      }
+    for (int o = 1; o < 4; o <<= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = v > mx ? v : mx;
     }
+    if (shared_group) {
+      if (kq == 0) s_max[wid][r8] = mx;
+      __syncthreads();
+      mx = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) mx = s_max[q][r8] > mx ? s_max[q][r8] : mx;
+      __syncthreads();   // s_max is rewritten by the next item
+    }
+    if (rg >= ngroups) continue;   // a warp past the job's last group (8-group items)
+    const int eb_r = (int)(mx >> 52);
+    if (live && kq == 0 && (!shared_group || wid == 0)) ((int32_t*)slots[j.exp_slot])[j.exp_off + row] = eb_r;
     const int tile_rows = j.tile_rows;
     const int64_t mt = row / tile_rows;
     const int rin = (int)(row % tile_rows);
     const int64_t tile_bytes = (int64_t)tile_rows * TK * 2;
     char* base = (char*)slots[j.dst_slot] + j.dst_off_bytes;
     const int64_t inner = (int64_t)(rin >> 3) * 512 + kq * 128 + (rin & 7) * 16;
+    for (int kt = shared_group ? wid : 0; kt < KT; kt += shared_group ? 8 : 1) {
+      const int k0 = kt * TK + kq * 8;
+      uint32_t sl[MAXN][4];
 #pragma unroll
-    for (int i = 0; i < MAXN; ++i) {
-      if (i < nslice) {
-        uint4 v = make_uint4(sl[i][0], sl[i][1], sl[i][2], sl[i][3]);
-        *(uint4*)(base + ((mt * KT + kt) * nslice + i) * tile_bytes + inner) = v;
+      for (int i = 0; i < MAXN; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sl[i][q] = 0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = k0 + e;
+        unsigned long long bits = 0;
+        if (live && k < j.K) bits = __double_as_longlong(src[k]);
+        const int eb = (int)((bits >> 52) & 0x7FF);
+        // |x| 2^(F-E-2) rounded half up: m53 * 2^-rs with rs = 54 - F + E_r - E >= 12
+        unsigned long long fix = 0;
+        if (eb != 0 && eb_r != 0) {
+          const unsigned long long m53 = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+          const int rs = 54 - F + (eb_r - eb);
+          fix = rs >= 64 ? 0ull : ((m53 >> (rs - 1)) + 1ull) >> 1;
+        }
+        long long v = (bits >> 63) ? -(long long)fix : (long long)fix;
+        // balanced digits, least significant first; the top digit takes the rest
+        int dg[MAXN];
+#pragma unroll
+        for (int i = MAXN - 1; i >= 0; --i) {
+          if (i < nslice) {
+            if (i > 0) {
+              const long long r = ((v + half) & (long long)mask) - half;
+              dg[i] = (int)r;
+              v = (v - r) >> beta;
+            } else {
+              dg[0] = (int)v;
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < MAXN; ++i) {
+          if (i < nslice) {
+            const int d = dg[i];
+            const uint32_t b = slice_bits((uint32_t)(d < 0 ? -d : d), d < 0 ? 1u : 0u, f16);
+            sl[i][e >> 1] |= (e & 1) ? (b << 16) : b;
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < MAXN; ++i) {
+        if (i < nslice) {
+          uint4 v = make_uint4(sl[i][0], sl[i][1], sl[i][2], sl[i][3]);
+          *(uint4*)(base + ((mt * KT + kt) * nslice + i) * tile_bytes + inner) = v;
+        }
       }
     }
   }
@@ -529,23 +530,13 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
 
 }  // namespace
 
-cudaError_t tnx_launch_row_exponents(const SliceJob* jobs, const int64_t* row_start, int njobs, int64_t total_rows,
-                                     double* const* slots, cudaStream_t st) {
-  if (total_rows <= 0) return cudaSuccess;
-  int64_t blocks = (total_rows + 7) / 8;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  row_exponent_kernel<<<(int)blocks, 256, 0, st>>>(jobs, row_start, njobs, total_rows, slots);
-  tnx_note_launch(1);
-  return cudaGetLastError();
-}
-
-cudaError_t tnx_launch_slices(const SliceJob* jobs, const int64_t* warp_start, int njobs, int64_t total_warps,
-                              int nslice, int beta, int f16, double* const* slots, cudaStream_t st) {
-  if (total_warps <= 0) return cudaSuccess;
+cudaError_t tnx_launch_slices(const SliceJob* jobs, const int2* items, int64_t total_items, int nslice, int beta,
+                              int f16, double* const* slots, cudaStream_t st) {
+  if (total_items <= 0) return cudaSuccess;
   if (nslice < 1 || nslice > MAXN || beta < 1 || beta > 8 || nslice * beta > 53) return cudaErrorInvalidValue;
-  int64_t blocks = (total_warps + 7) / 8;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  slice_kernel<<<(int)blocks, 256, 0, st>>>(jobs, warp_start, njobs, total_warps, nslice, beta, f16, slots);
+  int64_t blocks = total_items;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  slice_rows_kernel<<<(int)blocks, 256, 0, st>>>(jobs, items, total_items, nslice, beta, f16, slots);
   tnx_note_launch(1);
   return cudaGetLastError();
 }

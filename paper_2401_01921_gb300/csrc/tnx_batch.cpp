@@ -99,9 +99,7 @@ void enqueue_batch(tnx_batch& B, cudaStream_t st) {
     } else {
       if (s.jobs.n) {
         ProfScope ps(c, st, TNX_KC_SLICE, (double)s.jobs.elems * (16.0 + 2.0 * B.nslice));
-        CUDA_CHECK(tnx_launch_row_exponents(s.jobs.d, s.jobs.row_start, s.jobs.n, s.jobs.rows, B.d_slots, st));
-        CUDA_CHECK(tnx_launch_slices(s.jobs.d, s.jobs.warp_start, s.jobs.n, s.jobs.warps, B.nslice, B.beta, f16,
-                                     B.d_slots, st));
+        CUDA_CHECK(tnx_launch_slices(s.jobs.d, s.jobs.items, s.jobs.nitems, B.nslice, B.beta, f16, B.d_slots, st));
       }
       ProfScope ps(c, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
       CUDA_CHECK(tnx_launch_gemm_split(s.dSG, s.dST, s.nst, B.nslice, B.beta, f16, B.d_slots, c->d_status, st,
@@ -172,7 +170,6 @@ extern "C" tnx_status tnx_batch_create(tnx_ctx* ctx, int n, tnx_network* const* 
       std::vector<GemmGroup> gg;
       std::vector<GemmTile> tt, ts;
       std::vector<SliceJob> jobs;
-      std::vector<int64_t> rs(1, 0), ws(1, 0);
       std::vector<SplitGroup> sg;
       std::vector<GemmTile> st;
       for (size_t i = 0; i < B->plans.size(); ++i) {
@@ -197,8 +194,6 @@ extern "C" tnx_status tnx_batch_create(tnx_ctx* ctx, int n, tnx_network* const* 
             j.dst_slot = shift_slot(j.dst_slot, b);
             j.exp_slot = shift_slot(j.exp_slot, b);
             jobs.push_back(j);
-            rs.push_back(rs.back() + sp.jobsAll.hrows[q]);
-            ws.push_back(ws.back() + sp.jobsAll.hwarps[q]);
           }
           bs.jobs.elems += sp.jobsAll.elems;
           for (SplitGroup g : sp.hSG) {
@@ -222,12 +217,12 @@ extern "C" tnx_status tnx_batch_create(tnx_ctx* ctx, int n, tnx_network* const* 
         std::stable_sort(st.begin(), st.end(), [&](const GemmTile& x, const GemmTile& y) {
           return sg[x.group].K > sg[y.group].K;
         });
+        // the merged launch is larger than any instance's: schedule it afresh
+        const std::vector<int2> items = tnx_slice_schedule(jobs);
         bs.jobs.n = (int)jobs.size();
-        bs.jobs.rows = rs.back();
-        bs.jobs.warps = ws.back();
+        bs.jobs.nitems = (int64_t)items.size();
         bs.jobs.d = B->upload(jobs);
-        bs.jobs.row_start = B->upload(rs);
-        bs.jobs.warp_start = B->upload(ws);
+        bs.jobs.items = B->upload(items);
         bs.dSG = B->upload(sg);
         bs.dST = B->upload(st);
         bs.nst = (int)st.size();

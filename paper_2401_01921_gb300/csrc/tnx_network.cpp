@@ -780,6 +780,13 @@ void build_step(Plan& p, StepPlan& s) {
   std::vector<GemmGroup> gg(G);
   std::vector<GemmTile> tiles, stiles;
   s.skinny.assign(G, 0);
+  // Groups with K <= 16 run on the skinny FP64 kernel.  Under split precision
+  // that holds only when every group of the step is that small: otherwise the
+  // few small groups ride along in the split GEMM launch (one K tile each)
+  // instead of costing a launch of their own.
+  bool all_small = true;
+  for (int g = 0; g < G; ++g) all_small = all_small && s.mkn[3 * g + 1] <= 16;
+  const bool split_prec = p.prec == TNX_PREC_SPLIT_BF16 || p.prec == TNX_PREC_SPLIT_F16;
   for (int g = 0; g < G; ++g) {
     GemmGroup& x = gg[g];
     memset(&x, 0, sizeof(x));
@@ -794,7 +801,7 @@ void build_step(Plan& p, StepPlan& s) {
     x.N = (int32_t)s.mkn[3 * g + 2];
     x.lda = x.ldb = (int32_t)s.ldK[g];
     x.ldc = x.N;
-    if (x.K <= 16) {
+    if (x.K <= 16 && (!split_prec || all_small)) {
       s.skinny[g] = 1;
       for (int m0 = 0; m0 < x.M; m0 += 128)
         for (int n0 = 0; n0 < x.N; n0 += 64) stiles.push_back(GemmTile{g, m0, n0, 0});

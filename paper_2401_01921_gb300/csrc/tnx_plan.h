@@ -62,16 +62,13 @@ struct StepPlan {
   double flops_skinny = 0;      // useful flops of the skinny groups
   // split precision
   int slotSA = -1, slotSB = -1, slotEA = -1, slotEB = -1;
-  struct Jobs {             // one list of slicing jobs with its prefix arrays
+  struct Jobs {             // one slicing launch: its jobs and work items
     SliceJob* d = nullptr;
     int n = 0;
-    int64_t* row_start = nullptr;
-    int64_t rows = 0;
-    int64_t* warp_start = nullptr;
-    int64_t warps = 0;
+    int2* items = nullptr;      // (job, first 8-row group) per CTA work item
+    int64_t nitems = 0;
     int64_t elems = 0;
-    std::vector<SliceJob> h;    // host copies
-    std::vector<int64_t> hrows, hwarps;   // per-job row and warp counts
+    std::vector<SliceJob> h;    // host copies (batched plans merge them)
   } jobsAll, jobsA, jobsB;
   int64_t slice_elems = 0;      // packed elements that get sliced (split precision)
   SplitGroup* dSG = nullptr;
@@ -152,6 +149,7 @@ struct tnx_network {
 // split-precision planning and launch (tnx_split.cpp)
 void tnx_build_split_parts(Plan& p, StepPlan& s);
 void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB);
+std::vector<int2> tnx_slice_schedule(std::vector<SliceJob>& jobs);
 
 // relayout chunks (tnx_network.cpp)
 void tnx_make_copy_chunks(const std::vector<CopyTask>& tasks, std::vector<int4>& chunks);

@@ -12,12 +12,33 @@ constexpr int TM = 128, TN = 64, TK = 32;
 constexpr int64_t KMAX = 8192;   // the 64-bit fixed-point accumulator is exact up to this K
 }
 
+// Work items of one slicing launch (k_split.cu), one CTA each: with few
+// 8-row groups in the launch, every job shares each group among the 8 warps
+// of a CTA (more CTAs, shorter per-warp loops); with many, jobs whose rows
+// span at most 8 K tiles give one group to each warp, 8 groups per item.
+std::vector<int2> tnx_slice_schedule(std::vector<SliceJob>& jobs) {
+  auto groups_of = [](const SliceJob& j) {
+    return ((int64_t)j.rows + j.tile_rows - 1) / j.tile_rows * (j.tile_rows / 8);
+  };
+  int64_t groups = 0;
+  for (const SliceJob& j : jobs) groups += groups_of(j);
+  const bool many = groups >= 4 * 8 * 152;
+  std::vector<int2> items;
+  for (size_t q = 0; q < jobs.size(); ++q) {
+    SliceJob& j = jobs[q];
+    j.cta_mode = (!many || (j.K + TK - 1) / TK > 8) ? 1 : 0;
+    const int64_t g = groups_of(j);
+    if (g > INT32_MAX) fail(TNX_ERR_UNSUPPORTED, "slicing job above 2^31 row groups");
+    for (int64_t r = 0; r < g; r += j.cta_mode ? 1 : 8) items.push_back(make_int2((int)q, (int)r));
+  }
+  return items;
+}
+
 void tnx_build_split_parts(Plan& p, StepPlan& s) {
   if (p.prec == TNX_PREC_TF32) fail(TNX_ERR_UNSUPPORTED, "TF32 products are not available in this build");
   const int G = s.G;
   const int n = p.nslice;
   std::vector<SliceJob> jobs[2];
-  std::vector<int64_t> row_start[2], warp_start[2];
   int64_t elems[2] = {0, 0};
   std::vector<int64_t> offSA(G), offSB(G), offEA(G), offEB(G);
   int64_t sa = 0, sb = 0, ea = 0, eb = 0;
@@ -63,42 +84,26 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
       j.K = (int32_t)K;
       j.ld = (int32_t)s.ldK[g];
       j.tile_rows = tr;
-      const int64_t KT = (K + TK - 1) / TK;
-      const int64_t padded = (rows + tr - 1) / tr * tr;
       jobs[side].push_back(j);
       elems[side] += rows * K;
-      row_start[side].push_back(rows);
-      warp_start[side].push_back(padded / 8 * KT);
     }
   }
-  auto make = [&](const std::vector<SliceJob>& js, const std::vector<int64_t>& rc, const std::vector<int64_t>& wc,
-                  int64_t el) {
+  auto make = [&](std::vector<SliceJob> js, int64_t el) {
+    const std::vector<int2> items = tnx_slice_schedule(js);
     StepPlan::Jobs J;
-    std::vector<int64_t> rs(1, 0), ws(1, 0);
-    for (size_t i = 0; i < js.size(); ++i) {
-      rs.push_back(rs.back() + rc[i]);
-      ws.push_back(ws.back() + wc[i]);
-    }
     J.n = (int)js.size();
-    J.rows = rs.back();
-    J.warps = ws.back();
+    J.nitems = (int64_t)items.size();
     J.elems = el;
     J.d = p.upload(js);
-    J.row_start = p.upload(rs);
-    J.warp_start = p.upload(ws);
+    J.items = p.upload(items);
     J.h = js;
-    J.hrows = rc;
-    J.hwarps = wc;
     return J;
   };
   std::vector<SliceJob> all = jobs[0];
   all.insert(all.end(), jobs[1].begin(), jobs[1].end());
-  std::vector<int64_t> rall = row_start[0], wall = warp_start[0];
-  rall.insert(rall.end(), row_start[1].begin(), row_start[1].end());
-  wall.insert(wall.end(), warp_start[1].begin(), warp_start[1].end());
-  s.jobsA = make(jobs[0], row_start[0], warp_start[0], elems[0]);
-  s.jobsB = make(jobs[1], row_start[1], warp_start[1], elems[1]);
-  s.jobsAll = make(all, rall, wall, elems[0] + elems[1]);
+  s.jobsA = make(jobs[0], elems[0]);
+  s.jobsB = make(jobs[1], elems[1]);
+  s.jobsAll = make(all, elems[0] + elems[1]);
   s.slice_elems = elems[0] + elems[1];
   std::vector<SplitGroup> sg(G);
   std::vector<GemmTile> tiles;
@@ -137,8 +142,7 @@ void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool n
   const StepPlan::Jobs* J = (needA && needB) ? &s.jobsAll : needA ? &s.jobsA : needB ? &s.jobsB : nullptr;
   if (J && J->n) {
     ProfScope ps(p.ctx, st, TNX_KC_SLICE, (double)J->elems * (8.0 + 8.0 + 2.0 * p.nslice));
-    CUDA_CHECK(tnx_launch_row_exponents(J->d, J->row_start, J->n, J->rows, p.d_slots, st));
-    CUDA_CHECK(tnx_launch_slices(J->d, J->warp_start, J->n, J->warps, p.nslice, p.beta, f16, p.d_slots, st));
+    CUDA_CHECK(tnx_launch_slices(J->d, J->items, J->nitems, p.nslice, p.beta, f16, p.d_slots, st));
   }
   ProfScope ps(p.ctx, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
   CUDA_CHECK(tnx_launch_gemm_split(s.dSG, s.dST, s.nstiles, p.nslice, p.beta, f16, p.d_slots, p.ctx->d_status, st));
