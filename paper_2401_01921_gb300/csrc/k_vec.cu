@@ -90,12 +90,41 @@ __global__ void lanczos_init_kernel(LanczosDev L, const double* v0) {
 __global__ void set_slot_kernel(double** slot, double* p) { *slot = p; }
 
 // partial[b*m + i] = <V_i, w> over this block's contiguous chunk, i < m.  A
-// fixed grid of MD_BLOCKS blocks keeps the number of partial sums (and so the
-// FP64 additions of the reduction tree) bounded; each thread keeps 16 running
-// sums, w is read once per group of 16 vectors, and the block reduction goes
-// through shared memory: 16 rows of MD_T values, 8 threads per row.
+// grid of multidot_blocks(n) blocks keeps the number of partial sums (and so the
+// FP64 additions of the reduction tree) bounded; each thread keeps NG <= 16
+// running sums (NG fixed at compile time, so no FP64 instruction is issued for
+// a vector that does not exist), w is read once per group of vectors, and the
+// block reduction goes through shared memory: 16 rows of MD_T values, 8
+// threads per row.  FP64 issue slots are scarce on this part, so the grid is
+// only large enough to keep the loads in flight.
 constexpr int MD_T = 128;
-constexpr int MD_BLOCKS = 608;   // 4 per SM: enough warps in flight to hide load latency
+constexpr int MD_BLOCKS_MAX = 608;
+
+// Blocks of the multidot kernel: about 416 vector entries per block (an
+// L2-resident basis is bound by FP64 issue, where fewer partial sums help),
+// rounded to a multiple of the SM count, at least 1 and at most 4 per SM (a
+// basis in HBM needs the loads of that many blocks in flight).
+int multidot_blocks(int64_t n) {
+  int64_t b = (n / 416 + 151) / 152 * 152;
+  if (b < 152) b = 152;
+  if (b > MD_BLOCKS_MAX) b = MD_BLOCKS_MAX;
+  return (int)b;
+}
+
+template <int NG>
+__device__ __forceinline__ void multidot_group(const LanczosDev& L, int g0, int64_t c0, int64_t c1,
+                                               double (*sh)[MD_T + 1]) {
+  double acc[NG];
+#pragma unroll
+  for (int i = 0; i < NG; ++i) acc[i] = 0.0;
+  for (int64_t x = c0 + threadIdx.x; x < c1; x += MD_T) {
+    const double wx = L.w[x];
+#pragma unroll
+    for (int i = 0; i < NG; ++i) acc[i] = fma(L.V[(int64_t)(g0 + i) * L.n + x], wx, acc[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < NG; ++i) sh[i][threadIdx.x] = acc[i];
+}
 
 __global__ void __launch_bounds__(MD_T) multidot_kernel(LanczosDev L, int m) {
   __shared__ double sh[16][MD_T + 1];
@@ -103,26 +132,36 @@ __global__ void __launch_bounds__(MD_T) multidot_kernel(LanczosDev L, int m) {
   const int64_t chunk = (L.n + gridDim.x - 1) / gridDim.x;
   const int64_t c0 = chunk * blockIdx.x, c1 = min(L.n, c0 + chunk);
   for (int g0 = 0; g0 < m; g0 += 16) {
-    double acc[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) acc[i] = 0.0;
-    for (int64_t x = c0 + threadIdx.x; x < c1; x += MD_T) {
-      const double wx = L.w[x];
-#pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (g0 + i < m) acc[i] = fma(L.V[(int64_t)(g0 + i) * L.n + x], wx, acc[i]);
+    const int ng = m - g0 < 16 ? m - g0 : 16;
+    switch (ng) {
+      case 1: multidot_group<1>(L, g0, c0, c1, sh); break;
+      case 2: multidot_group<2>(L, g0, c0, c1, sh); break;
+      case 3: multidot_group<3>(L, g0, c0, c1, sh); break;
+      case 4: multidot_group<4>(L, g0, c0, c1, sh); break;
+      case 5: multidot_group<5>(L, g0, c0, c1, sh); break;
+      case 6: multidot_group<6>(L, g0, c0, c1, sh); break;
+      case 7: multidot_group<7>(L, g0, c0, c1, sh); break;
+      case 8: multidot_group<8>(L, g0, c0, c1, sh); break;
+      case 9: multidot_group<9>(L, g0, c0, c1, sh); break;
+      case 10: multidot_group<10>(L, g0, c0, c1, sh); break;
+      case 11: multidot_group<11>(L, g0, c0, c1, sh); break;
+      case 12: multidot_group<12>(L, g0, c0, c1, sh); break;
+      case 13: multidot_group<13>(L, g0, c0, c1, sh); break;
+      case 14: multidot_group<14>(L, g0, c0, c1, sh); break;
+      case 15: multidot_group<15>(L, g0, c0, c1, sh); break;
+      default: multidot_group<16>(L, g0, c0, c1, sh); break;
     }
-#pragma unroll
-    for (int i = 0; i < 16; ++i) sh[i][threadIdx.x] = acc[i];
     __syncthreads();
     // thread t sums 16 consecutive entries of row t/8, then 8 partners combine
     const int row = threadIdx.x >> 3, part = threadIdx.x & 7;
-    double v = 0.0;
+    if (row < ng) {
+      double v = 0.0;
 #pragma unroll
-    for (int q = 0; q < MD_T / 8; ++q) v += sh[row][part * (MD_T / 8) + q];
+      for (int q = 0; q < MD_T / 8; ++q) v += sh[row][part * (MD_T / 8) + q];
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, 8);
-    if (part == 0 && g0 + row < m) L.partial[(int64_t)blockIdx.x * m + g0 + row] = v;
+      for (int o = 4; o > 0; o >>= 1) v += __shfl_down_sync(0xffu << (threadIdx.x & 24), v, o, 8);
+      if (part == 0) L.partial[(int64_t)blockIdx.x * m + g0 + row] = v;
+    }
     __syncthreads();
   }
 }
@@ -183,6 +222,7 @@ __global__ void __launch_bounds__(RT) lanczos_beta_decide_kernel(LanczosDev L, i
   if (threadIdx.x == 0) {
     const double beta = sqrt(acc);
     L.beta[j + 1] = beta;
+    L.scratch[3 * L.nmax + 3] = 1.0 / beta;   // for the normalising kernel
     L.state[0] = j + 1;
     if (last || beta < 1e-14 * s_amax) L.state[1] = 1;
     else *next_slot = L.V + (int64_t)(j + 1) * L.n;
@@ -191,7 +231,7 @@ __global__ void __launch_bounds__(RT) lanczos_beta_decide_kernel(LanczosDev L, i
 
 __global__ void lanczos_normalize_kernel(LanczosDev L, int j) {
   if (stopped(L.state)) return;
-  const double inv = 1.0 / L.beta[j + 1];
+  const double inv = L.scratch[3 * L.nmax + 3];   // 1 / beta_{j+1}, one FP64 division per step
   double* vn = L.V + (int64_t)(j + 1) * L.n;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += (int64_t)gridDim.x * blockDim.x)
     vn[i] = L.w[i] * inv;
@@ -354,10 +394,11 @@ cudaError_t tnx_launch_lanczos_set_input(double** slot_ptr, const LanczosDev& L,
 cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, double** next_slot, cudaStream_t st) {
   const int nb = grid_for(L.n);
   const int m = j + 1;
+  const int mb = multidot_blocks(L.n);
   for (int pass = 0; pass < 2; ++pass) {
-    multidot_kernel<<<MD_BLOCKS, MD_T, 0, st>>>(L, m);
+    multidot_kernel<<<mb, MD_T, 0, st>>>(L, m);
     tnx_note_launch(1);
-    multidot_finalize_kernel<<<m, RT, 0, st>>>(L, m, MD_BLOCKS, pass == 0 ? j : -1);
+    multidot_finalize_kernel<<<m, RT, 0, st>>>(L, m, mb, pass == 0 ? j : -1);
     tnx_note_launch(1);
     gs_update_kernel<<<nb, RT, 0, st>>>(L, m, pass == 1);
     tnx_note_launch(1);
