@@ -266,6 +266,7 @@ extern "C" tnx_status tnx_batch_launch_into(tnx_batch* b, tnx_tensor* const* out
         tnx_capture_graph(c, c->stream, *b->graph, [&] { enqueue_batch(*b, c->stream); });
       }
       CUDA_CHECK(cudaGraphLaunch(b->graph->exec, c->stream));
+      tnx_note_launch(b->graph->nlaunch);
       if (c->prof) {
         CUDA_CHECK(cudaStreamSynchronize(c->stream));
         prof_accumulate(c, b->graph->recs);

@@ -44,8 +44,16 @@ DevBuf::~DevBuf() { if (ctx && p) ctx->dfree(p, bytes); }
 
 // ----------------------------------------------------------------- counters
 static std::atomic<long long> g_launches{0};
+// While a thread captures a CUDA graph, its launches are counted into the
+// graph's record instead (they run when the graph is launched).
+static thread_local long long* t_capture_count = nullptr;
 
-void tnx_note_launch(int n) { g_launches += n; }
+void tnx_note_launch(long long n) {
+  if (t_capture_count) *t_capture_count += n;
+  else g_launches += n;
+}
+
+void tnx_count_into(long long* c) { t_capture_count = c; }
 
 extern "C" tnx_status tnx_kernel_launches(int64_t* n) {
   if (!n) return TNX_ERR_ARG;

@@ -105,7 +105,8 @@ struct MatchArgs {
 };
 
 // Counts kernel launches made by this library (defined in tnx_host.cpp).
-void tnx_note_launch(int n);
+void tnx_note_launch(long long n);   // kernel launches (into a graph's record while capturing)
+void tnx_count_into(long long* c);    // nullptr: count globally again
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files).  All enqueue on `st`.

@@ -1119,16 +1119,20 @@ void enqueue_plan(Plan& p, cudaStream_t st, uint64_t fixed = 0) {
 void capture_graph(tnx_ctx* c, cudaStream_t st, GraphRec& g, const std::function<void()>& body) {
   g.prof = c->prof;
   c->capture_recs = &g.recs;
+  g.nlaunch = 0;
+  tnx_count_into(&g.nlaunch);
   CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   try {
     body();
   } catch (...) {
+    tnx_count_into(nullptr);
     cudaGraph_t gr = nullptr;
     cudaStreamEndCapture(st, &gr);
     if (gr) cudaGraphDestroy(gr);
     c->capture_recs = nullptr;
     throw;
   }
+  tnx_count_into(nullptr);
   c->capture_recs = nullptr;
   cudaGraph_t gr = nullptr;
   CUDA_CHECK(cudaStreamEndCapture(st, &gr));
@@ -1175,6 +1179,7 @@ void tnx_apply_enqueue(tnx_network* net, tnx_tensor* out, cudaStream_t st) {
       capture_graph(c, st, *p->apply_graph, [&] { enqueue_plan(*p, st); });
     }
     CUDA_CHECK(cudaGraphLaunch(p->apply_graph->exec, st));
+    tnx_note_launch(p->apply_graph->nlaunch);
     if (c->prof) {
       CUDA_CHECK(cudaStreamSynchronize(st));
       prof_accumulate(c, p->apply_graph->recs);
@@ -1483,6 +1488,7 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
       capture_graph(ctx, st, *lc->graph, body);
     }
     CUDA_CHECK(cudaGraphLaunch(lc->graph->exec, st));
+    tnx_note_launch(lc->graph->nlaunch);
   } else {
     body();
   }

@@ -82,6 +82,7 @@ struct StepPlan {
 struct GraphRec {
   cudaGraphExec_t exec = nullptr;
   std::vector<ProfRec> recs;
+  long long nlaunch = 0;          // kernel launches inside the graph (counted per replay)
   bool prof = false;
   ~GraphRec() {
     if (exec) cudaGraphExecDestroy(exec);

@@ -324,3 +324,25 @@ def test_sparse_order_search(ctx, name):
         assert got == "(L,((psi,R),(W1,W2)))"
     onet.set_order(False, got)
     assert rel_fro(net.launch(B["psi"]).block_dict(), onet.launch()) <= TOL_F64
+
+
+def test_launch_counter_counts_graph_replays(ctx):
+    """Applies replayed from a CUDA graph count their kernels on every replay, and
+    the capture itself counts nothing."""
+    import paper_2401_01921_gb300 as tnx
+    wl = I.heisenberg_workload(40, 9)
+    net, T, B = lib_heff(ctx, wl, prec="split_bf16")
+    out = tnx.Tensor(ctx, B["psi"])
+    net.launch_into(out)   # plan + capture + first replay
+    ctx.sync()
+    n0 = tnx.kernel_launches()
+    net.launch_into(out)
+    ctx.sync()
+    n1 = tnx.kernel_launches()
+    net.launch_into(out)
+    net.launch_into(out)
+    ctx.sync()
+    n2 = tnx.kernel_launches()
+    per_apply = n1 - n0
+    assert per_apply >= 2 * net.nsteps()   # at least a relayout and a product per step
+    assert n2 - n1 == 2 * per_apply
