@@ -337,6 +337,14 @@ enum { TNX_KC_MATCH = 0, TNX_KC_RELAYOUT = 1, TNX_KC_GEMM = 2, TNX_KC_SLICE = 3,
  * stream with CUDA events (adds two event records per launch); 0 stops.
  * Resets the accumulated figures either way. */
 tnx_status tnx_profile_enable(tnx_ctx* ctx, int enable);
+/* As tnx_profile_enable, for the classes whose bit (1 << TNX_KC_*) is set in
+ * class_mask only (0 stops): the event records of the other classes are left
+ * out of the stream and of captured graphs.  With TNX_PROF_LAST_APPLY also
+ * set, a Lanczos solve times only the operator apply of its last step (event
+ * records in a captured graph cost time of their own; a solve's applies run
+ * the same kernels on the same shapes). */
+#define TNX_PROF_LAST_APPLY 0x80000000u
+tnx_status tnx_profile_classes(tnx_ctx* ctx, uint32_t class_mask);
 /* Synchronises the stream and returns, per kernel class (arrays of
  * TNX_KC_COUNT entries, any may be NULL): summed device milliseconds, number
  * of launches, and the algorithmic work of those launches (useful flops for

@@ -101,6 +101,7 @@ _SIGS = {
     "tnx_profile_enable": (C.c_int, [_p, C.c_int]),
     "tnx_profile_read": (C.c_int, [_p, C.POINTER(C.c_double), _i64p, C.POINTER(C.c_double)]),
     "tnx_kernel_launches": (C.c_int, [_i64p]),
+    "tnx_profile_classes": (C.c_int, [C.c_void_p, C.c_uint32]),
 }
 KERNEL_CLASSES = ["match", "relayout", "gemm", "slice", "vector", "final", "skinny"]
 
@@ -179,9 +180,18 @@ class Context:
             lib().tnx_ctx_destroy(self.h)
             self.h = None
 
-    def profile(self, enable: bool):
-        """tnx_profile_enable: CUDA-event timing of every kernel class."""
-        self.check(lib().tnx_profile_enable(self.h, 1 if enable else 0))
+    def profile(self, enable: bool, classes=None, last_apply_only: bool = False):
+        """tnx_profile_enable / tnx_profile_classes: CUDA-event timing of every kernel
+        class, or only of the named ones (e.g. classes=["gemm"]); last_apply_only:
+        Lanczos solves time only the apply of their last step."""
+        if classes is None and not last_apply_only:
+            self.check(lib().tnx_profile_enable(self.h, 1 if enable else 0))
+        else:
+            names = KERNEL_CLASSES if classes is None else classes
+            mask = sum(1 << KERNEL_CLASSES.index(c) for c in names) if enable else 0
+            if mask and last_apply_only:
+                mask |= 0x80000000
+            self.check(lib().tnx_profile_classes(self.h, mask))
 
     def profile_read(self) -> dict:
         """{class: (milliseconds, launches, algorithmic work)} since profile(True)."""

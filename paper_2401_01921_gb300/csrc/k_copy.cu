@@ -138,6 +138,7 @@ __device__ __forceinline__ void copy_run(const CopyTask& t, const double* src, d
 // 32 x 32 tile of a transposing task.
 __global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ tasks, const int4* __restrict__ chunks,
                                                   double* const* __restrict__ slots) {
+  tnx_grid_dependency();
   __shared__ CopyTask st[TNX_COPY_PACK];
   __shared__ int sstart[TNX_COPY_PACK + 1];
   const int4 ch = chunks[blockIdx.x];
@@ -196,7 +197,10 @@ __global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ t
 cudaError_t tnx_launch_copy(const CopyTask* tasks, const int4* chunks, int nchunks, double* const* slots,
                             cudaStream_t st) {
   if (nchunks <= 0) return cudaSuccess;
-  copy_kernel<<<nchunks, CT, 0, st>>>(tasks, chunks, slots);
+  {
+    const cudaError_t le = tnx_launch(copy_kernel, dim3(nchunks), dim3(CT), 0, st, tasks, chunks, slots);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
   return cudaGetLastError();
 }

@@ -21,6 +21,7 @@ template <typename TC>
 __global__ void __launch_bounds__(256) gemm_kernel(const GemmGroup* __restrict__ groups,
                                                    const GemmTile* __restrict__ tiles,
                                                    double* const* __restrict__ slots) {
+  tnx_grid_dependency();
   __shared__ TC As[BK][BM + 1];
   __shared__ TC Bs[BK][BN + 1];
   const GemmTile tl = tiles[blockIdx.x];
@@ -99,6 +100,7 @@ __device__ __forceinline__ void skinny_rows(const GemmGroup& g, const GemmTile& 
 __global__ void __launch_bounds__(128) gemm_skinny_kernel(const GemmGroup* __restrict__ groups,
                                                           const GemmTile* __restrict__ tiles,
                                                           double* const* __restrict__ slots) {
+  tnx_grid_dependency();
   __shared__ double Bs[64][SK_MAXK];
   const GemmTile tl = tiles[blockIdx.x];
   const GemmGroup g = groups[tl.group];
@@ -124,7 +126,10 @@ __global__ void __launch_bounds__(128) gemm_skinny_kernel(const GemmGroup* __res
 cudaError_t tnx_launch_gemm_skinny(const GemmGroup* groups, const GemmTile* tiles, int ntiles, double* const* slots,
                                    cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
-  gemm_skinny_kernel<<<ntiles, 128, 0, st>>>(groups, tiles, slots);
+  {
+    const cudaError_t le = tnx_launch(gemm_skinny_kernel, dim3(ntiles), dim3(128), 0, st, groups, tiles, slots);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
   return cudaGetLastError();
 }
@@ -132,7 +137,10 @@ cudaError_t tnx_launch_gemm_skinny(const GemmGroup* groups, const GemmTile* tile
 cudaError_t tnx_launch_gemm_f64(const GemmGroup* groups, const GemmTile* tiles, int ntiles,
                                 double* const* slots, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
-  gemm_kernel<double><<<ntiles, 256, 0, st>>>(groups, tiles, slots);
+  {
+    const cudaError_t le = tnx_launch(gemm_kernel<double>, dim3(ntiles), dim3(256), 0, st, groups, tiles, slots);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
   return cudaGetLastError();
 }
@@ -140,7 +148,10 @@ cudaError_t tnx_launch_gemm_f64(const GemmGroup* groups, const GemmTile* tiles, 
 cudaError_t tnx_launch_gemm_f32(const GemmGroup* groups, const GemmTile* tiles, int ntiles,
                                 double* const* slots, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
-  gemm_kernel<float><<<ntiles, 256, 0, st>>>(groups, tiles, slots);
+  {
+    const cudaError_t le = tnx_launch(gemm_kernel<float>, dim3(ntiles), dim3(256), 0, st, groups, tiles, slots);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
   return cudaGetLastError();
 }

@@ -209,6 +209,7 @@ __device__ __forceinline__ uint16_t slice_bits(uint32_t s, uint32_t neg, int f16
 __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restrict__ jobs,
                                                          const int2* __restrict__ items, int64_t total, int nslice,
                                                          int beta, int f16, double* const* __restrict__ slots) {
+  tnx_grid_dependency();
   __shared__ unsigned long long s_max[8][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int r8 = lane >> 2, kq = lane & 3;
@@ -328,6 +329,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
                                                              const GemmTile* __restrict__ tiles, int ntiles, int beta,
                                                              int f16, double* const* __restrict__ slots,
                                                              int32_t* status) {
+  tnx_grid_dependency();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* ring = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int STAGE_BYTES = NS * (ATILE + BTILE);
@@ -536,7 +538,11 @@ cudaError_t tnx_launch_slices(const SliceJob* jobs, const int2* items, int64_t t
   if (nslice < 1 || nslice > MAXN || beta < 1 || beta > 8 || nslice * beta > 53) return cudaErrorInvalidValue;
   int64_t blocks = total_items;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  slice_rows_kernel<<<(int)blocks, 256, 0, st>>>(jobs, items, total_items, nslice, beta, f16, slots);
+  {
+    const cudaError_t le = tnx_launch(slice_rows_kernel, dim3((int)blocks), dim3(256), 0, st,
+                                      jobs, items, total_items, nslice, beta, f16, slots);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
   return cudaGetLastError();
 }
@@ -560,7 +566,11 @@ cudaError_t tnx_launch_gemm_split(const SplitGroup* groups, const GemmTile* tile
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  split_gemm_kernel<MAXN><<<grid, SPLIT_THREADS, smem, st>>>(groups, tiles, ntiles, beta, f16, slots, status);
+  {
+    const cudaError_t le = tnx_launch(split_gemm_kernel<MAXN>, dim3(grid), dim3(SPLIT_THREADS), smem, st,
+                                      groups, tiles, ntiles, beta, f16, slots, status);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
   return cudaGetLastError();
 }

@@ -42,11 +42,13 @@ __device__ double block_sum(double v, double* sh) {
 __device__ __forceinline__ bool stopped(const int32_t* state) { return *(volatile const int32_t*)(state + 1) != 0; }
 
 __global__ void scale_kernel(double* x, int64_t n, double a) {
+  tnx_grid_dependency();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] *= a;
 }
 
 __global__ void add_scalar_kernel(double* x, int64_t n, double a) {
+  tnx_grid_dependency();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] += a;
 }
@@ -54,6 +56,7 @@ __global__ void add_scalar_kernel(double* x, int64_t n, double a) {
 // partial[b] = sum over this block's grid-stride share of x*y
 __global__ void __launch_bounds__(RT) dot_partial_kernel(const double* __restrict__ x, const double* __restrict__ y,
                                                          int64_t n, double* partial, const int32_t* state) {
+  tnx_grid_dependency();
   __shared__ double sh[32];
   if (state && stopped(state)) return;
   double acc = 0.0;
@@ -66,6 +69,7 @@ __global__ void __launch_bounds__(RT) dot_partial_kernel(const double* __restric
 // mode 0: out = sum; mode 1: out = sqrt(sum)
 __global__ void __launch_bounds__(RT) finalize_kernel(const double* partial, int np, double* out, int mode,
                                                       const int32_t* state) {
+  tnx_grid_dependency();
   __shared__ double sh[32];
   if (state && stopped(state)) return;
   double acc = 0.0;
@@ -76,6 +80,7 @@ __global__ void __launch_bounds__(RT) finalize_kernel(const double* partial, int
 
 // ---------------------------------------------------------------- Lanczos
 __global__ void lanczos_init_kernel(LanczosDev L, const double* v0) {
+  tnx_grid_dependency();
   // V[0] = v0 / ||v0|| (norm already in L.scratch[0]); state reset
   const double inv = 1.0 / L.scratch[0];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += (int64_t)gridDim.x * blockDim.x)
@@ -87,7 +92,10 @@ __global__ void lanczos_init_kernel(LanczosDev L, const double* v0) {
   }
 }
 
-__global__ void set_slot_kernel(double** slot, double* p) { *slot = p; }
+__global__ void set_slot_kernel(double** slot, double* p) {
+  tnx_grid_dependency();
+  *slot = p;
+}
 
 // partial[b*m + i] = <V_i, w> over this block's contiguous chunk, i < m.  A
 // grid of multidot_blocks(n) blocks keeps the number of partial sums (and so the
@@ -127,6 +135,7 @@ __device__ __forceinline__ void multidot_group(const LanczosDev& L, int g0, int6
 }
 
 __global__ void __launch_bounds__(MD_T) multidot_kernel(LanczosDev L, int m) {
+  tnx_grid_dependency();
   __shared__ double sh[16][MD_T + 1];
   if (stopped(L.state)) return;
   const int64_t chunk = (L.n + gridDim.x - 1) / gridDim.x;
@@ -169,6 +178,7 @@ __global__ void __launch_bounds__(MD_T) multidot_kernel(LanczosDev L, int m) {
 // coef[i] = sum_b partial[b*m + i]   (one block per i, fixed order);
 // on the first pass, the coefficient of v_j is alpha_j = <v_j, H v_j>.
 __global__ void __launch_bounds__(RT) multidot_finalize_kernel(LanczosDev L, int m, int nb, int alpha_j) {
+  tnx_grid_dependency();
   __shared__ double sh[32];
   if (stopped(L.state)) return;
   const int i = blockIdx.x;
@@ -184,6 +194,7 @@ __global__ void __launch_bounds__(RT) multidot_finalize_kernel(LanczosDev L, int
 // w -= sum_i coef[i] V_i; with norm != 0 also partial[b] = sum of the new w^2
 // over this block's grid-stride share (fixed order).
 __global__ void __launch_bounds__(RT) gs_update_kernel(LanczosDev L, int m, int norm) {
+  tnx_grid_dependency();
   __shared__ double c[512];
   __shared__ double sh[32];
   if (stopped(L.state)) return;
@@ -206,6 +217,7 @@ __global__ void __launch_bounds__(RT) gs_update_kernel(LanczosDev L, int m, int 
 // the next apply's input slot at v_{j+1} (which the next kernel writes)
 __global__ void __launch_bounds__(RT) lanczos_beta_decide_kernel(LanczosDev L, int j, int nb, int last,
                                                                  double** next_slot) {
+  tnx_grid_dependency();
   __shared__ double sh[32];
   __shared__ double s_amax;
   if (stopped(L.state)) return;
@@ -230,6 +242,7 @@ __global__ void __launch_bounds__(RT) lanczos_beta_decide_kernel(LanczosDev L, i
 }
 
 __global__ void lanczos_normalize_kernel(LanczosDev L, int j) {
+  tnx_grid_dependency();
   if (stopped(L.state)) return;
   const double inv = L.scratch[3 * L.nmax + 3];   // 1 / beta_{j+1}, one FP64 division per step
   double* vn = L.V + (int64_t)(j + 1) * L.n;
@@ -255,6 +268,7 @@ __device__ int sturm_count(const double* a, const double* b, int k, double x) {
 // shrinking.  Then inverse iteration (Thomas algorithm, 3 sweeps) for the
 // eigenvector y on thread 0.  beta[j] couples rows j-1 and j (beta[0] unused).
 __global__ void __launch_bounds__(RT) tridiag_kernel(LanczosDev L) {
+  tnx_grid_dependency();
   __shared__ double s_lo, s_hi;
   __shared__ int s_first;
   const int k = L.state[0];
@@ -326,6 +340,7 @@ __global__ void __launch_bounds__(RT) tridiag_kernel(LanczosDev L) {
 }
 
 __global__ void __launch_bounds__(RT) ritz_kernel(LanczosDev L, double* out) {
+  tnx_grid_dependency();
   __shared__ double c[512];
   const int k = L.state[0];
   for (int i = threadIdx.x; i < k; i += RT) c[i] = L.y[i];
@@ -348,40 +363,65 @@ int tnx_reduce_blocks(int64_t n) { return grid_for(n); }
 
 cudaError_t tnx_launch_scale(double* x, int64_t n, double alpha, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  scale_kernel<<<grid_for(n), RT, 0, st>>>(x, n, alpha);
+  {
+    const cudaError_t le = tnx_launch(scale_kernel, dim3(grid_for(n)), dim3(RT), 0, st, x, n, alpha);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
   return cudaGetLastError();
 }
 
 cudaError_t tnx_launch_add_scalar(double* x, int64_t n, double alpha, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  add_scalar_kernel<<<grid_for(n), RT, 0, st>>>(x, n, alpha);
+  {
+    const cudaError_t le = tnx_launch(add_scalar_kernel, dim3(grid_for(n)), dim3(RT), 0, st, x, n, alpha);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
   return cudaGetLastError();
 }
 
 cudaError_t tnx_launch_norm2(const double* x, int64_t n, double* partial, double* out, cudaStream_t st) {
   const int nb = grid_for(n);
-  dot_partial_kernel<<<nb, RT, 0, st>>>(x, x, n, partial, nullptr);
+  {
+    const cudaError_t le = tnx_launch(dot_partial_kernel, dim3(nb), dim3(RT), 0, st, x, x, n, partial, nullptr);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
-  finalize_kernel<<<1, RT, 0, st>>>(partial, nb, out, 1, nullptr);
+  {
+    const cudaError_t le = tnx_launch(finalize_kernel, dim3(1), dim3(RT), 0, st, partial, nb, out, 1, nullptr);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
   return cudaGetLastError();
 }
 
 cudaError_t tnx_launch_lanczos_init(const LanczosDev& L, const double* v0, cudaStream_t st) {
   const int nb = grid_for(L.n);
-  dot_partial_kernel<<<nb, RT, 0, st>>>(v0, v0, L.n, L.partial, nullptr);
+  {
+    const cudaError_t le = tnx_launch(dot_partial_kernel, dim3(nb), dim3(RT), 0, st, v0, v0, L.n, L.partial, nullptr);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
-  finalize_kernel<<<1, RT, 0, st>>>(L.partial, nb, L.scratch, 1, nullptr);
+  {
+    const cudaError_t le = tnx_launch(finalize_kernel, dim3(1), dim3(RT), 0, st,
+                                      L.partial, nb, L.scratch, 1, nullptr);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
-  lanczos_init_kernel<<<nb, RT, 0, st>>>(L, v0);
+  {
+    const cudaError_t le = tnx_launch(lanczos_init_kernel, dim3(nb), dim3(RT), 0, st, L, v0);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
   return cudaGetLastError();
 }
 
 cudaError_t tnx_launch_lanczos_set_input(double** slot_ptr, const LanczosDev& L, int j, cudaStream_t st) {
-  set_slot_kernel<<<1, 1, 0, st>>>(slot_ptr, L.V + (int64_t)j * L.n);
+  {
+    const cudaError_t le = tnx_launch(set_slot_kernel, dim3(1), dim3(1), 0, st, slot_ptr, L.V + (int64_t)j * L.n);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
   return cudaGetLastError();
 }
@@ -396,25 +436,48 @@ cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, double** next_sl
   const int m = j + 1;
   const int mb = multidot_blocks(L.n);
   for (int pass = 0; pass < 2; ++pass) {
-    multidot_kernel<<<mb, MD_T, 0, st>>>(L, m);
+    {
+      const cudaError_t le = tnx_launch(multidot_kernel, dim3(mb), dim3(MD_T), 0, st, L, m);
+      if (le != cudaSuccess) return le;
+    }
     tnx_note_launch(1);
-    multidot_finalize_kernel<<<m, RT, 0, st>>>(L, m, mb, pass == 0 ? j : -1);
+    {
+      const cudaError_t le = tnx_launch(multidot_finalize_kernel, dim3(m), dim3(RT), 0, st,
+                                        L, m, mb, pass == 0 ? j : -1);
+      if (le != cudaSuccess) return le;
+    }
     tnx_note_launch(1);
-    gs_update_kernel<<<nb, RT, 0, st>>>(L, m, pass == 1);
+    {
+      const cudaError_t le = tnx_launch(gs_update_kernel, dim3(nb), dim3(RT), 0, st, L, m, pass == 1);
+      if (le != cudaSuccess) return le;
+    }
     tnx_note_launch(1);
   }
-  lanczos_beta_decide_kernel<<<1, RT, 0, st>>>(L, j, nb, j == L.nmax - 1, next_slot);
+  {
+    const cudaError_t le = tnx_launch(lanczos_beta_decide_kernel, dim3(1), dim3(RT), 0, st,
+                                      L, j, nb, j == L.nmax - 1, next_slot);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
-  lanczos_normalize_kernel<<<nb, RT, 0, st>>>(L, j);
+  {
+    const cudaError_t le = tnx_launch(lanczos_normalize_kernel, dim3(nb), dim3(RT), 0, st, L, j);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
   return cudaGetLastError();
 }
 
 cudaError_t tnx_launch_lanczos_finish(const LanczosDev& L, double* evec, cudaStream_t st) {
-  tridiag_kernel<<<1, RT, 0, st>>>(L);
+  {
+    const cudaError_t le = tnx_launch(tridiag_kernel, dim3(1), dim3(RT), 0, st, L);
+    if (le != cudaSuccess) return le;
+  }
   tnx_note_launch(1);
   if (evec) {
-    ritz_kernel<<<grid_for(L.n), RT, 0, st>>>(L, evec);
+    {
+      const cudaError_t le = tnx_launch(ritz_kernel, dim3(grid_for(L.n)), dim3(RT), 0, st, L, evec);
+      if (le != cudaSuccess) return le;
+    }
     tnx_note_launch(1);
   }
   return cudaGetLastError();

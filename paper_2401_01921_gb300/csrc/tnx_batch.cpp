@@ -284,8 +284,8 @@ extern "C" tnx_status tnx_batch_autotune(tnx_batch* b, tnx_tensor* const* outs, 
     check_fresh(*b);
     bind(*b, outs);
     tnx_ctx* c = b->ctx;
-    const bool prof = c->prof;
-    c->prof = false;
+    const uint32_t prof = c->prof;
+    c->prof = 0;
     const int cands[] = {0, 152, 304, 456};
     float best = 1e30f;
     int pick = 0;

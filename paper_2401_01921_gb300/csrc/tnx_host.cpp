@@ -80,7 +80,7 @@ static void record_event(tnx_ctx* c, cudaEvent_t e, cudaStream_t st) {
 }
 
 ProfScope::ProfScope(tnx_ctx* c_, cudaStream_t s_, int cls_, double work_) : c(c_), st(s_), cls(cls_), work(work_) {
-  if (c->prof) {
+  if ((c->prof >> cls) & 1u) {
     if (c->capture_recs) cudaEventCreate(&a);
     else a = c->get_event();
     record_event(c, a, st);
@@ -126,14 +126,19 @@ static void prof_drain(tnx_ctx* c) {
   c->prof_pending.clear();
 }
 
-extern "C" tnx_status tnx_profile_enable(tnx_ctx* ctx, int enable) {
+extern "C" tnx_status tnx_profile_classes(tnx_ctx* ctx, uint32_t class_mask) {
   if (!ctx) return TNX_ERR_ARG;
   return tnx_guard(ctx, [&] {
     CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
     prof_drain(ctx);
     for (int i = 0; i < TNX_KC_COUNT; ++i) ctx->prof_ms[i] = 0, ctx->prof_n[i] = 0, ctx->prof_work[i] = 0;
-    ctx->prof = enable != 0;
+    ctx->prof = class_mask & (((1u << TNX_KC_COUNT) - 1u) | TNX_PROF_LAST_APPLY);
+    if (!(ctx->prof & ((1u << TNX_KC_COUNT) - 1u))) ctx->prof = 0;
   });
+}
+
+extern "C" tnx_status tnx_profile_enable(tnx_ctx* ctx, int enable) {
+  return tnx_profile_classes(ctx, enable ? (1u << TNX_KC_COUNT) - 1u : 0u);
 }
 
 extern "C" tnx_status tnx_profile_read(tnx_ctx* ctx, double* ms, int64_t* launches, double* work) {

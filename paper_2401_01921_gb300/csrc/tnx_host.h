@@ -42,7 +42,7 @@ struct tnx_ctx {
   int32_t* d_status = nullptr; // device status word written by bounded waits (0 = ok)
   bool use_graphs = true;      // capture applies / Lanczos solves in CUDA graphs (needs a non-default stream)
   // profiler (CUDA events around kernel classes)
-  bool prof = false;
+  uint32_t prof = 0;                 // bit c set: kernel class c is timed
   std::vector<ProfRec> prof_pending;
   std::vector<cudaEvent_t> event_pool;
   double prof_ms[TNX_KC_COUNT] = {};

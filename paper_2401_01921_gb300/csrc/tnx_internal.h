@@ -1,6 +1,8 @@
 // Internal declarations shared by the host planner and the CUDA kernels.
 #pragma once
 
+#include <utility>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -105,6 +107,33 @@ struct MatchArgs {
 };
 
 // Counts kernel launches made by this library (defined in tnx_host.cpp).
+// Programmatic dependent launch: every kernel of the library starts with
+// tnx_grid_dependency(), which waits until the grids it depends on have
+// completed and their writes are visible.  A kernel launched with tnx_launch
+// may be launched as soon as every CTA of the previous kernel in the stream
+// has exited (no explicit early trigger: waiting CTAs would take SM slots
+// from the running kernel), so its launch overlaps the previous kernel's
+// completion; without the launch attribute the wait returns at once.
+#ifdef __CUDACC__
+__device__ __forceinline__ void tnx_grid_dependency() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t tnx_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+#endif
+
 void tnx_note_launch(long long n);   // kernel launches (into a graph's record while capturing)
 void tnx_count_into(long long* c);    // nullptr: count globally again
 

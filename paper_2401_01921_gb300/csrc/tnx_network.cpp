@@ -1471,7 +1471,18 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
     for (int j = 0; j < nsteps; ++j) {
       // the input slot points at v_0 here; each step kernel points it at v_{j+1}
       if (j == 0) CUDA_CHECK(tnx_launch_lanczos_set_input(p->d_slots + slot, L, 0, st));
-      enqueue_plan(*p, st, j == 0 ? 0 : fixed);
+      {
+        // TNX_PROF_LAST_APPLY: the events of the earlier applies are left out
+        const uint32_t prof = ctx->prof;
+        if ((prof & TNX_PROF_LAST_APPLY) && j != nsteps - 1) ctx->prof = 0;
+        try {
+          enqueue_plan(*p, st, j == 0 ? 0 : fixed);
+        } catch (...) {
+          ctx->prof = prof;
+          throw;
+        }
+        ctx->prof = prof;
+      }
       // bytes of one step: two Gram-Schmidt passes over j+1 vectors (dots
       // (j+1)n + n, update (j+1)n + 2n), norm folded in, scale (2n)
       ProfScope ps(ctx, st, TNX_KC_VECTOR, 8.0 * (double)n * (2 * (2.0 * (j + 1) + 3) + 2));

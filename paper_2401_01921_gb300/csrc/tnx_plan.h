@@ -83,7 +83,7 @@ struct GraphRec {
   cudaGraphExec_t exec = nullptr;
   std::vector<ProfRec> recs;
   long long nlaunch = 0;          // kernel launches inside the graph (counted per replay)
-  bool prof = false;
+  uint32_t prof = 0;              // profiled classes when captured
   ~GraphRec() {
     if (exec) cudaGraphExecDestroy(exec);
     for (auto& r : recs) {
