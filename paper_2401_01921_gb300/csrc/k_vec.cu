@@ -250,11 +250,13 @@ __global__ void lanczos_normalize_kernel(LanczosDev L, int j) {
     vn[i] = L.w[i] * inv;
 }
 
-__device__ int sturm_count(const double* a, const double* b, int k, double x) {
+// Sturm count on the shared-memory copy of T: number of negative pivots of the
+// LDL^T factorisation of T - xI (b2[j] = beta_j^2, b2[0] unused).
+__device__ int sturm_count(const double* a, const double* b2, int k, double x) {
   int cnt = 0;
   double d = 1.0;
   for (int j = 0; j < k; ++j) {
-    d = (a[j] - x) - (j > 0 ? (b[j] * b[j]) / d : 0.0);
+    d = (a[j] - x) - (j > 0 ? b2[j] / d : 0.0);
     if (d == 0.0) d = -1e-300;
     if (d < 0) ++cnt;
   }
@@ -267,35 +269,46 @@ __device__ int sturm_count(const double* a, const double* b, int k, double x) {
 // reaches 1 (the same test as bisection, RT points per round), until it stops
 // shrinking.  Then inverse iteration (Thomas algorithm, 3 sweeps) for the
 // eigenvector y on thread 0.  beta[j] couples rows j-1 and j (beta[0] unused).
+// T is copied to shared memory first: the sequential parts run on thread 0,
+// where every global-memory access would be a dependent trip to L2; the LU
+// factors of T - shift I are the same in every sweep and computed once.
+constexpr int TD_MAX = 512;   // Lanczos steps are limited to 500
+
 __global__ void __launch_bounds__(RT) tridiag_kernel(LanczosDev L) {
   tnx_grid_dependency();
+  __shared__ double sa[TD_MAX], sb[TD_MAX], sb2[TD_MAX], sl[TD_MAX], sy[TD_MAX];
   __shared__ double s_lo, s_hi;
   __shared__ int s_first;
   const int k = L.state[0];
-  const double* a = L.alpha;
-  const double* b = L.beta;
+  for (int j = threadIdx.x; j < k; j += RT) {
+    sa[j] = L.alpha[j];
+    sb[j] = L.beta[j];
+    sb2[j] = j > 0 ? sb[j] * sb[j] : 0.0;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     double lo = 0.0, hi = 0.0;
     for (int j = 0; j < k; ++j) {
-      const double r = (j > 0 ? fabs(b[j]) : 0.0) + (j + 1 < k ? fabs(b[j + 1]) : 0.0);
-      if (j == 0 || a[j] - r < lo) lo = a[j] - r;
-      if (j == 0 || a[j] + r > hi) hi = a[j] + r;
+      const double r = (j > 0 ? fabs(sb[j]) : 0.0) + (j + 1 < k ? fabs(sb[j + 1]) : 0.0);
+      if (j == 0 || sa[j] - r < lo) lo = sa[j] - r;
+      if (j == 0 || sa[j] + r > hi) hi = sa[j] + r;
     }
     s_lo = lo;
     s_hi = hi;
   }
   __syncthreads();
+  const double frac = (double)(threadIdx.x + 1) / (double)(RT + 1);
   for (int round = 0; round < 64; ++round) {
     const double lo = s_lo, hi = s_hi;
-    const double x = lo + (hi - lo) * (double)(threadIdx.x + 1) / (double)(RT + 1);
+    const double x = lo + (hi - lo) * frac;
     if (threadIdx.x == 0) s_first = RT;
     __syncthreads();
-    if (x > lo && x < hi && sturm_count(a, b, k, x) >= 1) atomicMin(&s_first, (int)threadIdx.x);
+    if (x > lo && x < hi && sturm_count(sa, sb2, k, x) >= 1) atomicMin(&s_first, (int)threadIdx.x);
     __syncthreads();
     if (threadIdx.x == 0) {
       const int f = s_first;
-      const double nlo = f == 0 ? lo : lo + (hi - lo) * (double)f / (double)(RT + 1);
-      const double nhi = f == RT ? hi : lo + (hi - lo) * (double)(f + 1) / (double)(RT + 1);
+      const double nlo = f == 0 ? lo : lo + (hi - lo) * ((double)f / (double)(RT + 1));
+      const double nhi = f == RT ? hi : lo + (hi - lo) * ((double)(f + 1) / (double)(RT + 1));
       s_lo = nlo > lo ? nlo : lo;
       s_hi = nhi < hi ? nhi : hi;
     }
@@ -308,35 +321,34 @@ __global__ void __launch_bounds__(RT) tridiag_kernel(LanczosDev L) {
   for (int it = 0; it < 200; ++it) {
     const double mid = 0.5 * (lo + hi);
     if (mid <= lo || mid >= hi) break;
-    if (sturm_count(a, b, k, mid) >= 1) hi = mid; else lo = mid;
+    if (sturm_count(sa, sb2, k, mid) >= 1) hi = mid; else lo = mid;
   }
   const double lam = hi;
   *L.eval = lam;
-  double* y = L.y;
-  double* dd = L.scratch;
-  double* rhs = L.scratch + L.nmax;
+  // LU of T - shift I (no pivoting): sa becomes the pivots, sl the multipliers
   const double shift = lam - 1e-13 * fmax(1.0, fabs(lam));
-  for (int j = 0; j < k; ++j) y[j] = 1.0 / sqrt((double)k);
+  for (int j = 0; j < k; ++j) sa[j] -= shift;
+  for (int j = 1; j < k; ++j) {
+    const double piv = sa[j - 1] != 0.0 ? sa[j - 1] : 1e-300;
+    sl[j] = sb[j] / piv;
+    sa[j] -= sl[j] * sb[j];
+  }
+  const double inv0 = 1.0 / sqrt((double)k);
+  for (int j = 0; j < k; ++j) sy[j] = inv0;
   for (int sweep = 0; sweep < 3; ++sweep) {
-    for (int j = 0; j < k; ++j) { dd[j] = a[j] - shift; rhs[j] = y[j]; }
-    for (int j = 1; j < k; ++j) {
-      const double piv = dd[j - 1] != 0.0 ? dd[j - 1] : 1e-300;
-      const double mm = b[j] / piv;
-      dd[j] -= mm * b[j];
-      rhs[j] -= mm * rhs[j - 1];
-    }
-    y[k - 1] = rhs[k - 1] / (dd[k - 1] != 0.0 ? dd[k - 1] : 1e-300);
-    for (int j = k - 2; j >= 0; --j) y[j] = (rhs[j] - b[j + 1] * y[j + 1]) / (dd[j] != 0.0 ? dd[j] : 1e-300);
+    for (int j = 1; j < k; ++j) sy[j] -= sl[j] * sy[j - 1];
+    sy[k - 1] = sy[k - 1] / (sa[k - 1] != 0.0 ? sa[k - 1] : 1e-300);
+    for (int j = k - 2; j >= 0; --j) sy[j] = (sy[j] - sb[j + 1] * sy[j + 1]) / (sa[j] != 0.0 ? sa[j] : 1e-300);
     double nrm = 0.0;
-    for (int j = 0; j < k; ++j) nrm += y[j] * y[j];
-    nrm = sqrt(nrm);
-    for (int j = 0; j < k; ++j) y[j] /= nrm;
+    for (int j = 0; j < k; ++j) nrm += sy[j] * sy[j];
+    const double inv = 1.0 / sqrt(nrm);
+    for (int j = 0; j < k; ++j) sy[j] *= inv;
   }
   int jm = 0;
   for (int j = 1; j < k; ++j)
-    if (fabs(y[j]) > fabs(y[jm])) jm = j;
-  if (y[jm] < 0)
-    for (int j = 0; j < k; ++j) y[j] = -y[j];
+    if (fabs(sy[j]) > fabs(sy[jm])) jm = j;
+  const double sgn = sy[jm] < 0 ? -1.0 : 1.0;
+  for (int j = 0; j < k; ++j) L.y[j] = sgn * sy[j];
 }
 
 __global__ void __launch_bounds__(RT) ritz_kernel(LanczosDev L, double* out) {
