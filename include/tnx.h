@@ -239,8 +239,10 @@ tnx_status tnx_lanczos(tnx_network* net, const char* vec_slot, tnx_tensor* v0, i
  * launch over all their charge sectors; a launch of the batch is one CUDA
  * graph.  Each network must be fully put; its plan is built now and the batch
  * keeps references (a network must outlive the batch; re-planning a network
- * invalidates the batch: TNX_ERR_ARG at launch).  No counterpart in the paper,
- * which contracts one network per call (Sec. 8). */
+ * invalidates the batch: TNX_ERR_ARG at launch).  A network that joins a batch
+ * keeps 64-wide split-GEMM tiles from then on (one merged launch needs one tile
+ * width).  No counterpart in the paper, which contracts one network per call
+ * (Sec. 8). */
 typedef struct tnx_batch tnx_batch;
 tnx_status tnx_batch_create(tnx_ctx* ctx, int nnet, tnx_network* const* nets, tnx_batch** out);
 tnx_status tnx_batch_destroy(tnx_batch* b);

@@ -44,16 +44,14 @@
 namespace {
 
 constexpr int TM = 128;            // tile rows (A)
-constexpr int TN = 64;             // tile columns (B rows)
 constexpr int TK = 32;             // K per stage
 constexpr int KC = 640;            // K per exact chunk
 constexpr int STAGES = 3;
 constexpr int MAXN = 6;            // slices
 constexpr int ATILE = TM * TK * 2; // bytes of one A slice tile (8 KB)
-constexpr int BTILE = TN * TK * 2; // bytes of one B slice tile (4 KB)
+// tile columns (B rows): TNV = 64 (wide) or 32 (narrow); one B slice tile is TNV * TK * 2 bytes
 constexpr long long WAIT_LIMIT = 2000000000LL;   // clock cycles (~1 s)
-constexpr int EPI_WARPS = 8;       // epilogue warps: two per TMEM lane quarter
-constexpr int ECOLS = TN / 2;      // tile columns per epilogue warp
+constexpr int EPI_WARPS = 8;       // epilogue warps: two per TMEM lane quarter, each takes half the columns
 constexpr int SPLIT_THREADS = 32 * (2 + EPI_WARPS);
 
 // ------------------------------------------------------------- PTX helpers
@@ -324,7 +322,7 @@ struct SplitShared {
 // up once per CTA; the stage ring and the chunk hand-off between the MMA warp
 // and the epilogue warps continue across tiles, so the producer streams the
 // next tile's slices while the epilogue drains the current one.
-template <int NS>
+template <int NS, int TNV>
 __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const SplitGroup* __restrict__ groups,
                                                              const GemmTile* __restrict__ tiles, int ntiles, int beta,
                                                              int f16, double* const* __restrict__ slots,
@@ -332,6 +330,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
   tnx_grid_dependency();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* ring = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int BTILE = TNV * TK * 2;
+  constexpr int ECOLS = TNV / 2;     // tile columns per epilogue warp
   constexpr int STAGE_BYTES = NS * (ATILE + BTILE);
   SplitShared* sh = (SplitShared*)(ring + STAGES * STAGE_BYTES);
   double (*sh_stage)[4] = (double (*)[4])(ring + STAGES * STAGE_BYTES + ((sizeof(SplitShared) + 15) & ~(size_t)15));
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
         const SplitGroup gr = groups[tl.group];
         const int KT = (gr.K + TK - 1) / TK;
         const char* Ab = (const char*)slots[gr.a_slot] + gr.a_off_bytes + ((int64_t)(tl.m0 / TM) * KT) * NS * ATILE;
-        const char* Bb = (const char*)slots[gr.b_slot] + gr.b_off_bytes + ((int64_t)(tl.n0 / TN) * KT) * NS * BTILE;
+        const char* Bb = (const char*)slots[gr.b_slot] + gr.b_off_bytes + ((int64_t)(tl.n0 / TNV) * KT) * NS * BTILE;
         for (int kt = 0; kt < KT; ++kt, ++g) {
           const int s = g % STAGES;
           const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
           const uint32_t sa = smem_u32(ring + s * STAGE_BYTES);
           const uint32_t sb = sa + NS * ATILE;
           // A slice i meets the B slices j = 0 .. NS-1-i stacked along N (they are
-          // consecutive 64-row tiles, so the stack is one taller K-major operand);
+          // consecutive TNV-row tiles, so the stack is one taller K-major operand);
           // its output columns are the accumulators of levels i .. NS-1, also
           // consecutive: one MMA (N <= 256, else two) per A slice and K step.
 #pragma unroll
@@ -423,11 +423,12 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
               const uint64_t ad = smem_desc(sa + i * ATILE + ks * 256);
               const uint32_t acc = (first_in_chunk && ks == 0 && i == 0) ? 0u : 1u;
               const int nj = NS - i;
+              constexpr int PER_MMA = 256 / TNV;   // B slices per MMA (N <= 256)
 #pragma unroll
-              for (int j0 = 0; j0 < nj; j0 += 4) {
-                const int cnt = (nj - j0) < 4 ? (nj - j0) : 4;
+              for (int j0 = 0; j0 < nj; j0 += PER_MMA) {
+                const int cnt = (nj - j0) < PER_MMA ? (nj - j0) : PER_MMA;
                 const uint64_t bd = smem_desc(sb + j0 * BTILE + ks * 256);
-                mma_f16(tmem + (uint32_t)((i + j0) * TN), ad, bd, instr_desc(f16, cnt * TN), acc);
+                mma_f16(tmem + (uint32_t)((i + j0) * TNV), ad, bd, instr_desc(f16, cnt * TNV), acc);
               }
             }
           }
@@ -465,7 +466,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
       {
         const int32_t* eb_c = (const int32_t*)slots[gr.eb_slot] + gr.eb_off;
         const int col = tl.n0 + cb + lane;
-        ebc_s[lane] = col < gr.N ? eb_c[col] : 0;
+        if (lane < ECOLS) ebc_s[lane] = col < gr.N ? eb_c[col] : 0;
       }
       long long acc[ECOLS];
 #pragma unroll
@@ -482,7 +483,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
           uint32_t v[NS][8];
 #pragma unroll
           for (int t = 0; t < NS; ++t)
-            tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(t * TN + cb + cg * 8), v[t]);
+            tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(t * TNV + cb + cg * 8), v[t]);
           tmem_wait_ld();
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
@@ -547,30 +548,40 @@ cudaError_t tnx_launch_slices(const SliceJob* jobs, const int2* items, int64_t t
   return cudaGetLastError();
 }
 
-size_t tnx_split_smem_bytes(int nslice) {
+size_t tnx_split_smem_bytes(int nslice, int tn) {
   // alignment slack + stage ring + barriers + epilogue staging (32 rows x 4 doubles
-  // per epilogue warp) + column exponents (ECOLS per epilogue warp)
-  return 1024 + (size_t)STAGES * nslice * (ATILE + BTILE) + ((sizeof(SplitShared) + 15) & ~(size_t)15) +
-         EPI_WARPS * 32 * 4 * sizeof(double) + EPI_WARPS * ECOLS * sizeof(int) + 64;
+  // per epilogue warp) + column exponents (tn / 2 per epilogue warp)
+  return 1024 + (size_t)STAGES * nslice * (ATILE + (size_t)tn * TK * 2) + ((sizeof(SplitShared) + 15) & ~(size_t)15) +
+         EPI_WARPS * 32 * 4 * sizeof(double) + EPI_WARPS * (tn / 2) * sizeof(int) + 64;
 }
 
+namespace {
+template <int TNV>
+cudaError_t launch_split(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int beta, int f16,
+                         double* const* slots, int32_t* status, cudaStream_t st, int grid) {
+  const size_t smem = tnx_split_smem_bytes(MAXN, TNV);
+  static int attr_dev = -1;   // the opt-in is per device
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (attr_dev != dev) {
+    e = cudaFuncSetAttribute(split_gemm_kernel<MAXN, TNV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_dev = dev;
+  }
+  return tnx_launch(split_gemm_kernel<MAXN, TNV>, dim3(grid), dim3(SPLIT_THREADS), smem, st,
+                    groups, tiles, ntiles, beta, f16, slots, status);
+}
+}  // namespace
+
 cudaError_t tnx_launch_gemm_split(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int nslice, int beta,
-                                  int f16, double* const* slots, int32_t* status, cudaStream_t st, int grid) {
+                                  int f16, double* const* slots, int32_t* status, cudaStream_t st, int grid, int tn) {
   if (ntiles <= 0) return cudaSuccess;
   if (grid <= 0 || grid > ntiles) grid = ntiles;
-  if (nslice != MAXN || beta != 7) return cudaErrorInvalidValue;
-  const size_t smem = tnx_split_smem_bytes(nslice);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<MAXN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  {
-    const cudaError_t le = tnx_launch(split_gemm_kernel<MAXN>, dim3(grid), dim3(SPLIT_THREADS), smem, st,
-                                      groups, tiles, ntiles, beta, f16, slots, status);
-    if (le != cudaSuccess) return le;
-  }
+  if (nslice != MAXN || beta != 7 || (tn != 32 && tn != 64)) return cudaErrorInvalidValue;
+  const cudaError_t le = tn == 32 ? launch_split<32>(groups, tiles, ntiles, beta, f16, slots, status, st, grid)
+                                  : launch_split<64>(groups, tiles, ntiles, beta, f16, slots, status, st, grid);
+  if (le != cudaSuccess) return le;
   tnx_note_launch(1);
   return cudaGetLastError();
 }

@@ -103,7 +103,7 @@ void enqueue_batch(tnx_batch& B, cudaStream_t st) {
       }
       ProfScope ps(c, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
       CUDA_CHECK(tnx_launch_gemm_split(s.dSG, s.dST, s.nst, B.nslice, B.beta, f16, B.d_slots, c->d_status, st,
-                                       B.split_grid));
+                                       B.split_grid, 64));
     }
   }
   ProfScope ps(c, st, TNX_KC_FINAL, 16.0 * (double)B.fin.total);
@@ -140,6 +140,8 @@ extern "C" tnx_status tnx_batch_create(tnx_ctx* ctx, int n, tnx_network* const* 
       if (!nets[i] || nets[i]->ctx != ctx) fail(TNX_ERR_ARG, "every network must belong to the context");
       for (int j = 0; j < i; ++j)
         if (nets[j] == nets[i]) fail(TNX_ERR_ARG, "a network appears twice in the batch");
+      // one merged launch needs one tile width: networks in a batch keep 64-wide split tiles
+      nets[i]->narrow_tiles = false;
       Plan* p = tnx_ensure_plan(nets[i]);
       if (i > 0 && (p->steps.size() != B->plans[0]->steps.size() || p->prec != B->prec))
         fail(TNX_ERR_ARG, "batched networks need the same number of contractions and the same precision");

@@ -160,10 +160,12 @@ cudaError_t tnx_launch_gemm_f32(const GemmGroup* groups, const GemmTile* tiles, 
 // item (one group when the job's cta_mode is set, else 8 groups)
 cudaError_t tnx_launch_slices(const SliceJob* jobs, const int2* items, int64_t total_items, int nslice, int beta,
                               int f16, double* const* slots, cudaStream_t st);
-// grid <= 0 or >= ntiles: one CTA per tile; otherwise a persistent grid of `grid` CTAs
+// grid <= 0 or >= ntiles: one CTA per tile; otherwise a persistent grid of `grid` CTAs.
+// tn: tile width (B rows per tile), 64 or 32; the B slices must be tiled with the same width.
 cudaError_t tnx_launch_gemm_split(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int nslice,
                                   int beta, int f16, double* const* slots, int32_t* status, cudaStream_t st,
-                                  int grid = 0);
+                                  int grid, int tn);
+size_t tnx_split_smem_bytes(int nslice, int tn);
 cudaError_t tnx_launch_gemm_tf32(const SplitGroup* groups, const GemmTile* tiles, int ntiles,
                                  double* const* slots, int32_t* status, cudaStream_t st);
 

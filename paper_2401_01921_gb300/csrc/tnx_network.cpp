@@ -938,7 +938,7 @@ void build_final(Plan& p, const OpView& root, const std::vector<std::string>& to
 }
 
 std::string plan_key(const tnx_network* net, const std::string& order) {
-  std::string k = order + "#" + std::to_string(net->prec);
+  std::string k = order + "#" + std::to_string(net->prec) + (net->narrow_tiles ? "#n" : "#w");
   for (auto& t : net->ts) {
     k += "#" + t.name + "(";
     for (size_t j = 0; j < t.perm.size(); ++j) k += t.t->bonds[t.perm[j]].key() + "/";
@@ -990,6 +990,7 @@ Plan* ensure_plan(tnx_network* net) {
   p->serial = ++serial;
   p->ctx = net->ctx;
   p->prec = net->prec;
+  p->narrow_tiles = net->narrow_tiles;
   p->key = key;
   p->order = order;
   p->nin = (int)net->ts.size();

@@ -74,6 +74,7 @@ struct StepPlan {
   SplitGroup* dSG = nullptr;
   GemmTile* dST = nullptr;
   int nstiles = 0;
+  int split_tn = 64;            // tile width of the split GEMM (B slices are tiled to match)
   std::vector<SplitGroup> hSG;  // host copies
   std::vector<GemmTile> hST;
 };
@@ -107,6 +108,7 @@ struct Plan {
   TaskList fin;
   int prec = TNX_PREC_F64;
   int nslice = 6, beta = 7;
+  bool narrow_tiles = true;       // from the network (a batch needs the same tile width in every plan)
   int32_t* d_status = nullptr;
   std::string key;
   std::string order;
@@ -139,6 +141,7 @@ struct tnx_network {
   std::vector<TreeNode> tree;
   int root = -1;
   int optimal = 0;                 // 0 explicit order, 1 dense-cost search, 2 block-sparse-cost search
+  bool narrow_tiles = true;        // split GEMM steps with few tiles may use 32-wide tiles
   int prec = TNX_PREC_F64;
   std::string order_dims_key;      // dims for which the optimal tree was computed
   std::unique_ptr<Plan> plan;

@@ -5,10 +5,9 @@
 
 #include "tnx_plan.h"
 
-size_t tnx_split_smem_bytes(int nslice);
 
 namespace {
-constexpr int TM = 128, TN = 64, TK = 32;
+constexpr int TM = 128, TK = 32;
 constexpr int64_t KMAX = 8192;   // the 64-bit fixed-point accumulator is exact up to this K
 }
 
@@ -42,6 +41,13 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
   int64_t elems[2] = {0, 0};
   std::vector<int64_t> offSA(G), offSB(G), offEA(G), offEB(G);
   int64_t sa = 0, sb = 0, ea = 0, eb = 0;
+  // Tile width: 64 columns, or 32 when the step has fewer 64-wide tiles than
+  // SMs (the CTAs then take half the columns each and twice as many run).
+  int64_t tiles64 = 0;
+  for (int g = 0; g < G; ++g)
+    if (!s.skinny[g]) tiles64 += (s.mkn[3 * g] + TM - 1) / TM * ((s.mkn[3 * g + 2] + 63) / 64);
+  const int TN = (p.narrow_tiles && tiles64 < 152) ? 32 : 64;
+  s.split_tn = TN;
   for (int g = 0; g < G; ++g) {
     const int64_t M = s.mkn[3 * g], K = s.mkn[3 * g + 1], N = s.mkn[3 * g + 2];
     if (s.skinny[g]) {
@@ -145,5 +151,6 @@ void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool n
     CUDA_CHECK(tnx_launch_slices(J->d, J->items, J->nitems, p.nslice, p.beta, f16, p.d_slots, st));
   }
   ProfScope ps(p.ctx, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
-  CUDA_CHECK(tnx_launch_gemm_split(s.dSG, s.dST, s.nstiles, p.nslice, p.beta, f16, p.d_slots, p.ctx->d_status, st));
+  CUDA_CHECK(tnx_launch_gemm_split(s.dSG, s.dST, s.nstiles, p.nslice, p.beta, f16, p.d_slots, p.ctx->d_status, st, 0,
+                                   s.split_tn));
 }
