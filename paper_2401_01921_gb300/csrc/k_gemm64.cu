@@ -72,52 +72,63 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmGroup* __restrict__
   }
 }
 
-// Skinny products (K <= 16): one thread per row of a 128 x 64 tile keeps its
-// K entries of A in registers and walks the 64 columns, reading B from shared
-// memory (every thread reads the same B entry: a broadcast).  Used for the
-// MPO steps of H_eff (K, N ~ 10), where a square tile would be mostly padding.
+// Skinny products (K <= 16): one thread per row of a 128 x 64 tile.  The
+// MPO-like operand B of these steps is small and mostly zeros (the two-site
+// MPO product of the Heisenberg H_eff stores 30 nonzeros in 114 entries), and
+// FP64 FMAs are the scarce resource of this part: each CTA first lists the
+// nonzeros of every output column of its tile in shared memory (one thread per
+// column, in k order), then every thread walks those lists against its row of
+// A (staged in shared memory).  Skipping a zero term leaves an FMA chain
+// unchanged, so the result equals the dense product bit for bit.
 constexpr int SK_MAXK = 16;
-
-// KB = K rounded up to a multiple of 4: the FMA loop runs over KB entries only
-// (the MPO steps have K of 1..10, and FP64 FMAs are the scarce resource).
-template <int KB>
-__device__ __forceinline__ void skinny_rows(const GemmGroup& g, const GemmTile& tl, const double* A, double* C,
-                                            const double (*Bs)[SK_MAXK], int nn) {
-  const int m = tl.m0 + threadIdx.x;
-  if (m >= g.M) return;
-  double a[KB];
-#pragma unroll
-  for (int k = 0; k < KB; ++k) a[k] = k < g.K ? A[(int64_t)m * g.lda + k] : 0.0;
-  double* crow = C + (int64_t)m * g.ldc + tl.n0;
-  for (int n = 0; n < nn; ++n) {
-    double acc = 0.0;
-#pragma unroll
-    for (int k = 0; k < KB; ++k) acc = fma(a[k], Bs[n][k], acc);
-    crow[n] = acc;
-  }
-}
 
 __global__ void __launch_bounds__(128) gemm_skinny_kernel(const GemmGroup* __restrict__ groups,
                                                           const GemmTile* __restrict__ tiles,
                                                           double* const* __restrict__ slots) {
   tnx_grid_dependency();
-  __shared__ double Bs[64][SK_MAXK];
+  __shared__ double s_v[64][SK_MAXK];          // nonzero B entries of each output column
+  __shared__ unsigned char s_k[64][SK_MAXK];   // their k
+  __shared__ int s_cnt[64];
+  __shared__ double s_a[128][SK_MAXK + 1];     // the CTA's rows of A (padded: conflict-free)
   const GemmTile tl = tiles[blockIdx.x];
   const GemmGroup g = groups[tl.group];
   const double* A = slots[g.a_slot] + g.a_off;
   const double* B = slots[g.b_slot] + g.b_off;
   double* C = slots[g.c_slot] + g.c_off;
   const int nn = min(64, g.N - tl.n0);
-  for (int i = threadIdx.x; i < 64 * SK_MAXK; i += 128) {
-    const int n = i / SK_MAXK, k = i % SK_MAXK;
-    Bs[n][k] = (n < nn && k < g.K) ? B[(int64_t)(tl.n0 + n) * g.ldb + k] : 0.0;
+  const int K = g.K;
+  if ((int)threadIdx.x < nn) {
+    const double* brow = B + (int64_t)(tl.n0 + threadIdx.x) * g.ldb;
+    int c = 0;
+    for (int k = 0; k < K; ++k) {
+      const double v = brow[k];
+      if (v != 0.0) {
+        s_v[threadIdx.x][c] = v;
+        s_k[threadIdx.x][c] = (unsigned char)k;
+        ++c;
+      }
+    }
+    s_cnt[threadIdx.x] = c;
+  }
+  const int m = tl.m0 + threadIdx.x;
+  if (m < g.M) {
+    double a[SK_MAXK];
+#pragma unroll
+    for (int k = 0; k < SK_MAXK; ++k)
+      if (k < K) a[k] = A[(int64_t)m * g.lda + k];
+#pragma unroll
+    for (int k = 0; k < SK_MAXK; ++k)
+      if (k < K) s_a[threadIdx.x][k] = a[k];
   }
   __syncthreads();
-  switch ((g.K + 3) >> 2) {
-    case 1: skinny_rows<4>(g, tl, A, C, Bs, nn); break;
-    case 2: skinny_rows<8>(g, tl, A, C, Bs, nn); break;
-    case 3: skinny_rows<12>(g, tl, A, C, Bs, nn); break;
-    default: skinny_rows<16>(g, tl, A, C, Bs, nn); break;
+  if (m >= g.M) return;
+  const double* arow = s_a[threadIdx.x];
+  double* crow = C + (int64_t)m * g.ldc + tl.n0;
+  for (int n = 0; n < nn; ++n) {
+    double acc = 0.0;
+    const int c = s_cnt[n];
+    for (int e = 0; e < c; ++e) acc = fma(arow[s_k[n][e]], s_v[n][e], acc);
+    crow[n] = acc;
   }
 }
 

@@ -226,11 +226,18 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restr
     const double* src = slots[j.src_slot] + j.src_off + row * j.ld;
     // row exponent
     const int kstart = shared_group ? wid * 4 + kq : kq, kstep = shared_group ? 32 : 4;
+    // eight independent loads in flight per lane, then a fixed-order max
     unsigned long long mx = 0;
     if (live)
-      for (int k = kstart; k < j.K; k += kstep) {
-        const unsigned long long b = __double_as_longlong(src[k]) & 0x7FFFFFFFFFFFFFFFull;
-        mx = b > mx ? b : mx;
+      for (int k0 = kstart; k0 < j.K; k0 += 8 * kstep) {
+        unsigned long long b[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int k = k0 + u * kstep;
+          b[u] = k < j.K ? (__double_as_longlong(src[k]) & 0x7FFFFFFFFFFFFFFFull) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) mx = b[u] > mx ? b[u] : mx;
       }
 #pragma unroll
     for (int o = 1; o < 4; o <<= 1) {

@@ -203,6 +203,7 @@ __global__ void __launch_bounds__(RT) gs_update_kernel(LanczosDev L, int m, int 
   double nrm = 0.0;
   for (int64_t x = (int64_t)blockIdx.x * RT + threadIdx.x; x < L.n; x += (int64_t)gridDim.x * RT) {
     double w = L.w[x];
+#pragma unroll 8
     for (int i = 0; i < m; ++i) w -= c[i] * L.V[(int64_t)i * L.n + x];
     L.w[x] = w;
     nrm = fma(w, w, nrm);
