@@ -211,9 +211,7 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restr
   __shared__ unsigned long long s_max[8][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int r8 = lane >> 2, kq = lane & 3;
-  const int F = nslice * beta;
-  const uint32_t mask = (1u << beta) - 1u;
-  const long long half = 1ll << (beta - 1);
+  constexpr int F = MAXN * 7;   // six digits of 7 bits (checked by the launcher)
   for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
     const int2 item = items[w];   // (job, first 8-row group)
     const SliceJob& j = jobs[item.x];
@@ -281,36 +279,42 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restr
           const int rs = 54 - F + (eb_r - eb);
           fix = rs >= 64 ? 0ull : ((m53 >> (rs - 1)) + 1ull) >> 1;
         }
-        long long v = (bits >> 63) ? -(long long)fix : (long long)fix;
-        // balanced digits, least significant first; the top digit takes the rest
+        // balanced base-128 digits of fix <= 2^41 in 32-bit arithmetic: the six
+        // unsigned 7-bit digits, then least significant first a digit >= 64
+        // becomes digit - 128 with a carry into the next; the top digit takes
+        // the rest (at most 64).  The sign of x goes on every digit.
+        const uint32_t lo = (uint32_t)(fix & 0x1FFFFFull), hi = (uint32_t)(fix >> 21);
+        uint32_t u[MAXN];
+        u[5] = lo & 127u;
+        u[4] = (lo >> 7) & 127u;
+        u[3] = lo >> 14;
+        u[2] = hi & 127u;
+        u[1] = (hi >> 7) & 127u;
+        u[0] = hi >> 14;
         int dg[MAXN];
+        uint32_t carry = 0;
 #pragma unroll
-        for (int i = MAXN - 1; i >= 0; --i) {
-          if (i < nslice) {
-            if (i > 0) {
-              const long long r = ((v + half) & (long long)mask) - half;
-              dg[i] = (int)r;
-              v = (v - r) >> beta;
-            } else {
-              dg[0] = (int)v;
-            }
-          }
+        for (int i = MAXN - 1; i > 0; --i) {
+          const uint32_t t = u[i] + carry;
+          carry = t >= 64u ? 1u : 0u;
+          dg[i] = (int)t - (int)(carry << 7);
+        }
+        dg[0] = (int)(u[0] + carry);
+        if (bits >> 63) {
+#pragma unroll
+          for (int i = 0; i < MAXN; ++i) dg[i] = -dg[i];
         }
 #pragma unroll
         for (int i = 0; i < MAXN; ++i) {
-          if (i < nslice) {
-            const int d = dg[i];
-            const uint32_t b = slice_bits((uint32_t)(d < 0 ? -d : d), d < 0 ? 1u : 0u, f16);
-            sl[i][e >> 1] |= (e & 1) ? (b << 16) : b;
-          }
+          const int d = dg[i];
+          const uint32_t b = slice_bits((uint32_t)(d < 0 ? -d : d), d < 0 ? 1u : 0u, f16);
+          sl[i][e >> 1] |= (e & 1) ? (b << 16) : b;
         }
       }
 #pragma unroll
       for (int i = 0; i < MAXN; ++i) {
-        if (i < nslice) {
-          uint4 v = make_uint4(sl[i][0], sl[i][1], sl[i][2], sl[i][3]);
-          *(uint4*)(base + ((mt * KT + kt) * nslice + i) * tile_bytes + inner) = v;
-        }
+        uint4 v = make_uint4(sl[i][0], sl[i][1], sl[i][2], sl[i][3]);
+        *(uint4*)(base + ((mt * KT + kt) * MAXN + i) * tile_bytes + inner) = v;
       }
     }
   }
@@ -543,7 +547,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
 cudaError_t tnx_launch_slices(const SliceJob* jobs, const int2* items, int64_t total_items, int nslice, int beta,
                               int f16, double* const* slots, cudaStream_t st) {
   if (total_items <= 0) return cudaSuccess;
-  if (nslice < 1 || nslice > MAXN || beta < 1 || beta > 8 || nslice * beta > 53) return cudaErrorInvalidValue;
+  if (nslice != MAXN || beta != 7) return cudaErrorInvalidValue;   // the digit code is specialised
   int64_t blocks = total_items;
   if (blocks > 152 * 8) blocks = 152 * 8;
   {

@@ -41,12 +41,13 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
   int64_t elems[2] = {0, 0};
   std::vector<int64_t> offSA(G), offSB(G), offEA(G), offEB(G);
   int64_t sa = 0, sb = 0, ea = 0, eb = 0;
-  // Tile width: 64 columns, or 32 when the step has fewer 64-wide tiles than
-  // SMs (the CTAs then take half the columns each and twice as many run).
-  int64_t tiles64 = 0;
+  // Tile width: 32 columns when the 32-wide tiles of the step fit in one wave
+  // on the 152 SMs (the CTAs then take half the columns each, which halves
+  // their drain and conversion), else 64.
+  int64_t tiles32 = 0;
   for (int g = 0; g < G; ++g)
-    if (!s.skinny[g]) tiles64 += (s.mkn[3 * g] + TM - 1) / TM * ((s.mkn[3 * g + 2] + 63) / 64);
-  const int TN = (p.narrow_tiles && tiles64 < 152) ? 32 : 64;
+    if (!s.skinny[g]) tiles32 += (s.mkn[3 * g] + TM - 1) / TM * ((s.mkn[3 * g + 2] + 31) / 32);
+  const int TN = (p.narrow_tiles && tiles32 <= 152) ? 32 : 64;
   s.split_tn = TN;
   for (int g = 0; g < G; ++g) {
     const int64_t M = s.mkn[3 * g], K = s.mkn[3 * g + 1], N = s.mkn[3 * g + 2];
