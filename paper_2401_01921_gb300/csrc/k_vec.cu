@@ -125,7 +125,20 @@ __device__ __forceinline__ void multidot_group(const LanczosDev& L, int g0, int6
   double acc[NG];
 #pragma unroll
   for (int i = 0; i < NG; ++i) acc[i] = 0.0;
-  for (int64_t x = c0 + threadIdx.x; x < c1; x += MD_T) {
+  // two entries per iteration: both rows' loads are in flight before the FMAs
+  int64_t x = c0 + threadIdx.x;
+  for (; x + MD_T < c1; x += 2 * MD_T) {
+    const double w0 = L.w[x], w1 = L.w[x + MD_T];
+    double v0[NG], v1[NG];
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+      v0[i] = L.V[(int64_t)(g0 + i) * L.n + x];
+      v1[i] = L.V[(int64_t)(g0 + i) * L.n + x + MD_T];
+    }
+#pragma unroll
+    for (int i = 0; i < NG; ++i) acc[i] = fma(v1[i], w1, fma(v0[i], w0, acc[i]));
+  }
+  if (x < c1) {
     const double wx = L.w[x];
 #pragma unroll
     for (int i = 0; i < NG; ++i) acc[i] = fma(L.V[(int64_t)(g0 + i) * L.n + x], wx, acc[i]);
