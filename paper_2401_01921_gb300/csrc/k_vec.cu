@@ -214,7 +214,25 @@ __global__ void __launch_bounds__(RT) gs_update_kernel(LanczosDev L, int m, int 
   for (int i = threadIdx.x; i < m; i += RT) c[i] = L.coef[i];
   __syncthreads();
   double nrm = 0.0;
-  for (int64_t x = (int64_t)blockIdx.x * RT + threadIdx.x; x < L.n; x += (int64_t)gridDim.x * RT) {
+  // two entries per iteration (the second one stride later), so that the loads
+  // of both are in flight together; each entry keeps its own subtraction order
+  const int64_t stride = (int64_t)gridDim.x * RT;
+  int64_t x = (int64_t)blockIdx.x * RT + threadIdx.x;
+  for (; x + stride < L.n; x += 2 * stride) {
+    double w0 = L.w[x], w1 = L.w[x + stride];
+#pragma unroll 4
+    for (int i = 0; i < m; ++i) {
+      const double* vi = L.V + (int64_t)i * L.n;
+      const double a0 = vi[x], a1 = vi[x + stride];
+      w0 -= c[i] * a0;
+      w1 -= c[i] * a1;
+    }
+    L.w[x] = w0;
+    L.w[x + stride] = w1;
+    nrm = fma(w0, w0, nrm);
+    nrm = fma(w1, w1, nrm);
+  }
+  if (x < L.n) {
     double w = L.w[x];
 #pragma unroll 8
     for (int i = 0; i < m; ++i) w -= c[i] * L.V[(int64_t)i * L.n + x];
