@@ -33,6 +33,19 @@ sys.path.insert(0, ROOT)
 METRIC = "H_eff*psi useful TFLOP/s (Lanczos solve, block-sparse U(1))"
 LANCZOS_STEPS = 20
 
+# DRAM bytes (read + write) per split-GEMM launch, averaged over the GEMM launches
+# of one apply, from the ncu capture summarised in profiles/ (workload -> (bytes,
+# summary file, sha256 of k_split.cu when the counters were taken)).  Reported as
+# roofline.traffic only while the kernel source is unchanged, else null.
+SPLIT_TRAFFIC = {
+    "heisenberg_u1_chi512_d2_D5_lanczos20":
+        (9305600, "profiles/split_gemm_heisenberg_u1_chi512.md",
+         "1edccaadeb9ebab7b4ab4b062a986006f94f024ad0ed51f81a11861a747bc22f"),
+    "heisenberg_u1_chi2048_d2_D5_sectorscaled_lanczos20":
+        (94286976, "profiles/split_gemm_heisenberg_u1_chi2048.md",
+         "1edccaadeb9ebab7b4ab4b062a986006f94f024ad0ed51f81a11861a747bc22f"),
+}
+
 
 def workload(name: str):
     import tnx_inputs as I
@@ -43,6 +56,19 @@ def workload(name: str):
     if name == "dense32":
         return I.dense_workload(32), "heisenberg_dense_chi32_d2_D5_lanczos20"
     raise SystemExit(f"unknown workload {name}")
+
+
+def split_traffic(wname: str):
+    import hashlib
+    ent = SPLIT_TRAFFIC.get(wname)
+    if not ent:
+        return None, None
+    src = os.path.join(ROOT, "paper_2401_01921_gb300", "csrc", "k_split.cu")
+    with open(src, "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()
+    if digest != ent[2]:
+        return None, f"{ent[1]} (stale: k_split.cu changed since the capture)"
+    return ent[0], ent[1]
 
 
 def peaks():
@@ -529,8 +555,10 @@ def main():
         achieved = 21.0 * useful_rate
         kname = ("split BF16 GEMM on tcgen05: 21 x useful flops per launch (slice-pair products the method "
                  "requires, tile padding excluded) / CUDA-event launch time")
+    traffic, traffic_src = split_traffic(wname) if prec != "f64" else (None, None)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None, "traffic": None, "kernel": kname,
+                "frac": achieved / peak if peak else None, "traffic": traffic, "traffic_source": traffic_src,
+                "kernel": kname,
                 "achieved_useful_tflops": useful_rate,
                 "flops_per_launch": gwork / max(gn, 1), "avg_launch_ms": gms / max(gn, 1), "peak_source": peak_src,
                 "kernel_ms": {k: v[0] for k, v in prof_all.items()},
