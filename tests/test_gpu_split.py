@@ -62,12 +62,14 @@ def test_f32_error_reported(ctx):
     assert 1e-12 < err < 1e-5
 
 
+@pytest.mark.parametrize("chi,n", [(40, 9), (512, 20)])
 @pytest.mark.parametrize("prec", ["split_bf16", "split_f16"])
-def test_split_exact_on_integers(ctx, prec):
-    """Integer entries in [-3, 3]: every slice is exact, so the split products equal the FP64 ones bit for bit."""
+def test_split_exact_on_integers(ctx, prec, chi, n):
+    """Integer entries in [-3, 3]: every slice is exact, so the split products equal the FP64 ones bit for bit
+    (chi=512 has charge groups with K up to 434, summed exactly in one FP32 level chunk)."""
     import paper_2401_01921_gb300 as tnx
     from paper_2401_01921_gb300.heff import build_network
-    wl = I.heisenberg_workload(40, 9)
+    wl = I.heisenberg_workload(chi, n)
     bonds = I.heff_bonds(wl)
 
     def ints(name):
