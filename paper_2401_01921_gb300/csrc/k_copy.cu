@@ -100,7 +100,7 @@ __device__ __forceinline__ void offsets(const CopyTask& t, int i, int& so, int& 
 
 // Elements [e0, e0 + n) of one task (n <= EPT): one decomposition, then steps
 // along the innermost leg; a carry into the next leg re-decomposes.
-constexpr int EPT = 4;
+constexpr int EPT = 2;
 
 __device__ __forceinline__ void copy_run(const CopyTask& t, const double* src, double* dst, int e0, int n) {
   int so, dof;

@@ -141,7 +141,7 @@ void tnx_count_into(long long* c);    // nullptr: count globally again
 // Kernel launchers (defined in the .cu files).  All enqueue on `st`.
 // ---------------------------------------------------------------------------
 cudaError_t tnx_launch_match(const MatchArgs& a, cudaStream_t st);
-#define TNX_COPY_CHUNK 1024    // elements per relayout CTA
+#define TNX_COPY_CHUNK 512     // elements per relayout CTA
 #define TNX_COPY_PACK 64       // small tasks per relayout CTA at most
 // chunks[i] = (first task, first element, task count, element count): a large
 // task is cut into chunks of TNX_COPY_CHUNK elements (task count 1), runs of
