@@ -95,3 +95,15 @@ def test_split_lanczos(ctx):
         net, T, B = lib_heff(ctx, wl, symmetric=True, prec=p)
         lam[p], _ = tnx.lanczos(net, "psi", T["psi"], 20)
     assert abs(lam["f64"] - lam["split_bf16"]) <= 1e-10 * abs(lam["f64"])
+
+
+def test_precision_sweep_chi2048(ctx):
+    """The C3 sweep: chi=2048 U(1) apply with per-sector 10^U(-3,0) scaling, every precision the
+    library offers against the FP64 oracle (errors printed; FP64 <= 1e-12, split <= 1e-10)."""
+    bounds = {"f64": 1e-12, "split_bf16": TOL_SPLIT, "split_f16": TOL_SPLIT, "f32": 1e-5}
+    ref = reference("u1_chi2048_scaled")
+    for prec, tol in bounds.items():
+        net, T, B = lib_heff(ctx, WORKLOADS["u1_chi2048_scaled"](), prec=prec)
+        err = rel_fro(net.launch(B["psi"]).block_dict(), ref)
+        print(f"u1_chi2048_scaled {prec}: rel err {err:.3e}")
+        assert err <= tol, (prec, err)
