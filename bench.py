@@ -58,6 +58,19 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def replica_rate(units: float, ms: float, dist=None, device="cpu"):
+    """Whole-job rate of independent replicas: the units every rank processed over
+    the slowest rank's time.  Returns (units per second, slowest ms)."""
+    if dist is None:
+        return units / (ms * 1e-3), ms
+    import torch
+    slow = torch.tensor([ms], dtype=torch.float64, device=device)
+    total = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(slow, op=dist.ReduceOp.MAX)
+    dist.all_reduce(total, op=dist.ReduceOp.SUM)
+    return float(total.item()) / (float(slow.item()) * 1e-3), float(slow.item())
+
+
 def split_traffic(wname: str):
     import hashlib
     ent = SPLIT_TRAFFIC.get(wname)
@@ -269,7 +282,8 @@ def run_batch(args, torch, dev, tnx, I, build_network, dist, world, rank, local)
         prof_all[prec] = ctx.profile_read()
         prof_all[prec]["gemm"] = prof_gemm["gemm"]
         ctx.profile(False)
-        res[prec] = {"value": flops * args.steps / (sum(times) * 1e-3) / 1e12, "ms": sum(times) / args.steps,
+        rate, slow_ms = replica_rate(flops * args.steps, sum(times), dist, dev)
+        res[prec] = {"value": rate / 1e12, "ms": slow_ms / args.steps,
                      "flops": flops, "schedule": choice, "clocks": clk.summary(), "launches": launches}
         del batch, nets, outs, keep
     main_prec = "split_bf16" if "split_bf16" in res else args.prec
@@ -480,14 +494,11 @@ def main():
     ctx.profile(False)
     launches = tnx.kernel_launches() - launches0
     torch.cuda.synchronize(dev)
-    total_ms = sum(times)
-    if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
     useful = apply_flops * matvecs
-    value = useful * world / (total_ms * 1e-3) / 1e12
+    rate, total_ms = replica_rate(useful, sum(times), dist, dev)
+    if dist:
+        dist.barrier()
+    value = rate / 1e12
 
     # ---- e2e through the C-ABI with host buffers (pinned), copies inside the timed region
     host = {}
@@ -522,11 +533,8 @@ def main():
         t0 = time.perf_counter()
         e2e_mv += e2e_step()
         e2e_ms += (time.perf_counter() - t0) * 1e3
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = apply_flops * e2e_mv * world / (e2e_ms * 1e-3) / 1e12
+    e2e_rate, e2e_ms = replica_rate(apply_flops * e2e_mv, e2e_ms, dist, dev)
+    e2e_value = e2e_rate / 1e12
 
     # ---- per-class breakdown: the same steps again with events around every kernel class
     #      (not timed: the events themselves cost time in a graph this size)
