@@ -147,12 +147,8 @@ __device__ __forceinline__ void multidot_group(const LanczosDev& L, int g0, int6
   for (int i = 0; i < NG; ++i) sh[i][threadIdx.x] = acc[i];
 }
 
-__global__ void __launch_bounds__(MD_T) multidot_kernel(LanczosDev L, int m) {
-  tnx_grid_dependency();
-  __shared__ double sh[16][MD_T + 1];
-  if (stopped(L.state)) return;
-  const int64_t chunk = (L.n + gridDim.x - 1) / gridDim.x;
-  const int64_t c0 = chunk * blockIdx.x, c1 = min(L.n, c0 + chunk);
+// Dots of this block's chunk [c0, c1) against V_0 .. V_{m-1} into partial[b*m + i].
+__device__ void block_multidot(const LanczosDev& L, int m, int64_t c0, int64_t c1, double (*sh)[MD_T + 1]) {
   for (int g0 = 0; g0 < m; g0 += 16) {
     const int ng = m - g0 < 16 ? m - g0 : 16;
     switch (ng) {
@@ -186,6 +182,50 @@ __global__ void __launch_bounds__(MD_T) multidot_kernel(LanczosDev L, int m) {
     }
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(MD_T) multidot_kernel(LanczosDev L, int m) {
+  tnx_grid_dependency();
+  __shared__ double sh[16][MD_T + 1];
+  if (stopped(L.state)) return;
+  const int64_t chunk = (L.n + gridDim.x - 1) / gridDim.x;
+  const int64_t c0 = chunk * blockIdx.x, c1 = min(L.n, c0 + chunk);
+  block_multidot(L, m, c0, c1, sh);
+}
+
+// The first Gram-Schmidt update and the second pass's dots in one launch: each
+// block updates its own chunk (w -= sum_i coef[i] V_i, in the same order as the
+// separate update kernel) and then forms the chunk's dots of the new w, every
+// thread reading back only the entries it wrote.
+__global__ void __launch_bounds__(MD_T) update_multidot_kernel(LanczosDev L, int m) {
+  tnx_grid_dependency();
+  __shared__ double sh[16][MD_T + 1];
+  __shared__ double c[512];
+  if (stopped(L.state)) return;
+  for (int i = threadIdx.x; i < m; i += MD_T) c[i] = L.coef[i];
+  __syncthreads();
+  const int64_t chunk = (L.n + gridDim.x - 1) / gridDim.x;
+  const int64_t c0 = chunk * blockIdx.x, c1 = min(L.n, c0 + chunk);
+  int64_t x = c0 + threadIdx.x;
+  for (; x + MD_T < c1; x += 2 * MD_T) {
+    double w0 = L.w[x], w1 = L.w[x + MD_T];
+#pragma unroll 4
+    for (int i = 0; i < m; ++i) {
+      const double* vi = L.V + (int64_t)i * L.n;
+      const double a0 = vi[x], a1 = vi[x + MD_T];
+      w0 -= c[i] * a0;
+      w1 -= c[i] * a1;
+    }
+    L.w[x] = w0;
+    L.w[x + MD_T] = w1;
+  }
+  if (x < c1) {
+    double w = L.w[x];
+#pragma unroll 8
+    for (int i = 0; i < m; ++i) w -= c[i] * L.V[(int64_t)i * L.n + x];
+    L.w[x] = w;
+  }
+  block_multidot(L, m, c0, c1, sh);
 }
 
 // coef[i] = sum_b partial[b*m + i]   (one block per i, fixed order);
@@ -479,24 +519,29 @@ cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, double** next_sl
   const int nb = grid_for(L.n);
   const int m = j + 1;
   const int mb = multidot_blocks(L.n);
-  for (int pass = 0; pass < 2; ++pass) {
-    {
-      const cudaError_t le = tnx_launch(multidot_kernel, dim3(mb), dim3(MD_T), 0, st, L, m);
-      if (le != cudaSuccess) return le;
-    }
-    tnx_note_launch(1);
-    {
-      const cudaError_t le = tnx_launch(multidot_finalize_kernel, dim3(m), dim3(RT), 0, st,
-                                        L, m, mb, pass == 0 ? j : -1);
-      if (le != cudaSuccess) return le;
-    }
-    tnx_note_launch(1);
-    {
-      const cudaError_t le = tnx_launch(gs_update_kernel, dim3(nb), dim3(RT), 0, st, L, m, pass == 1);
-      if (le != cudaSuccess) return le;
-    }
-    tnx_note_launch(1);
+  // pass 1 dots and coefficients; the pass 1 update fused with the pass 2 dots;
+  // pass 2 coefficients; the pass 2 update with the norm's partial sums
+  {
+    const cudaError_t le = tnx_launch(multidot_kernel, dim3(mb), dim3(MD_T), 0, st, L, m);
+    if (le != cudaSuccess) return le;
   }
+  {
+    const cudaError_t le = tnx_launch(multidot_finalize_kernel, dim3(m), dim3(RT), 0, st, L, m, mb, j);
+    if (le != cudaSuccess) return le;
+  }
+  {
+    const cudaError_t le = tnx_launch(update_multidot_kernel, dim3(mb), dim3(MD_T), 0, st, L, m);
+    if (le != cudaSuccess) return le;
+  }
+  {
+    const cudaError_t le = tnx_launch(multidot_finalize_kernel, dim3(m), dim3(RT), 0, st, L, m, mb, -1);
+    if (le != cudaSuccess) return le;
+  }
+  {
+    const cudaError_t le = tnx_launch(gs_update_kernel, dim3(nb), dim3(RT), 0, st, L, m, 1);
+    if (le != cudaSuccess) return le;
+  }
+  tnx_note_launch(5);
   {
     const cudaError_t le = tnx_launch(lanczos_beta_decide_kernel, dim3(1), dim3(RT), 0, st,
                                       L, j, nb, j == L.nmax - 1, next_slot);
