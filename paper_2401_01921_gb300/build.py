@@ -49,7 +49,7 @@ def _compile(src: str, nvcc: str, verbose: bool) -> str:
 def build(verbose: bool = False, force: bool = False) -> str:
     srcs = sources()
     newest = max(os.path.getmtime(p) for p in srcs + [os.path.join(INCLUDE, "tnx.h")] +
-                 [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")])
+                 [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))])
     if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= newest and not verbose:
         return OUT
     os.makedirs(BUILD, exist_ok=True)

@@ -15,11 +15,16 @@
 // its threads walk destination order so stores coalesce, and loads coalesce
 // whenever the source is contiguous along the same leg.  When the source is
 // contiguous along another leg, the task is moved in 32 x 32 tiles staged
-// through shared memory instead, so both sides coalesce.  Index arithmetic is
-// 32-bit inside a task, and an index is split over the legs with
-// multiply-high divisions by the leg extents (constants the planner
-// precomputes) instead of hardware integer divisions.
-#include "tnx_internal.h"
+// through shared memory instead, so both sides coalesce.  Blocks that share
+// the rows of a narrow matrix on one side (a packed GEMM operand of K <= 96
+// columns they are written into, or a GEMM output of <= 96 columns they are
+// read from) move as one band: a tile of whole rows is staged in shared
+// memory, the wide side is accessed row by row and each block's other side
+// along its own contiguous leg.  Index arithmetic is 32-bit inside a task, and
+// an index is split over the legs with multiply-high divisions by the leg
+// extents (constants the planner precomputes) instead of hardware integer
+// divisions.
+#include "tnx_band.cuh"
 
 namespace {
 
@@ -35,8 +40,7 @@ __device__ __forceinline__ int fdiv(int n, uint32_t magic, uint32_t shift) {
 // per index of S and one row per index of the other legs (in task order), and
 // move it in 32 x 32 tiles through shared memory: loads run along S, stores
 // along the rows (consecutive rows are consecutive in the destination).
-__device__ void copy_transpose(const CopyTask& t, int tile, double* const* __restrict__ slots) {
-  __shared__ double sm[32][33];
+__device__ void copy_transpose(const CopyTask& t, int tile, double* const* __restrict__ slots, double (*sm)[33]) {
   const int r = t.rank, S = t.tleg;
   const int ncols = t.shape[S];
   const int nrows = (int)(t.nelem / ncols);
@@ -77,6 +81,82 @@ __device__ void copy_transpose(const CopyTask& t, int tile, double* const* __res
     for (int i = 0; i < 4; ++i) {
       const int cc = wid + 8 * i, col = c0 + cc;
       if (col < ncols) dst[dof + col * t.dstride[S]] = sm[lane][cc];
+    }
+  }
+}
+
+// One tile of a band (see tnx_internal.h): rows (p, q) of the wide side for
+// p in [p0, p0 + tP), q in [q0, q0 + tQ), all W columns.  Shared memory holds
+// the tile row by row (pitch W | 1, so that a column walk is free of bank
+// conflicts), the Q rows innermost when the members' narrow sides run along
+// Q, else the P rows.  Destination-wide: the members gather their elements
+// into the zeroed tile, which is then written as whole rows (columns no member
+// covers are structural zeros or padding of the operand).  Source-wide: whole
+// rows are read, then each member scatters its columns.  Each member walks its
+// elements in the order of its narrow-side strides, so that side coalesces too.
+__device__ void copy_band(const CopyTask* __restrict__ tasks, int h, int tile, double* const* __restrict__ slots,
+                          double* buf, tnx_band::Member* mem, int* pre) {
+  using namespace tnx_band;
+  const CopyTask& H = tasks[h];
+  const int nt = H.rank;
+  const int EP = H.shape[0], EQ = H.shape[1], W = H.shape[2], TP = H.shape[3], TQ = H.shape[4];
+  const bool dwide = H.shape[5] != 0, qin = H.shape[6] != 0;
+  const int Wp = W | 1;
+  const int ntq = (EQ + TQ - 1) / TQ;
+  const int tp = tile / ntq, tq = tile - tp * ntq;
+  const int p0 = tp * TP, q0 = tq * TQ;
+  const int tP = min(TP, EP - p0), tQ = min(TQ, EQ - q0);
+  const int wP = qin ? tQ * Wp : Wp, wQ = qin ? Wp : tP * Wp;
+  if ((int)threadIdx.x < nt) mem[threadIdx.x] = stage(tasks[h + 1 + threadIdx.x], dwide, p0, q0, tP, tQ, wP, wQ);
+  const int rows = tP * tQ;
+  const long long XP = H.sstride[0], XQ = H.sstride[1];
+  const long long wbase = (dwide ? H.dst_off : H.src_off) + (long long)p0 * XP + (long long)q0 * XQ;
+  double* wptr = slots[dwide ? H.dst_slot : H.src_slot] + wbase;
+  const float invW = 1.0f / (float)W, invR = 1.0f / (float)(qin ? tQ : tP);
+  // wide row r of the tile -> offset of its first element on the wide side
+  auto rowoff = [&](int r) -> long long {
+    int p, q;
+    if (qin) {
+      p = qdiv(r, tQ, invR);
+      q = r - p * tQ;
+    } else {
+      q = qdiv(r, tP, invR);
+      p = r - q * tP;
+    }
+    return (long long)p * XP + (long long)q * XQ;
+  };
+  if (dwide) {
+    for (int i = threadIdx.x; i < rows * Wp; i += CT) buf[i] = 0.0;
+  } else {
+    // kUnroll loads in flight per thread before their shared-memory stores
+    for (int e0 = threadIdx.x; e0 < rows * W; e0 += CT * kUnroll) {
+      double v[kUnroll];
+      int so[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int e = e0 + u * CT;
+        so[u] = -1;
+        if (e < rows * W) {
+          const int r = qdiv(e, W, invW), c = e - r * W;
+          so[u] = r * Wp + c;
+          v[u] = __ldg(wptr + rowoff(r) + c);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+        if (so[u] >= 0) buf[so[u]] = v[u];
+    }
+  }
+  __syncthreads();
+  prefix(mem, nt, pre);
+  __syncthreads();
+  if (dwide) move<CT, true>(mem, pre, nt, buf, slots);
+  else move<CT, false>(mem, pre, nt, buf, slots);
+  if (dwide) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * W; e += CT) {
+      const int r = qdiv(e, W, invW), c = e - r * W;
+      wptr[rowoff(r) + c] = buf[r * Wp + c];
     }
   }
 }
@@ -134,16 +214,26 @@ __device__ __forceinline__ void copy_run(const CopyTask& t, const double* src, d
 // One task: its elements [first, first + count), EPT consecutive ones per
 // thread.  Several (small) tasks: all their elements, back to back; the
 // chunk's descriptors are staged in shared memory and each thread finds its
-// task by binary search over their starts.  A negative task count marks one
-// 32 x 32 tile of a transposing task.
+// task by binary search over their starts.  Task count -1 marks one 32 x 32
+// tile of a transposing task, -2 one tile of a band.
 __global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ tasks, const int4* __restrict__ chunks,
                                                   double* const* __restrict__ slots) {
   tnx_grid_dependency();
-  __shared__ CopyTask st[TNX_COPY_PACK];
-  __shared__ int sstart[TNX_COPY_PACK + 1];
+  // packed tasks | transposing tile | band tile (members, then the staged rows)
+  constexpr int kPack = TNX_COPY_PACK * (int)sizeof(CopyTask);
+  constexpr int kBand = TNX_BAND_MAXM * (int)sizeof(tnx_band::Member) + TNX_BAND_CAP * 8;
+  constexpr int kRaw = kPack > kBand ? kPack : kBand;
+  static_assert(32 * 33 * 8 <= kRaw, "shared memory of the transposing tile");
+  __shared__ __align__(16) unsigned char raw[kRaw];
+  __shared__ int sstart[TNX_BAND_MAXM > TNX_COPY_PACK ? TNX_BAND_MAXM + 1 : TNX_COPY_PACK + 1];
+  CopyTask* st = (CopyTask*)raw;
   const int4 ch = chunks[blockIdx.x];
-  if (ch.z < 0) {
-    copy_transpose(tasks[ch.x], ch.y, slots);
+  if (ch.z == -1) {
+    copy_transpose(tasks[ch.x], ch.y, slots, (double (*)[33])raw);
+    return;
+  }
+  if (ch.z == -2) {
+    copy_band(tasks, ch.x, ch.y, slots, (double*)(raw + TNX_BAND_MAXM * sizeof(tnx_band::Member)), (tnx_band::Member*)raw, sstart);
     return;
   }
   if (ch.z == 1) {

@@ -24,9 +24,25 @@
 // element offsets reach 2^31); the slot offsets are 64-bit.  magic/shift
 // divide an index below 2^31 by shape[l] without a hardware division:
 // q = magic ? umulhi(n, magic) >> shift : n.
+//
+// Bands (tleg == TNX_BAND_HEADER): blocks that share the rows of one side's
+// matrix ("wide" side: the packed GEMM operand they are written into, or the
+// GEMM output they are read from), each covering a column range of those rows,
+// move together in tiles staged through shared memory, so the wide side is
+// accessed in whole rows and the other ("narrow") side along its own
+// contiguous leg.  The header is followed by its `rank` members
+// (tleg == TNX_BAND_MEMBER).  Header: wide slot in src_slot (source-wide) or
+// dst_slot (destination-wide), the other slot -1; wide base offset in
+// src_off / dst_off (element (p, q, c) of the band's rows lies at
+// base + p * sstride[0] + q * sstride[1] + c); shape = {EP, EQ, W, TP, TQ,
+// destination-wide, Q rows innermost in the tile}; nelem 0.  Member: rank 3
+// with legs (P, Q, I) of extents (EP, EQ, n) and strides on both sides (the
+// wide side's I stride is 1), wcol = its first column in the wide rows.
+#define TNX_BAND_HEADER (-2)
+#define TNX_BAND_MEMBER (-3)
 struct CopyTask {
   int32_t src_slot, dst_slot;
-  int32_t rank, tleg;         // tleg >= 0: transposing task, source contiguous along leg tleg
+  int32_t rank, tleg;         // tleg >= 0: transposing task, source contiguous along leg tleg; else -1 or a band mark
   int64_t src_off, dst_off;
   int64_t nelem;
   int32_t shape[TNX_MAXR];
@@ -34,6 +50,7 @@ struct CopyTask {
   int32_t sstride[TNX_MAXR];
   int32_t dstride[TNX_MAXR];
   uint8_t shift[TNX_MAXR];
+  int32_t wcol, pad0;         // band member: first column in the wide rows
 };
 
 // One dense product C[M,N] = A[M,K] * B[N,K]^T (both operands K-major, C row-major).
@@ -143,12 +160,39 @@ void tnx_count_into(long long* c);    // nullptr: count globally again
 cudaError_t tnx_launch_match(const MatchArgs& a, cudaStream_t st);
 #define TNX_COPY_CHUNK 512     // elements per relayout CTA
 #define TNX_COPY_PACK 64       // small tasks per relayout CTA at most
+#define TNX_BAND_CAP 2048      // elements of a band tile staged in shared memory
+#define TNX_BAND_MAXM 64       // members of a band at most
 // chunks[i] = (first task, first element, task count, element count): a large
 // task is cut into chunks of TNX_COPY_CHUNK elements (task count 1), runs of
-// small tasks are packed (task count > 1, first element 0), and a transposing
-// task has one chunk per 32 x 32 tile: (task, tile index, -1, 0).
+// small tasks are packed (task count > 1, first element 0), a transposing
+// task has one chunk per 32 x 32 tile: (task, tile index, -1, 0), and a band
+// one chunk per tile: (header, tile index, -2, 0).
 cudaError_t tnx_launch_copy(const CopyTask* tasks, const int4* chunks, int nchunks, double* const* slots,
                             cudaStream_t st);
+// Fused skinny step (k_fused.cu): one CTA per tile of up to 128 rows (p, q),
+// p in [p0, p0 + tP), q in [q0, q0 + tQ), of one row block of A_g (the rows a
+// destination band of the step's relayout fills).  Column c < W (= ldK of the
+// group) of those rows is described by FusedCol gcol + c: the A element of row
+// (p, q) lies at ptr + p * sP + q * sQ (ptr null: a structural zero).  The rows
+// are multiplied by the packed B_g (K <= 16, N <= 64) in FP64, and output
+// column c < N of row (p, q) is stored through FusedCol scol + c the same way
+// (ptr null: no step reads it).  scol < 0 writes the output rows to C_g
+// instead: row (p, q) to row row0 + p * EQ + q of the group, EQ = -scol - 1.
+// The pointers are plan buffers (fused steps read and write no rebindable
+// slot).  kp, np: shared-memory pitches of the A and output rows (odd, > every
+// W and N).
+struct FusedCol {
+  double* ptr;
+  int32_t sP, sQ;
+};
+struct FusedTile {
+  int32_t group, gcol, scol, row0;
+  int32_t p0, q0, tP, tQ;
+  int32_t W, N, pad0, pad1;
+};
+cudaError_t tnx_launch_fused_skinny(const GemmGroup* groups, const FusedTile* tiles, int ntiles, const FusedCol* cols,
+                                    int kp, int np, double* const* slots, cudaStream_t st);
+size_t tnx_fused_smem_bytes(int kp, int np);
 cudaError_t tnx_launch_gemm_f64(const GemmGroup* groups, const GemmTile* tiles, int ntiles,
                                 double* const* slots, cudaStream_t st);
 // K <= 16 products, tiles of 128 rows x 64 columns (FP64)

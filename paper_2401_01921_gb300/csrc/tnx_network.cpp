@@ -24,6 +24,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <set>
+#include <tuple>
 
 #include "tnx_host.h"
 
@@ -402,14 +403,21 @@ void sort_view(OpView& v) {
   });
   std::vector<int32_t> qn(v.qn.size());
   std::vector<int64_t> base(v.nblk), stride(v.stride.size());
+  std::vector<int64_t> rs(v.rowstart.size()), rl(v.rowld.size());
   for (int64_t i = 0; i < v.nblk; ++i) {
     std::copy(v.qn.begin() + idx[i] * r, v.qn.begin() + (idx[i] + 1) * r, qn.begin() + i * r);
     std::copy(v.stride.begin() + idx[i] * r, v.stride.begin() + (idx[i] + 1) * r, stride.begin() + i * r);
     base[i] = v.base[idx[i]];
+    if (!rs.empty()) {
+      rs[i] = v.rowstart[idx[i]];
+      rl[i] = v.rowld[idx[i]];
+    }
   }
   v.qn.swap(qn);
   v.base.swap(base);
   v.stride.swap(stride);
+  v.rowstart.swap(rs);
+  v.rowld.swap(rl);
 }
 
 OpView input_view(const NetTensor& nt, int slot) {
@@ -435,6 +443,21 @@ OpView input_view(const NetTensor& nt, int slot) {
 }
 
 // Drop unit legs and merge neighbours that are contiguous in both source and destination.
+// Division by the invariant d for indices n < 2^31 (Granlund and Montgomery,
+// PLDI 1994): with p = ceil(log2 d) and m = ceil(2^(31+p) / d), m < 2^32 and
+// floor(n / d) = floor(n m / 2^(31+p)) = umulhi(n, m) >> (p - 1), because
+// n m / 2^(31+p) exceeds n / d by less than 1 / d.  d = 1: magic 0 (q = n).
+void leg_magic(uint64_t d, uint32_t& magic, uint8_t& shift) {
+  magic = 0;
+  shift = 0;
+  if (d > 1) {
+    int lg = 0;
+    while ((1ull << lg) < d) ++lg;
+    magic = (uint32_t)(((1ull << (31 + lg)) + d - 1) / d);
+    shift = (uint8_t)(lg - 1);
+  }
+}
+
 void finish_task(CopyTask& t, std::vector<int64_t> shape, std::vector<int64_t> ss, std::vector<int64_t> ds) {
   std::vector<int64_t> sh2, s2, d2;
   for (size_t l = 0; l < shape.size(); ++l) {
@@ -473,17 +496,7 @@ void finish_task(CopyTask& t, std::vector<int64_t> shape, std::vector<int64_t> s
     t.shape[l] = (int32_t)d;
     t.sstride[l] = (int32_t)s2[l];
     t.dstride[l] = (int32_t)d2[l];
-    // Division by the invariant d for indices n < 2^31 (Granlund and
-    // Montgomery, PLDI 1994): with p = ceil(log2 d) and m = ceil(2^(31+p) / d),
-    // m < 2^32 and floor(n / d) = floor(n m / 2^(31+p)) = umulhi(n, m) >> (p - 1),
-    // because n m / 2^(31+p) exceeds n / d by less than 1 / d.
-    if (d > 1) {
-      int lg = 0;
-      while ((1ull << lg) < d) ++lg;
-      const uint64_t m = ((1ull << (31 + lg)) + d - 1) / d;
-      t.magic[l] = (uint32_t)m;
-      t.shift[l] = (uint8_t)(lg - 1);
-    }
+    leg_magic(d, t.magic[l], t.shift[l]);
   }
   // transposing task: the source's unit-stride leg is not the destination's
   t.tleg = -1;
@@ -495,18 +508,198 @@ void finish_task(CopyTask& t, std::vector<int64_t> shape, std::vector<int64_t> s
   }
 }
 
+// A block copy before it is finished: its legs in task order, and where its
+// rows lie in a row-major matrix on either side, when that is known (the
+// packed GEMM operands on the destination side, GEMM outputs on the source
+// side).
+struct RawTask {
+  CopyTask t;                          // slots and base offsets
+  std::vector<int64_t> shape, ss, ds;
+  std::vector<char> drow, srow;        // leg is a row leg of the destination / source matrix
+  int64_t drow0 = -1, dW = 0;          // destination: offset of the block's first row start; row length
+  int64_t srow0 = -1, sW = 0;          // source: the same
+};
+
+// A band member's legs (P, Q, I): extent, wide-side stride, narrow-side stride.
+struct BandLegs {
+  int64_t ext[3], wst[3], nst[3];
+  int64_t wcol;
+};
+
+// Views a block as a band member on the wide side `dside` (destination or
+// source): at most two row legs (P outer, Q inner) and one column leg I that is
+// contiguous on the wide side, after extent-1 legs are dropped and legs
+// contiguous on both sides are merged.  False when the block does not fit.
+bool band_legs(const RawTask& r, bool dside, BandLegs& b) {
+  const std::vector<int64_t>& ws = dside ? r.ds : r.ss;
+  const std::vector<int64_t>& nsv = dside ? r.ss : r.ds;
+  const std::vector<char>& isrow = dside ? r.drow : r.srow;
+  struct Leg { int64_t e, w, n; };
+  std::vector<Leg> rows, cols;
+  for (size_t l = 0; l < r.shape.size(); ++l) {
+    if (r.shape[l] == 1) continue;
+    (isrow[l] ? rows : cols).push_back(Leg{r.shape[l], ws[l], nsv[l]});
+  }
+  auto reduce = [](std::vector<Leg>& v) {
+    std::sort(v.begin(), v.end(), [](const Leg& a, const Leg& b) { return a.w > b.w; });
+    std::vector<Leg> o;
+    for (const Leg& g : v) {
+      if (!o.empty() && o.back().w == g.w * g.e && o.back().n == g.n * g.e) {
+        o.back().e *= g.e;
+        o.back().w = g.w;
+        o.back().n = g.n;
+      } else {
+        o.push_back(g);
+      }
+    }
+    v.swap(o);
+  };
+  reduce(rows);
+  reduce(cols);
+  if (rows.size() > 2 || cols.size() > 1) return false;
+  const Leg one{1, 0, 0};
+  const Leg P = rows.size() == 2 ? rows[0] : one;
+  const Leg Q = rows.size() == 2 ? rows[1] : (rows.size() == 1 ? rows[0] : one);
+  const Leg I = cols.empty() ? one : cols[0];
+  if (!cols.empty() && I.w != 1) return false;
+  const Leg L3[3] = {P, Q, I};
+  for (int k = 0; k < 3; ++k) {
+    b.ext[k] = L3[k].e;
+    b.wst[k] = L3[k].w;
+    b.nst[k] = L3[k].n;
+  }
+  b.wcol = dside ? r.t.dst_off - r.drow0 : r.t.src_off - r.srow0;
+  const int64_t W = dside ? r.dW : r.sW;
+  return b.wcol >= 0 && b.wcol + I.e <= W;
+}
+
+// Turns the raw copies into tasks: blocks that share the rows of a narrow
+// matrix (<= 96 columns) on the destination side, else on the source side,
+// become bands; everything else is finished as a plain task.  A destination
+// band writes whole rows, so it must hold every block written into those
+// rows: rows with a block that does not fit are left to plain tasks.
+std::vector<CopyTask> emit_tasks(const std::vector<RawTask>& raw) {
+  constexpr int64_t kMaxW = 96;
+  std::vector<CopyTask> out;
+  std::vector<char> used(raw.size(), 0);
+  for (int side = 1; side >= 0; --side) {
+    const bool dside = side == 1;
+    typedef std::tuple<int, int64_t, int64_t> Key;   // slot, first row start, row length
+    std::map<Key, std::vector<std::pair<size_t, BandLegs>>> bands;
+    std::set<Key> bad;
+    for (size_t i = 0; i < raw.size(); ++i) {
+      if (used[i]) continue;
+      const RawTask& r = raw[i];
+      const int64_t row0 = dside ? r.drow0 : r.srow0, W = dside ? r.dW : r.sW;
+      const int slot = dside ? r.t.dst_slot : r.t.src_slot;
+      if (row0 < 0 || slot < 0) continue;
+      const Key k(slot, row0, W);
+      BandLegs b;
+      if (W > kMaxW || !band_legs(r, dside, b)) bad.insert(k);
+      else bands[k].push_back({i, b});
+    }
+    for (auto& kv : bands) {
+      if (bad.count(kv.first)) continue;
+      auto& m = kv.second;
+      const int64_t W = std::get<2>(kv.first);
+      const BandLegs& f = m[0].second;
+      bool ok = m.size() <= TNX_BAND_MAXM, narrow = false;
+      for (auto& x : m) {
+        const BandLegs& b = x.second;
+        for (int k = 0; k < 2; ++k) ok = ok && b.ext[k] == f.ext[k] && (b.ext[k] == 1 || b.wst[k] == f.wst[k]);
+        narrow = narrow || b.ext[2] < 16;
+      }
+      // a band pays off when some block covers short column runs; a destination
+      // band must be kept whenever it is well formed (its rows are all in it)
+      const int64_t EP = f.ext[0], EQ = f.ext[1], Wp = W | 1;
+      // rows of a row-major matrix: (p, q) starts at row0 + (p * EQ + q) * W
+      ok = ok && (EQ == 1 || f.wst[1] == W) && (EP == 1 || f.wst[0] == EQ * W) && EP * EQ * W <= INT32_MAX;
+      for (auto& x : m) {
+        const BandLegs& b = x.second;
+        int64_t nmax = 0;
+        for (int k = 0; k < 3; ++k) nmax += (b.ext[k] - 1) * b.nst[k];
+        ok = ok && nmax <= INT32_MAX;
+      }
+      if (!ok || (!narrow && !dside)) continue;
+      // tile: up to 64 rows along the leg the members' narrow sides run along
+      const bool qin = EQ > 1 && (EP == 1 || f.nst[1] <= f.nst[0]);
+      const int64_t Ein = qin ? EQ : EP, Eout = qin ? EP : EQ;
+      // balanced: the tiles of a leg differ in extent by one at most
+      auto balance = [](int64_t E, int64_t Tmax) {
+        const int64_t n = (E + Tmax - 1) / Tmax;
+        return (E + n - 1) / n;
+      };
+      const int64_t Tin = balance(Ein, std::min<int64_t>(64, std::max<int64_t>(1, TNX_BAND_CAP / Wp)));
+      const int64_t Tout = balance(Eout, std::max<int64_t>(1, TNX_BAND_CAP / (Tin * Wp)));
+      CopyTask h;
+      memset(&h, 0, sizeof(h));
+      h.tleg = TNX_BAND_HEADER;
+      h.rank = (int)m.size();
+      h.src_slot = dside ? -1 : std::get<0>(kv.first);
+      h.dst_slot = dside ? std::get<0>(kv.first) : -1;
+      (dside ? h.dst_off : h.src_off) = std::get<1>(kv.first);
+      h.shape[0] = (int32_t)EP;
+      h.shape[1] = (int32_t)EQ;
+      h.shape[2] = (int32_t)W;
+      h.shape[3] = (int32_t)(qin ? Tout : Tin);
+      h.shape[4] = (int32_t)(qin ? Tin : Tout);
+      h.shape[5] = dside ? 1 : 0;
+      h.shape[6] = qin ? 1 : 0;
+      h.sstride[0] = (int32_t)(EP > 1 ? f.wst[0] : 0);
+      h.sstride[1] = (int32_t)(EQ > 1 ? f.wst[1] : 0);
+      out.push_back(h);
+      for (auto& x : m) {
+        const RawTask& r = raw[x.first];
+        const BandLegs& b = x.second;
+        CopyTask t = r.t;
+        t.rank = 3;
+        t.nelem = b.ext[0] * b.ext[1] * b.ext[2];
+        for (int k = 0; k < TNX_MAXR; ++k) {
+          t.shape[k] = 1;
+          t.sstride[k] = t.dstride[k] = 0;
+          t.magic[k] = 0;
+          t.shift[k] = 0;
+        }
+        for (int k = 0; k < 3; ++k) {
+          t.shape[k] = (int32_t)b.ext[k];
+          t.sstride[k] = (int32_t)(dside ? b.nst[k] : b.wst[k]);
+          t.dstride[k] = (int32_t)(dside ? b.wst[k] : b.nst[k]);
+          leg_magic((uint64_t)b.ext[k], t.magic[k], t.shift[k]);
+        }
+        t.tleg = TNX_BAND_MEMBER;
+        t.wcol = (int32_t)b.wcol;
+        out.push_back(t);
+        used[x.first] = 1;
+      }
+    }
+  }
+  for (size_t i = 0; i < raw.size(); ++i) {
+    if (used[i]) continue;
+    CopyTask t = raw[i].t;
+    finish_task(t, raw[i].shape, raw[i].ss, raw[i].ds);
+    out.push_back(t);
+  }
+  return out;
+}
+
 }  // namespace
 
 // Chunks of the relayout kernel (see k_copy.cu): large tasks cut into pieces of
 // TNX_COPY_CHUNK elements, consecutive small tasks packed together, transposing
-// tasks cut into 32 x 32 tiles.
+// tasks cut into 32 x 32 tiles, bands into their tiles.
 void tnx_make_copy_chunks(const std::vector<CopyTask>& tasks, std::vector<int4>& chunks) {
   chunks.clear();
   size_t i = 0;
   while (i < tasks.size()) {
     const CopyTask& t = tasks[i];
     if (t.nelem > INT32_MAX) fail(TNX_ERR_UNSUPPORTED, "block above 2^31 elements");
-    if (t.tleg >= 0) {
+    if (t.tleg == TNX_BAND_MEMBER) fail(TNX_ERR_ARG, "internal: band member without its header");
+    if (t.tleg == TNX_BAND_HEADER) {
+      const int64_t ntiles = (int64_t)((t.shape[0] + t.shape[3] - 1) / t.shape[3]) *
+                             ((t.shape[1] + t.shape[4] - 1) / t.shape[4]);
+      for (int64_t k = 0; k < ntiles; ++k) chunks.push_back(make_int4((int)i, (int)k, -2, 0));
+      i += 1 + (size_t)t.rank;
+    } else if (t.tleg >= 0) {
       const int64_t ncols = t.shape[t.tleg], nrows = t.nelem / ncols;
       const int64_t ntiles = ((nrows + 31) / 32) * ((ncols + 31) / 32);
       for (int64_t k = 0; k < ntiles; ++k) chunks.push_back(make_int4((int)i, (int)k, -1, 0));
@@ -518,7 +711,7 @@ void tnx_make_copy_chunks(const std::vector<CopyTask>& tasks, std::vector<int4>&
     } else {
       size_t j = i;
       int64_t tot = 0;
-      while (j < tasks.size() && j - i < TNX_COPY_PACK && tasks[j].tleg < 0 && tasks[j].nelem < TNX_COPY_CHUNK / 2 &&
+      while (j < tasks.size() && j - i < TNX_COPY_PACK && tasks[j].tleg == -1 && tasks[j].nelem < TNX_COPY_CHUNK / 2 &&
              tot + tasks[j].nelem <= TNX_COPY_CHUNK)
         tot += tasks[j++].nelem;
       chunks.push_back(make_int4((int)i, 0, (int)(j - i), (int)tot));
@@ -533,7 +726,38 @@ namespace {
 // Every element a task touches must lie inside its slot's buffer: checked on
 // the host before anything is launched.
 void validate_tasks(const Plan& p, const std::vector<CopyTask>& tasks) {
-  for (const auto& t : tasks) {
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    const CopyTask& t = tasks[i];
+    if (t.tleg == TNX_BAND_HEADER) {
+      // the tile fits the staging buffer, the members follow, and the wide rows
+      // (p, q, c), c < W, lie inside the wide slot
+      const int EP = t.shape[0], EQ = t.shape[1], W = t.shape[2], TP = t.shape[3], TQ = t.shape[4];
+      const bool dw = t.shape[5] != 0;
+      const int slot = dw ? t.dst_slot : t.src_slot;
+      const int64_t base = dw ? t.dst_off : t.src_off;
+      if (t.rank < 1 || t.rank > TNX_BAND_MAXM || i + t.rank >= tasks.size() || EP < 1 || EQ < 1 || W < 1 ||
+          TP < 1 || TQ < 1 || TP > EP || TQ > EQ || (int64_t)TP * TQ * (W | 1) > TNX_BAND_CAP ||
+          t.sstride[0] < 0 || t.sstride[1] < 0)
+        fail(TNX_ERR_ARG, "internal: malformed relayout band");
+      const int64_t mw = base + (int64_t)(EP - 1) * t.sstride[0] + (int64_t)(EQ - 1) * t.sstride[1] + W - 1;
+      if (slot < 0 || slot >= (int)p.slot_elems.size() || base < 0 || mw >= p.slot_elems[slot])
+        fail(TNX_ERR_ARG, "internal: relayout band out of bounds");
+      std::vector<std::pair<int, int>> cols;
+      for (int k = 1; k <= t.rank; ++k) cols.push_back({tasks[i + k].wcol, tasks[i + k].shape[2]});
+      std::sort(cols.begin(), cols.end());
+      for (size_t k = 1; k < cols.size(); ++k)
+        if (cols[k - 1].first + cols[k - 1].second > cols[k].first) fail(TNX_ERR_ARG, "internal: overlapping band members");
+      for (int k = 1; k <= t.rank; ++k) {
+        const CopyTask& m = tasks[i + k];
+        const int32_t* ws = dw ? m.dstride : m.sstride;
+        if (m.tleg != TNX_BAND_MEMBER || m.rank != 3 || m.shape[0] != EP || m.shape[1] != EQ || m.wcol < 0 ||
+            (int64_t)m.wcol + m.shape[2] > W || (dw ? m.dst_slot : m.src_slot) != slot ||
+            (dw ? m.dst_off : m.src_off) != base + m.wcol || (EP > 1 && ws[0] != t.sstride[0]) ||
+            (EQ > 1 && ws[1] != t.sstride[1]) || (m.shape[2] > 1 && ws[2] != 1))
+          fail(TNX_ERR_ARG, "internal: malformed relayout band member");
+      }
+      continue;
+    }
     int64_t ms = t.src_off, md = t.dst_off;
     for (int l = 0; l < t.rank; ++l) {
       if (t.sstride[l] < 0 || t.dstride[l] < 0 || t.shape[l] < 1) fail(TNX_ERR_ARG, "internal: malformed relayout task");
@@ -730,51 +954,48 @@ void build_step(Plan& p, StepPlan& s) {
   s.slotB = p.new_slot(p.alloc_zero((size_t)ob * 8), ob);
   s.slotC = p.new_slot(p.alloc_zero((size_t)oc * 8), oc);
 
-  // relayout tasks
-  std::vector<CopyTask> ta, tb;
   const int rA = A.rank(), rB = B.rank();
-  for (int64_t b = 0; b < A.nblk; ++b) {
-    const int64_t g = s.amap[3 * b];
-    if (g < 0) continue;
-    CopyTask t;
-    memset(&t, 0, sizeof(t));
-    t.src_slot = A.slot;
-    t.dst_slot = s.slotA;
-    t.src_off = A.base[b];
-    t.dst_off = s.offA[g] + s.amap[3 * b + 1] * s.ldK[g] + s.amap[3 * b + 2];
-    std::vector<int64_t> shape, ss, ds;
-    for (int l : s.fa) { shape.push_back(A.bonds[l].deg[A.qn[b * rA + l]]); ss.push_back(A.stride[b * rA + l]); }
-    for (int l : s.ka) { shape.push_back(A.bonds[l].deg[A.qn[b * rA + l]]); ss.push_back(A.stride[b * rA + l]); }
-    ds.assign(shape.size(), 0);
-    int64_t acc = 1;
-    for (int i = (int)shape.size() - 1; i >= (int)s.fa.size(); --i) { ds[i] = acc; acc *= shape[i]; }
-    acc = s.ldK[g];
-    for (int i = (int)s.fa.size() - 1; i >= 0; --i) { ds[i] = acc; acc *= shape[i]; }
-    finish_task(t, shape, ss, ds);
-    ta.push_back(t);
-  }
-  for (int64_t b = 0; b < B.nblk; ++b) {
-    const int64_t g = s.bmap[3 * b];
-    if (g < 0) continue;
-    CopyTask t;
-    memset(&t, 0, sizeof(t));
-    t.src_slot = B.slot;
-    t.dst_slot = s.slotB;
-    t.src_off = B.base[b];
-    t.dst_off = s.offB[g] + s.bmap[3 * b + 2] * s.ldK[g] + s.bmap[3 * b + 1];
-    std::vector<int64_t> shape, ss, ds;
-    for (int l : s.fb) { shape.push_back(B.bonds[l].deg[B.qn[b * rB + l]]); ss.push_back(B.stride[b * rB + l]); }
-    for (int l : s.kb) { shape.push_back(B.bonds[l].deg[B.qn[b * rB + l]]); ss.push_back(B.stride[b * rB + l]); }
-    ds.assign(shape.size(), 0);
-    int64_t acc = 1;
-    for (int i = (int)shape.size() - 1; i >= (int)s.fb.size(); --i) { ds[i] = acc; acc *= shape[i]; }
-    acc = s.ldK[g];
-    for (int i = (int)s.fb.size() - 1; i >= 0; --i) { ds[i] = acc; acc *= shape[i]; }
-    finish_task(t, shape, ss, ds);
-    tb.push_back(t);
-  }
-  s.copyA = upload_tasks(p, ta);
-  s.copyB = upload_tasks(p, tb);
+  // relayout tasks: block b of operand v (free legs f, contracted legs k) into
+  // rows [row, row + rows of b) and columns [col, col + columns of b) of its
+  // group's packed matrix (row length ldK)
+  auto raw_tasks = [&](const OpView& v, int dst_slot, const std::vector<int64_t>& off, const std::vector<int64_t>& map,
+                       int rowi, int coli, const std::vector<int>& f, const std::vector<int>& k) {
+    std::vector<RawTask> raw;
+    const int r = v.rank();
+    for (int64_t b = 0; b < v.nblk; ++b) {
+      const int64_t g = map[3 * b];
+      if (g < 0) continue;
+      RawTask x;
+      CopyTask& t = x.t;
+      memset(&t, 0, sizeof(t));
+      t.src_slot = v.slot;
+      t.dst_slot = dst_slot;
+      t.src_off = v.base[b];
+      x.drow0 = off[g] + map[3 * b + rowi] * s.ldK[g];
+      x.dW = s.ldK[g];
+      t.dst_off = x.drow0 + map[3 * b + coli];
+      if (v.nrow >= 0) {
+        x.srow0 = v.rowstart[b];
+        x.sW = v.rowld[b];
+      }
+      for (int pass = 0; pass < 2; ++pass)
+        for (int l : pass ? k : f) {
+          x.shape.push_back(v.bonds[l].deg[v.qn[b * r + l]]);
+          x.ss.push_back(v.stride[b * r + l]);
+          x.drow.push_back(pass == 0);
+          x.srow.push_back(l < v.nrow);
+        }
+      x.ds.assign(x.shape.size(), 0);
+      int64_t acc = 1;
+      for (int i = (int)x.shape.size() - 1; i >= (int)f.size(); --i) { x.ds[i] = acc; acc *= x.shape[i]; }
+      acc = s.ldK[g];
+      for (int i = (int)f.size() - 1; i >= 0; --i) { x.ds[i] = acc; acc *= x.shape[i]; }
+      raw.push_back(std::move(x));
+    }
+    return emit_tasks(raw);
+  };
+  s.copyA = upload_tasks(p, raw_tasks(A, s.slotA, s.offA, s.amap, 1, 2, s.fa, s.ka));
+  s.copyB = upload_tasks(p, raw_tasks(B, s.slotB, s.offB, s.bmap, 2, 1, s.fb, s.kb));
 
   // grouped GEMM
   std::vector<GemmGroup> gg(G);
@@ -843,6 +1064,7 @@ void build_step(Plan& p, StepPlan& s) {
   // output view: the fused matrices C_g, one block per (row tuple, column tuple)
   OpView& C = s.C;
   C.slot = s.slotC;
+  C.nrow = (int)s.fa.size();
   for (int l : s.fa) { C.bonds.push_back(A.bonds[l]); C.labels.push_back(A.labels[l]); }
   for (int l : s.fb) { C.bonds.push_back(B.bonds[l]); C.labels.push_back(B.labels[l]); }
   std::vector<std::map<std::vector<int32_t>, int64_t>> rows(G), cols(G);
@@ -868,6 +1090,8 @@ void build_step(Plan& p, StepPlan& s) {
         C.qn.insert(C.qn.end(), rr.first.begin(), rr.first.end());
         C.qn.insert(C.qn.end(), cc.first.begin(), cc.first.end());
         C.base.push_back(s.offC[g] + rr.second * N + cc.second);
+        C.rowstart.push_back(s.offC[g] + rr.second * N);
+        C.rowld.push_back(N);
         std::vector<int64_t> st(rC);
         int64_t a2 = 1;
         for (int i = (int)cc.first.size() - 1; i >= 0; --i) {
@@ -935,6 +1159,135 @@ void build_final(Plan& p, const OpView& root, const std::vector<std::string>& to
     off += n;
   }
   p.fin = upload_tasks(p, tasks);
+}
+
+// Fuses every step whose charge groups are all skinny (K <= 16, N <= 64) and
+// whose operand A is relaid entirely by destination bands: one kernel gathers
+// each band's A rows from their sources, forms the product and writes the
+// output rows.  When the step that consumes this step's output relays it
+// entirely by source bands over the same rows, the output rows go straight
+// into that step's packed operand and its relayout is skipped.  The bands'
+// members become per-column descriptors (k_fused.cu).
+void fuse_skinny_steps(Plan& p) {
+  for (size_t si = 0; si < p.steps.size(); ++si) {
+    StepPlan& s = p.steps[si];
+    if (s.nstiles_skinny == 0 || s.ntiles != 0 || s.nstiles != 0) continue;
+    bool ok = true;
+    int64_t maxld = 1, maxN = 1;
+    for (int g = 0; g < s.G; ++g) {
+      ok = ok && s.skinny[g];
+      maxld = std::max(maxld, s.ldK[g]);
+      maxN = std::max(maxN, s.mkn[3 * g + 2]);
+    }
+    if (!ok || maxld > 16 || maxN > 64) continue;
+    // destination bands of A: header, group, first row of the block, extents
+    struct Band { size_t h; int g; int64_t row; int EP, EQ; };
+    std::vector<Band> bands;
+    const std::vector<CopyTask>& ta = s.copyA.h;
+    for (size_t i = 0; ok && i < ta.size(); i += 1 + (size_t)ta[i].rank) {
+      const CopyTask& h = ta[i];
+      if (h.tleg != TNX_BAND_HEADER || h.shape[5] != 1) {
+        ok = false;
+        break;
+      }
+      const auto it = std::upper_bound(s.offA.begin(), s.offA.end(), h.dst_off);
+      const int g = (int)(it - s.offA.begin()) - 1;
+      if (g < 0 || (h.dst_off - s.offA[g]) % s.ldK[g] != 0 || h.shape[2] != s.ldK[g]) {
+        ok = false;
+        break;
+      }
+      bands.push_back(Band{i, g, (h.dst_off - s.offA[g]) / s.ldK[g], h.shape[0], h.shape[1]});
+    }
+    if (!ok || bands.empty()) continue;
+    // the consumer of C: its relayout of C must be source bands only
+    int ti = -1;
+    bool tA = false;
+    for (size_t tj = si + 1; tj < p.steps.size() && ti < 0; ++tj) {
+      if (p.steps[tj].A.slot == s.slotC) ti = (int)tj, tA = true;
+      else if (p.steps[tj].B.slot == s.slotC) ti = (int)tj, tA = false;
+    }
+    std::map<int64_t, size_t> scat;   // C row start -> header
+    const std::vector<CopyTask>* tl = nullptr;
+    if (ti >= 0) {
+      tl = tA ? &p.steps[ti].copyA.h : &p.steps[ti].copyB.h;
+      for (size_t i = 0; i < tl->size(); i += 1 + (size_t)(*tl)[i].rank) {
+        const CopyTask& h = (*tl)[i];
+        if (h.tleg != TNX_BAND_HEADER || h.shape[5] != 0 || h.src_slot != s.slotC) {
+          ti = -1;
+          break;
+        }
+        scat[h.src_off] = i;
+      }
+    }
+    std::vector<long long> sidx(bands.size(), -1);   // scatter header, -1: no reader
+    if (ti >= 0) {
+      size_t matched = 0;
+      for (size_t b = 0; b < bands.size() && ti >= 0; ++b) {
+        const Band& B = bands[b];
+        const auto it = scat.find(s.offC[B.g] + B.row * s.mkn[3 * B.g + 2]);
+        if (it == scat.end()) continue;
+        const CopyTask& h = (*tl)[it->second];
+        if (h.shape[0] != B.EP || h.shape[1] != B.EQ || h.shape[2] != s.mkn[3 * B.g + 2]) ti = -1;
+        sidx[b] = (long long)it->second;
+        ++matched;
+      }
+      if (ti >= 0 && matched != scat.size()) ti = -1;
+    }
+    // column descriptors: a band's members, column by column, with the plan
+    // buffers resolved (a fused step touches no rebindable slot)
+    std::vector<FusedCol> cols;
+    auto internal = [&](int slot) { return slot >= p.nin && slot != p.out_slot && slot < (int)p.h_slots.size(); };
+    auto add_cols = [&](const std::vector<CopyTask>& tasks, size_t h, int64_t W, bool gather) {
+      const size_t first = cols.size();
+      cols.resize(first + (size_t)W, FusedCol{nullptr, 0, 0});
+      if (h == (size_t)-1) return first;
+      for (int k = 1; k <= tasks[h].rank; ++k) {
+        const CopyTask& m = tasks[h + k];
+        const int32_t* st = gather ? m.sstride : m.dstride;
+        const int slot = gather ? m.src_slot : m.dst_slot;
+        if (!internal(slot)) ok = false;
+        if (!ok) break;
+        for (int i = 0; i < m.shape[2]; ++i) {
+          FusedCol& d = cols[first + (size_t)m.wcol + (size_t)i];
+          d.ptr = p.h_slots[slot] + (gather ? m.src_off : m.dst_off) + (int64_t)i * st[2];
+          d.sP = st[0];
+          d.sQ = st[1];
+        }
+      }
+      return first;
+    };
+    auto balance = [](int64_t E, int64_t Tmax) {
+      const int64_t n = (E + Tmax - 1) / Tmax;
+      return (E + n - 1) / n;
+    };
+    std::vector<FusedTile> tiles;
+    for (size_t b = 0; b < bands.size(); ++b) {
+      const Band& B = bands[b];
+      const int64_t N = s.mkn[3 * B.g + 2];
+      const size_t gcol = add_cols(ta, B.h, s.ldK[B.g], true);
+      int64_t scol = -(int64_t)B.EQ - 1;   // write the rows to C
+      if (ti >= 0) scol = (int64_t)add_cols(*tl, sidx[b] < 0 ? (size_t)-1 : (size_t)sidx[b], N, false);
+      const int tQ = (int)balance(B.EQ, 16), tP = (int)balance(B.EP, 128 / tQ);
+      for (int p0 = 0; p0 < B.EP; p0 += tP)
+        for (int q0 = 0; q0 < B.EQ; q0 += tQ)
+          tiles.push_back(FusedTile{B.g, (int32_t)gcol, (int32_t)scol, (int32_t)B.row, p0, q0,
+                                    std::min(tP, B.EP - p0), std::min(tQ, B.EQ - q0), (int32_t)s.ldK[B.g],
+                                    (int32_t)N, 0, 0});
+    }
+    if (!ok || tiles.size() > INT32_MAX || cols.size() > INT32_MAX) continue;
+    s.hFT = tiles;
+    s.hFC = cols;
+    s.dFT = p.upload(tiles);
+    s.dFC = p.upload(cols);
+    s.nftiles = (int)tiles.size();
+    s.fkp = (int)(maxld | 1);
+    s.fnp = (int)(maxN | 1);
+    if (ti >= 0) {
+      s.fscatter = true;
+      StepPlan& t = p.steps[ti];
+      (tA ? t.skipA : t.skipB) = true;
+    }
+  }
 }
 
 std::string plan_key(const tnx_network* net, const std::string& order) {
@@ -1040,23 +1393,31 @@ Plan* ensure_plan(tnx_network* net) {
   };
   OpView root = walk(net->root);
   build_final(*p, root, net->tout);
+  fuse_skinny_steps(*p);
   if (const char* dbg = getenv("TNX_DEBUG_PLAN")) {
     if (*dbg && *dbg != '0') {
       auto stats = [](const TaskList& t) {
-        int tr = 0, packed = 0;
+        int tr = 0, packed = 0, band = 0;
         for (auto& c : t.hchunks) {
-          if (c.z < 0) ++tr;
+          if (c.z == -1) ++tr;
+          else if (c.z == -2) ++band;
           else if (c.z > 1) ++packed;
         }
         return std::to_string(t.n) + " tasks, " + std::to_string(t.total) + " elems, " + std::to_string(t.nchunks) +
-               " chunks (" + std::to_string(tr) + " transpose tiles, " + std::to_string(packed) + " packed)";
+               " chunks (" + std::to_string(tr) + " transpose tiles, " + std::to_string(band) + " band tiles, " +
+               std::to_string(packed) + " packed)";
       };
       fprintf(stderr, "[tnx plan] order %s prec %d\n", p->order.c_str(), p->prec);
       for (size_t i = 0; i < p->steps.size(); ++i) {
         const StepPlan& s = p->steps[i];
         fprintf(stderr, "[tnx plan] step %zu: G=%d flops=%.3e skinny=%.3e tiles=%d skinny_tiles=%d split_tiles=%d\n", i,
                 s.G, s.flops, s.flops_skinny, s.ntiles, s.nstiles_skinny, s.nstiles);
-        fprintf(stderr, "[tnx plan]   A: %s\n[tnx plan]   B: %s\n", stats(s.copyA).c_str(), stats(s.copyB).c_str());
+        fprintf(stderr, "[tnx plan]   A: %s%s\n[tnx plan]   B: %s%s\n", stats(s.copyA).c_str(),
+                s.skipA ? " (done by the fused step)" : "", stats(s.copyB).c_str(),
+                s.skipB ? " (done by the fused step)" : "");
+        if (s.nftiles)
+          fprintf(stderr, "[tnx plan]   fused skinny: %d tiles, output %s\n", s.nftiles,
+                  s.fscatter ? "scattered into the next operand" : "written to C");
       }
       fprintf(stderr, "[tnx plan] final: %s\n", stats(p->fin).c_str());
     }
@@ -1088,13 +1449,18 @@ void enqueue_plan(Plan& p, cudaStream_t st, uint64_t fixed = 0) {
     const bool needA = (s.leavesA & ~fixed) != 0;
     const bool needB = (s.leavesB & ~fixed) != 0;
     if (!needA && !needB) continue;
-    {
+    // relayouts of A and B, unless a fused step does them
+    const bool copyA = needA && !s.skipA && !s.nftiles, copyB = needB && !s.skipB;
+    if (copyA || copyB) {
       ProfScope ps(c, st, TNX_KC_RELAYOUT,
-                   16.0 * (double)((needA ? s.copyA.total : 0) + (needB ? s.copyB.total : 0)));
-      if (needA) CUDA_CHECK(tnx_launch_copy(s.copyA.d, s.copyA.chunks, s.copyA.nchunks, p.d_slots, st));
-      if (needB) CUDA_CHECK(tnx_launch_copy(s.copyB.d, s.copyB.chunks, s.copyB.nchunks, p.d_slots, st));
+                   16.0 * (double)((copyA ? s.copyA.total : 0) + (copyB ? s.copyB.total : 0)));
+      if (copyA) CUDA_CHECK(tnx_launch_copy(s.copyA.d, s.copyA.chunks, s.copyA.nchunks, p.d_slots, st));
+      if (copyB) CUDA_CHECK(tnx_launch_copy(s.copyB.d, s.copyB.chunks, s.copyB.nchunks, p.d_slots, st));
     }
-    if (s.nstiles_skinny) {
+    if (s.nftiles) {
+      ProfScope ps(c, st, TNX_KC_SKINNY, s.flops_skinny);
+      CUDA_CHECK(tnx_launch_fused_skinny(s.dG, s.dFT, s.nftiles, s.dFC, s.fkp, s.fnp, p.d_slots, st));
+    } else if (s.nstiles_skinny) {
       ProfScope ps(c, st, TNX_KC_SKINNY, s.flops_skinny);
       CUDA_CHECK(tnx_launch_gemm_skinny(s.dG, s.dTs, s.nstiles_skinny, p.d_slots, st));
     }

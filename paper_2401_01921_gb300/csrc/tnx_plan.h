@@ -25,6 +25,10 @@ struct OpView {
   std::vector<int32_t> qn;      // nblk * rank, lexicographic
   std::vector<int64_t> base;    // nblk
   std::vector<int64_t> stride;  // nblk * rank
+  // GEMM outputs only: legs [0, nrow) are row legs of a row-major matrix, and
+  // per block the offset of its first row's start and the row length
+  int nrow = -1;
+  std::vector<int64_t> rowstart, rowld;
   int slot = -1;
   int rank() const { return (int)bonds.size(); }
 };
@@ -77,6 +81,16 @@ struct StepPlan {
   int split_tn = 64;            // tile width of the split GEMM (B slices are tiled to match)
   std::vector<SplitGroup> hSG;  // host copies
   std::vector<GemmTile> hST;
+  // fused skinny step (k_fused.cu): one launch replaces the relayout of A, the
+  // skinny product and (when fscatter is set) the next step's relayout of C
+  FusedTile* dFT = nullptr;
+  FusedCol* dFC = nullptr;
+  int nftiles = 0;
+  int fkp = 0, fnp = 0;
+  bool fscatter = false;               // output stored into the next step's operand
+  bool skipA = false, skipB = false;   // this step's operand relayout is done by a fused step
+  std::vector<FusedTile> hFT;
+  std::vector<FusedCol> hFC;
 };
 
 // A captured CUDA graph plus the profiler events recorded inside it.

@@ -4,6 +4,7 @@ Integer tables must match bit-exactly; FP64 results to relative Frobenius
 error <= 1e-12 (the accumulation order differs; the oracle sums in numpy).
 """
 import math
+import re
 
 import numpy as np
 import pytest
@@ -76,6 +77,25 @@ def test_apply_parity_f64_chi2048_sector_scaled(ctx):
     onet, _ = oracle_heff(wl)
     ref = onet.launch()
     assert rel_fro(out.block_dict(), ref) <= TOL_F64
+
+
+@pytest.mark.parametrize("prec", ["f64", "split_bf16"])
+def test_relayout_bands(ctx, capfd, monkeypatch, prec):
+    """Blocks sharing the rows of a narrow matrix move as bands: the MPO step's
+    packed operand (destination rows of 8-20 columns) and the last step's operand
+    read from the MPO step's output (source rows of <= 20 columns).  Ragged
+    sector sizes give ragged tiles; the apply must still match the oracle."""
+    monkeypatch.setenv("TNX_DEBUG_PLAN", "1")
+    wl = I.heisenberg_workload(40, 9)
+    net, T, B = lib_heff(ctx, wl, prec=prec)
+    out = net.launch(B["psi"])
+    err = capfd.readouterr().err
+    bands = [int(m) for m in re.findall(r"(\d+) band tiles", err)]
+    assert sum(1 for b in bands if b > 0) >= 2, err
+    onet, _ = oracle_heff(wl)
+    ref = onet.launch()
+    tol = TOL_F64 if prec == "f64" else 1e-10   # split precision: the bound of the split-GEMM tests
+    assert rel_fro(out.block_dict(), ref) <= tol
 
 
 def test_launch_into_reuses_plan_and_tracks_new_data(ctx):
