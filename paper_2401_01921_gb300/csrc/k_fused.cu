@@ -35,7 +35,7 @@ struct FusedSmem {
   int s_cnt[FMAXN];
 };
 
-__global__ void __launch_bounds__(FT) fused_skinny_kernel(const GemmGroup* __restrict__ groups,
+__global__ void __launch_bounds__(FT, 6) fused_skinny_kernel(const GemmGroup* __restrict__ groups,
                                                           const FusedTile* __restrict__ tiles,
                                                           const FusedCol* __restrict__ cols, int kp, int np,
                                                           double* const* __restrict__ slots) {

@@ -577,23 +577,34 @@ bool band_legs(const RawTask& r, bool dside, BandLegs& b) {
 // matrix (<= 96 columns) on the destination side, else on the source side,
 // become bands; everything else is finished as a plain task.  A destination
 // band writes whole rows, so it must hold every block written into those
-// rows: rows with a block that does not fit are left to plain tasks.
-std::vector<CopyTask> emit_tasks(const std::vector<RawTask>& raw) {
+// rows: rows with a block that does not fit are left to plain tasks.  A
+// destination band is formed when some block runs along another leg on its
+// source side than along its columns (a plain copy would scatter it), or
+// always with `dest_bands` (the operand of a step the fused kernel gathers);
+// a source band when some block covers fewer than 16 columns.  Source bands
+// are formed first with `source_first` (the output of a fused step, which
+// stores into this operand when it is made of source bands only).
+std::vector<CopyTask> emit_tasks(const std::vector<RawTask>& raw, bool dest_bands, bool source_first) {
   constexpr int64_t kMaxW = 96;
   std::vector<CopyTask> out;
   std::vector<char> used(raw.size(), 0);
-  for (int side = 1; side >= 0; --side) {
-    const bool dside = side == 1;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool dside = source_first ? pass == 1 : pass == 0;
     typedef std::tuple<int, int64_t, int64_t> Key;   // slot, first row start, row length
     std::map<Key, std::vector<std::pair<size_t, BandLegs>>> bands;
     std::set<Key> bad;
     for (size_t i = 0; i < raw.size(); ++i) {
-      if (used[i]) continue;
       const RawTask& r = raw[i];
       const int64_t row0 = dside ? r.drow0 : r.srow0, W = dside ? r.dW : r.sW;
       const int slot = dside ? r.t.dst_slot : r.t.src_slot;
       if (row0 < 0 || slot < 0) continue;
       const Key k(slot, row0, W);
+      // a block already moved by a source band still writes into these
+      // destination rows: they cannot be written whole
+      if (used[i]) {
+        if (dside) bad.insert(k);
+        continue;
+      }
       BandLegs b;
       if (W > kMaxW || !band_legs(r, dside, b)) bad.insert(k);
       else bands[k].push_back({i, b});
@@ -603,14 +614,13 @@ std::vector<CopyTask> emit_tasks(const std::vector<RawTask>& raw) {
       auto& m = kv.second;
       const int64_t W = std::get<2>(kv.first);
       const BandLegs& f = m[0].second;
-      bool ok = m.size() <= TNX_BAND_MAXM, narrow = false;
+      bool ok = m.size() <= TNX_BAND_MAXM, narrow = false, transposing = false;
       for (auto& x : m) {
         const BandLegs& b = x.second;
         for (int k = 0; k < 2; ++k) ok = ok && b.ext[k] == f.ext[k] && (b.ext[k] == 1 || b.wst[k] == f.wst[k]);
         narrow = narrow || b.ext[2] < 16;
+        transposing = transposing || (b.ext[2] > 1 && b.nst[2] != 1);
       }
-      // a band pays off when some block covers short column runs; a destination
-      // band must be kept whenever it is well formed (its rows are all in it)
       const int64_t EP = f.ext[0], EQ = f.ext[1], Wp = W | 1;
       // rows of a row-major matrix: (p, q) starts at row0 + (p * EQ + q) * W
       ok = ok && (EQ == 1 || f.wst[1] == W) && (EP == 1 || f.wst[0] == EQ * W) && EP * EQ * W <= INT32_MAX;
@@ -620,7 +630,7 @@ std::vector<CopyTask> emit_tasks(const std::vector<RawTask>& raw) {
         for (int k = 0; k < 3; ++k) nmax += (b.ext[k] - 1) * b.nst[k];
         ok = ok && nmax <= INT32_MAX;
       }
-      if (!ok || (!narrow && !dside)) continue;
+      if (!ok || (dside ? !(dest_bands || transposing) : !narrow)) continue;
       // tile: up to 64 rows along the leg the members' narrow sides run along
       const bool qin = EQ > 1 && (EP == 1 || f.nst[1] <= f.nst[0]);
       const int64_t Ein = qin ? EQ : EP, Eout = qin ? EP : EQ;
@@ -959,7 +969,7 @@ void build_step(Plan& p, StepPlan& s) {
   // rows [row, row + rows of b) and columns [col, col + columns of b) of its
   // group's packed matrix (row length ldK)
   auto raw_tasks = [&](const OpView& v, int dst_slot, const std::vector<int64_t>& off, const std::vector<int64_t>& map,
-                       int rowi, int coli, const std::vector<int>& f, const std::vector<int>& k) {
+                       int rowi, int coli, const std::vector<int>& f, const std::vector<int>& k, bool dest_bands) {
     std::vector<RawTask> raw;
     const int r = v.rank();
     for (int64_t b = 0; b < v.nblk; ++b) {
@@ -992,10 +1002,14 @@ void build_step(Plan& p, StepPlan& s) {
       for (int i = (int)f.size() - 1; i >= 0; --i) { x.ds[i] = acc; acc *= x.shape[i]; }
       raw.push_back(std::move(x));
     }
-    return emit_tasks(raw);
+    return emit_tasks(raw, dest_bands, v.skinny_out && !dest_bands);
   };
-  s.copyA = upload_tasks(p, raw_tasks(A, s.slotA, s.offA, s.amap, 1, 2, s.fa, s.ka));
-  s.copyB = upload_tasks(p, raw_tasks(B, s.slotB, s.offB, s.bmap, 2, 1, s.fb, s.kb));
+  // a step whose groups all have K <= 16 runs on the fused skinny kernel,
+  // which gathers its A through destination bands
+  bool skinny_step = G > 0;
+  for (int g = 0; g < G; ++g) skinny_step = skinny_step && s.mkn[3 * g + 1] <= 16 && s.mkn[3 * g + 2] <= 64;
+  s.copyA = upload_tasks(p, raw_tasks(A, s.slotA, s.offA, s.amap, 1, 2, s.fa, s.ka, skinny_step));
+  s.copyB = upload_tasks(p, raw_tasks(B, s.slotB, s.offB, s.bmap, 2, 1, s.fb, s.kb, false));
 
   // grouped GEMM
   std::vector<GemmGroup> gg(G);
@@ -1065,6 +1079,7 @@ void build_step(Plan& p, StepPlan& s) {
   OpView& C = s.C;
   C.slot = s.slotC;
   C.nrow = (int)s.fa.size();
+  C.skinny_out = skinny_step;
   for (int l : s.fa) { C.bonds.push_back(A.bonds[l]); C.labels.push_back(A.labels[l]); }
   for (int l : s.fb) { C.bonds.push_back(B.bonds[l]); C.labels.push_back(B.labels[l]); }
   std::vector<std::map<std::vector<int32_t>, int64_t>> rows(G), cols(G);
@@ -1167,7 +1182,10 @@ void build_final(Plan& p, const OpView& root, const std::vector<std::string>& to
 // output rows.  When the step that consumes this step's output relays it
 // entirely by source bands over the same rows, the output rows go straight
 // into that step's packed operand and its relayout is skipped.  The bands'
-// members become per-column descriptors (k_fused.cu).
+// members become per-column descriptors (k_fused.cu).  A consumer that is
+// itself fused gathers its A from this output, so it must be written: that
+// holds by construction, as a fused step's A relayout is made of destination
+// bands, which a scattering step requires to be source bands.
 void fuse_skinny_steps(Plan& p) {
   for (size_t si = 0; si < p.steps.size(); ++si) {
     StepPlan& s = p.steps[si];

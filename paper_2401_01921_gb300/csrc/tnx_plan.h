@@ -29,6 +29,7 @@ struct OpView {
   // per block the offset of its first row's start and the row length
   int nrow = -1;
   std::vector<int64_t> rowstart, rowld;
+  bool skinny_out = false;      // output of a step whose groups all have K <= 16
   int slot = -1;
   int rank() const { return (int)bonds.size(); }
 };

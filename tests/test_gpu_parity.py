@@ -98,6 +98,23 @@ def test_relayout_bands(ctx, capfd, monkeypatch, prec):
     assert rel_fro(out.block_dict(), ref) <= tol
 
 
+@pytest.mark.parametrize("order, mode", [("(L,((psi,R),(W1,W2)))", "scattered into the next operand"),
+                                         ("((((L,psi),W1),W2),R)", "written to C")])
+def test_fused_skinny_steps(ctx, capfd, monkeypatch, order, mode):
+    """MPO steps (every charge group K <= 16) run as one gather-product-scatter
+    kernel: in the block-sparse optimal order the output goes straight into the
+    last step's operand; in the chain order the W1 step's output is read by a
+    fused step again and is written to C.  Both must match the oracle."""
+    monkeypatch.setenv("TNX_DEBUG_PLAN", "1")
+    wl = I.heisenberg_workload(40, 9)
+    net, T, B = lib_heff(ctx, wl, order=order)
+    out = net.launch(B["psi"])
+    err = capfd.readouterr().err
+    assert "fused skinny" in err and mode in err, err
+    onet, _ = oracle_heff(wl, order=order)
+    assert rel_fro(out.block_dict(), onet.launch()) <= TOL_F64
+
+
 def test_launch_into_reuses_plan_and_tracks_new_data(ctx):
     import paper_2401_01921_gb300 as tnx
     wl = I.heisenberg_workload(40, 9)
