@@ -63,8 +63,10 @@ TaskList merge_tasks(tnx_batch& B, const std::vector<const TaskList*>& parts) {
   std::vector<CopyTask> tasks;
   std::vector<int4> chunks;
   TaskList out;
+  // batches run the unfused kernels: bands, which only pay off inside a fused
+  // step, go back to plain tasks (small tasks of many instances pack together)
   for (size_t i = 0; i < parts.size(); ++i) {
-    for (CopyTask t : parts[i]->h) {
+    for (CopyTask t : tnx_unband_tasks(parts[i]->h)) {
       t.src_slot = shift_slot(t.src_slot, B.base[i]);
       t.dst_slot = shift_slot(t.dst_slot, B.base[i]);
       tasks.push_back(t);

@@ -577,13 +577,12 @@ bool band_legs(const RawTask& r, bool dside, BandLegs& b) {
 // matrix (<= 96 columns) on the destination side, else on the source side,
 // become bands; everything else is finished as a plain task.  A destination
 // band writes whole rows, so it must hold every block written into those
-// rows: rows with a block that does not fit are left to plain tasks.  A
-// destination band is formed when some block runs along another leg on its
-// source side than along its columns (a plain copy would scatter it), or
-// always with `dest_bands` (the operand of a step the fused kernel gathers);
-// a source band when some block covers fewer than 16 columns.  Source bands
-// are formed first with `source_first` (the output of a fused step, which
-// stores into this operand when it is made of source bands only).
+// rows: rows with a block that does not fit are left to plain tasks.  Bands
+// serve the fused skinny step only (on their own they measured no faster than
+// plain tasks, and far slower for many small blocks): destination bands with
+// `dest_bands` (the operand such a step gathers), source bands with
+// `source_first` (the output of such a step, which it stores straight into
+// this operand when the operand is made of source bands only).
 std::vector<CopyTask> emit_tasks(const std::vector<RawTask>& raw, bool dest_bands, bool source_first) {
   constexpr int64_t kMaxW = 96;
   std::vector<CopyTask> out;
@@ -614,12 +613,11 @@ std::vector<CopyTask> emit_tasks(const std::vector<RawTask>& raw, bool dest_band
       auto& m = kv.second;
       const int64_t W = std::get<2>(kv.first);
       const BandLegs& f = m[0].second;
-      bool ok = m.size() <= TNX_BAND_MAXM, narrow = false, transposing = false;
+      bool ok = m.size() <= TNX_BAND_MAXM, narrow = false;
       for (auto& x : m) {
         const BandLegs& b = x.second;
         for (int k = 0; k < 2; ++k) ok = ok && b.ext[k] == f.ext[k] && (b.ext[k] == 1 || b.wst[k] == f.wst[k]);
         narrow = narrow || b.ext[2] < 16;
-        transposing = transposing || (b.ext[2] > 1 && b.nst[2] != 1);
       }
       const int64_t EP = f.ext[0], EQ = f.ext[1], Wp = W | 1;
       // rows of a row-major matrix: (p, q) starts at row0 + (p * EQ + q) * W
@@ -630,7 +628,7 @@ std::vector<CopyTask> emit_tasks(const std::vector<RawTask>& raw, bool dest_band
         for (int k = 0; k < 3; ++k) nmax += (b.ext[k] - 1) * b.nst[k];
         ok = ok && nmax <= INT32_MAX;
       }
-      if (!ok || (dside ? !(dest_bands || transposing) : !narrow)) continue;
+      if (!ok || (dside ? !dest_bands : !(source_first && narrow))) continue;
       // tile: up to 64 rows along the leg the members' narrow sides run along
       const bool qin = EQ > 1 && (EP == 1 || f.nst[1] <= f.nst[0]);
       const int64_t Ein = qin ? EQ : EP, Eout = qin ? EP : EQ;
@@ -693,6 +691,30 @@ std::vector<CopyTask> emit_tasks(const std::vector<RawTask>& raw, bool dest_band
 }
 
 }  // namespace
+
+// The same copies as plain tasks: band headers dropped, members finished as
+// ordinary tasks (a destination band's row gaps are zeros already).
+std::vector<CopyTask> tnx_unband_tasks(const std::vector<CopyTask>& tasks) {
+  std::vector<CopyTask> out;
+  for (const CopyTask& t : tasks) {
+    if (t.tleg == TNX_BAND_HEADER) continue;
+    if (t.tleg != TNX_BAND_MEMBER) {
+      out.push_back(t);
+      continue;
+    }
+    CopyTask u = t;
+    std::vector<int64_t> shape, ss, ds;
+    for (int l = 0; l < t.rank; ++l) {
+      shape.push_back(t.shape[l]);
+      ss.push_back(t.sstride[l]);
+      ds.push_back(t.dstride[l]);
+    }
+    u.wcol = 0;
+    finish_task(u, shape, ss, ds);
+    out.push_back(u);
+  }
+  return out;
+}
 
 // Chunks of the relayout kernel (see k_copy.cu): large tasks cut into pieces of
 // TNX_COPY_CHUNK elements, consecutive small tasks packed together, transposing
@@ -1186,10 +1208,10 @@ void build_final(Plan& p, const OpView& root, const std::vector<std::string>& to
 // itself fused gathers its A from this output, so it must be written: that
 // holds by construction, as a fused step's A relayout is made of destination
 // bands, which a scattering step requires to be source bands.
-void fuse_skinny_steps(Plan& p) {
-  for (size_t si = 0; si < p.steps.size(); ++si) {
+bool fuse_skinny_step(Plan& p, size_t si, int ti, bool tA) {
+  {
     StepPlan& s = p.steps[si];
-    if (s.nstiles_skinny == 0 || s.ntiles != 0 || s.nstiles != 0) continue;
+    if (s.nstiles_skinny == 0 || s.ntiles != 0 || s.nstiles != 0) return false;
     bool ok = true;
     int64_t maxld = 1, maxN = 1;
     for (int g = 0; g < s.G; ++g) {
@@ -1197,7 +1219,7 @@ void fuse_skinny_steps(Plan& p) {
       maxld = std::max(maxld, s.ldK[g]);
       maxN = std::max(maxN, s.mkn[3 * g + 2]);
     }
-    if (!ok || maxld > 16 || maxN > 64) continue;
+    if (!ok || maxld > 16 || maxN > 64) return false;
     // destination bands of A: header, group, first row of the block, extents
     struct Band { size_t h; int g; int64_t row; int EP, EQ; };
     std::vector<Band> bands;
@@ -1216,14 +1238,8 @@ void fuse_skinny_steps(Plan& p) {
       }
       bands.push_back(Band{i, g, (h.dst_off - s.offA[g]) / s.ldK[g], h.shape[0], h.shape[1]});
     }
-    if (!ok || bands.empty()) continue;
-    // the consumer of C: its relayout of C must be source bands only
-    int ti = -1;
-    bool tA = false;
-    for (size_t tj = si + 1; tj < p.steps.size() && ti < 0; ++tj) {
-      if (p.steps[tj].A.slot == s.slotC) ti = (int)tj, tA = true;
-      else if (p.steps[tj].B.slot == s.slotC) ti = (int)tj, tA = false;
-    }
+    if (!ok || bands.empty()) return false;
+    // the consumer of C (step ti): its relayout of C must be source bands only
     std::map<int64_t, size_t> scat;   // C row start -> header
     const std::vector<CopyTask>* tl = nullptr;
     if (ti >= 0) {
@@ -1292,7 +1308,11 @@ void fuse_skinny_steps(Plan& p) {
                                     std::min(tP, B.EP - p0), std::min(tQ, B.EQ - q0), (int32_t)s.ldK[B.g],
                                     (int32_t)N, 0, 0});
     }
-    if (!ok || tiles.size() > INT32_MAX || cols.size() > INT32_MAX) continue;
+    // many nearly empty tiles (small sectors) run faster unfused: plain
+    // relayouts pack small blocks, the skinny kernel fills 128-row tiles
+    int64_t rows = 0;
+    for (const Band& B : bands) rows += (int64_t)B.EP * B.EQ;
+    if (!ok || tiles.size() > INT32_MAX || cols.size() > INT32_MAX || rows < 32 * (int64_t)tiles.size()) return false;
     s.hFT = tiles;
     s.hFC = cols;
     s.dFT = p.upload(tiles);
@@ -1305,6 +1325,35 @@ void fuse_skinny_steps(Plan& p) {
       StepPlan& t = p.steps[ti];
       (tA ? t.skipA : t.skipB) = true;
     }
+  }
+  return true;
+}
+
+void fuse_skinny_steps(Plan& p) {
+  // a relayout whose bands no fused step uses goes back to plain tasks (a
+  // relayout holds destination bands, for its own step's gather, or source
+  // bands, for the producing step's scatter, never both)
+  auto plain = [&](TaskList& t, int dest) {
+    for (const CopyTask& x : t.h)
+      if (x.tleg == TNX_BAND_HEADER && x.shape[5] == dest) {
+        t = upload_tasks(p, tnx_unband_tasks(t.h));
+        return;
+      }
+  };
+  auto consumer = [&](size_t si, bool& tA) -> int {
+    for (size_t tj = si + 1; tj < p.steps.size(); ++tj) {
+      if (p.steps[tj].A.slot == p.steps[si].slotC) return tA = true, (int)tj;
+      if (p.steps[tj].B.slot == p.steps[si].slotC) return tA = false, (int)tj;
+    }
+    return -1;
+  };
+  for (size_t si = 0; si < p.steps.size(); ++si) {
+    StepPlan& s = p.steps[si];
+    bool cA = false;
+    const int ci = consumer(si, cA);
+    const bool fused = fuse_skinny_step(p, si, ci, cA);
+    if (!fused) plain(s.copyA, 1);
+    if (ci >= 0 && !s.fscatter) plain(cA ? p.steps[ci].copyA : p.steps[ci].copyB, 0);
   }
 }
 

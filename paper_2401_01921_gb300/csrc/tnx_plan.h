@@ -172,6 +172,7 @@ std::vector<int2> tnx_slice_schedule(std::vector<SliceJob>& jobs);
 
 // relayout chunks (tnx_network.cpp)
 void tnx_make_copy_chunks(const std::vector<CopyTask>& tasks, std::vector<int4>& chunks);
+std::vector<CopyTask> tnx_unband_tasks(const std::vector<CopyTask>& tasks);
 
 // enqueue helpers shared by the C-ABI, the batch and the serving modules (tnx_network.cpp)
 Plan* tnx_ensure_plan(tnx_network* net);

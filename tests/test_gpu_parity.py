@@ -81,18 +81,20 @@ def test_apply_parity_f64_chi2048_sector_scaled(ctx):
 
 @pytest.mark.parametrize("prec", ["f64", "split_bf16"])
 def test_relayout_bands(ctx, capfd, monkeypatch, prec):
-    """Blocks sharing the rows of a narrow matrix move as bands: the MPO step's
-    packed operand (destination rows of 8-20 columns) and the last step's operand
-    read from the MPO step's output (source rows of <= 20 columns).  Ragged
-    sector sizes give ragged tiles; the apply must still match the oracle."""
+    """Blocks sharing the rows of a narrow matrix are planned as bands for the
+    fused MPO step: its packed operand (destination rows of <= 16 columns) and
+    the last step's operand read from its output (source rows of <= 64
+    columns).  Ragged sector sizes give ragged tiles; the apply must still match
+    the oracle."""
     monkeypatch.setenv("TNX_DEBUG_PLAN", "1")
-    wl = I.heisenberg_workload(40, 9)
-    net, T, B = lib_heff(ctx, wl, prec=prec)
+    wl = I.heisenberg_workload(512, 20)
+    order = "(L,((psi,R),(W1,W2)))"
+    net, T, B = lib_heff(ctx, wl, order=order, prec=prec)
     out = net.launch(B["psi"])
     err = capfd.readouterr().err
     bands = [int(m) for m in re.findall(r"(\d+) band tiles", err)]
     assert sum(1 for b in bands if b > 0) >= 2, err
-    onet, _ = oracle_heff(wl)
+    onet, _ = oracle_heff(wl, order=order)
     ref = onet.launch()
     tol = TOL_F64 if prec == "f64" else 1e-10   # split precision: the bound of the split-GEMM tests
     assert rel_fro(out.block_dict(), ref) <= tol
@@ -104,9 +106,10 @@ def test_fused_skinny_steps(ctx, capfd, monkeypatch, order, mode):
     """MPO steps (every charge group K <= 16) run as one gather-product-scatter
     kernel: in the block-sparse optimal order the output goes straight into the
     last step's operand; in the chain order the W1 step's output is read by a
-    fused step again and is written to C.  Both must match the oracle."""
+    fused step again and is written to C.  Both must match the oracle.  (Steps
+    whose sectors are so small that the tiles stay nearly empty run unfused.)"""
     monkeypatch.setenv("TNX_DEBUG_PLAN", "1")
-    wl = I.heisenberg_workload(40, 9)
+    wl = I.heisenberg_workload(512, 20)
     net, T, B = lib_heff(ctx, wl, order=order)
     out = net.launch(B["psi"])
     err = capfd.readouterr().err
