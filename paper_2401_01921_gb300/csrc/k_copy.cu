@@ -24,6 +24,8 @@
 // an index is split over the legs with multiply-high divisions by the leg
 // extents (constants the planner precomputes) instead of hardware integer
 // divisions.
+#include <algorithm>
+
 #include "tnx_band.cuh"
 
 namespace {
@@ -40,14 +42,16 @@ __device__ __forceinline__ int fdiv(int n, uint32_t magic, uint32_t shift) {
 // per index of S and one row per index of the other legs (in task order), and
 // move it in 32 x 32 tiles through shared memory: loads run along S, stores
 // along the rows (consecutive rows are consecutive in the destination).
-__device__ void copy_transpose(const CopyTask& t, int tile, double* const* __restrict__ slots, double (*sm)[33]) {
+template <bool SCALED>
+__device__ void copy_transpose(const CopyTask& t, int tile, double* const* __restrict__ slots, double (*sm)[33],
+                               const double* src_base, double scale) {
   const int r = t.rank, S = t.tleg;
   const int ncols = t.shape[S];
   const int nrows = (int)(t.nelem / ncols);
   const int nct = (ncols + 31) >> 5;
   const int r0 = (tile / nct) << 5, c0 = (tile % nct) << 5;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const double* src = t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr;
+  const double* src = SCALED ? src_base + t.src_off : (t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr);
   double* dst = slots[t.dst_slot] + t.dst_off;
   // row index -> (source offset, destination offset) over the legs other than S
   auto bases = [&](int row, int& so, int& dof) {
@@ -69,7 +73,8 @@ __device__ void copy_transpose(const CopyTask& t, int tile, double* const* __res
     if (row < nrows && c < ncols) {
       int so, dof;
       bases(row, so, dof);
-      sm[rr][lane] = src ? __ldg(src + so + c * t.sstride[S]) : 0.0;
+      const double x = src ? __ldg(src + so + c * t.sstride[S]) : 0.0;
+      sm[rr][lane] = SCALED ? x * scale : x;
     }
   }
   __syncthreads();
@@ -182,7 +187,9 @@ __device__ __forceinline__ void offsets(const CopyTask& t, int i, int& so, int& 
 // along the innermost leg; a carry into the next leg re-decomposes.
 constexpr int EPT = 2;
 
-__device__ __forceinline__ void copy_run(const CopyTask& t, const double* src, double* dst, int e0, int n) {
+template <bool SCALED>
+__device__ __forceinline__ void copy_run(const CopyTask& t, const double* src, double* dst, int e0, int n,
+                                         double scale) {
   int so, dof;
   offsets(t, e0, so, dof);
   const int last = t.rank - 1;
@@ -207,8 +214,21 @@ __device__ __forceinline__ void copy_run(const CopyTask& t, const double* src, d
   }
 #pragma unroll
   for (int j = 0; j < EPT; ++j)
-    if (j < n) dst[d[j]] = v[j];
+    if (j < n) dst[d[j]] = SCALED ? v[j] * scale : v[j];
 }
+
+// Scaled relayout (the normalising step of a Lanczos iteration, fused with the
+// next apply's relayout of the vector): every task reads src (instead of its
+// source slot) times *inv, and blocks past the chunks write vdst = src * *inv
+// over vn contiguous entries.  Nothing runs once the solve has stopped.
+struct ScaleArgs {
+  const double* src;
+  double* vdst;
+  int64_t vn;
+  int nchunks;
+  const double* inv;
+  const int32_t* state;
+};
 
 // chunk = (first task, first element, number of tasks, number of elements).
 // One task: its elements [first, first + count), EPT consecutive ones per
@@ -216,9 +236,21 @@ __device__ __forceinline__ void copy_run(const CopyTask& t, const double* src, d
 // chunk's descriptors are staged in shared memory and each thread finds its
 // task by binary search over their starts.  Task count -1 marks one 32 x 32
 // tile of a transposing task, -2 one tile of a band.
+template <bool SCALED>
 __global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ tasks, const int4* __restrict__ chunks,
-                                                  double* const* __restrict__ slots) {
+                                                  double* const* __restrict__ slots, ScaleArgs sa) {
   tnx_grid_dependency();
+  double scale = 1.0;
+  if (SCALED) {
+    if (*(volatile const int32_t*)(sa.state + 1) != 0) return;   // the solve has stopped
+    scale = *sa.inv;
+    if ((int)blockIdx.x >= sa.nchunks) {
+      const int64_t stride = (int64_t)(gridDim.x - sa.nchunks) * CT;
+      for (int64_t i = (int64_t)(blockIdx.x - sa.nchunks) * CT + threadIdx.x; i < sa.vn; i += stride)
+        sa.vdst[i] = sa.src[i] * scale;
+      return;
+    }
+  }
   // packed tasks | transposing tile | band tile (members, then the staged rows)
   constexpr int kPack = TNX_COPY_PACK * (int)sizeof(CopyTask);
   constexpr int kBand = TNX_BAND_MAXM * (int)sizeof(tnx_band::Member) + TNX_BAND_CAP * 8;
@@ -229,10 +261,10 @@ __global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ t
   CopyTask* st = (CopyTask*)raw;
   const int4 ch = chunks[blockIdx.x];
   if (ch.z == -1) {
-    copy_transpose(tasks[ch.x], ch.y, slots, (double (*)[33])raw);
+    copy_transpose<SCALED>(tasks[ch.x], ch.y, slots, (double (*)[33])raw, sa.src, scale);
     return;
   }
-  if (ch.z == -2) {
+  if (!SCALED && ch.z == -2) {
     copy_band(tasks, ch.x, ch.y, slots, (double*)(raw + TNX_BAND_MAXM * sizeof(tnx_band::Member)), (tnx_band::Member*)raw, sstart);
     return;
   }
@@ -244,10 +276,11 @@ __global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ t
     }
     __syncthreads();
     const CopyTask& t = st[0];
-    const double* src = t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr;
+    const double* src = SCALED ? sa.src + t.src_off : (t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr);
     double* dst = slots[t.dst_slot] + t.dst_off;
     const int end = ch.y + ch.w;
-    for (int e = ch.y + threadIdx.x * EPT; e < end; e += CT * EPT) copy_run(t, src, dst, e, min(EPT, end - e));
+    for (int e = ch.y + threadIdx.x * EPT; e < end; e += CT * EPT)
+      copy_run<SCALED>(t, src, dst, e, min(EPT, end - e), scale);
     return;
   }
   // several small tasks
@@ -275,10 +308,11 @@ __global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ t
       if (sstart[mid] <= e) lo = mid; else hi = mid;
     }
     const CopyTask& t = st[lo];
-    const double* src = t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr;
+    const double* src = SCALED ? sa.src + t.src_off : (t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr);
     int so, dof;
     offsets(t, e - sstart[lo], so, dof);
-    slots[t.dst_slot][t.dst_off + dof] = src ? __ldg(src + so) : 0.0;
+    const double x = src ? __ldg(src + so) : 0.0;
+    slots[t.dst_slot][t.dst_off + dof] = SCALED ? x * scale : x;
   }
 }
 
@@ -288,7 +322,24 @@ cudaError_t tnx_launch_copy(const CopyTask* tasks, const int4* chunks, int nchun
                             cudaStream_t st) {
   if (nchunks <= 0) return cudaSuccess;
   {
-    const cudaError_t le = tnx_launch(copy_kernel, dim3(nchunks), dim3(CT), 0, st, tasks, chunks, slots);
+    const cudaError_t le = tnx_launch(copy_kernel<false>, dim3(nchunks), dim3(CT), 0, st, tasks, chunks, slots,
+                                      ScaleArgs{nullptr, nullptr, 0, nchunks, nullptr, nullptr});
+    if (le != cudaSuccess) return le;
+  }
+  tnx_note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tnx_launch_copy_scaled(const CopyTask* tasks, const int4* chunks, int nchunks, double* const* slots,
+                                   const double* src, double* vdst, int64_t vn, const double* inv,
+                                   const int32_t* state, cudaStream_t st) {
+  if (nchunks < 0 || vn < 0) return cudaErrorInvalidValue;
+  const int64_t vb = std::min<int64_t>((vn + CT * 4 - 1) / (CT * 4), 1216);
+  const int64_t grid = (int64_t)nchunks + std::max<int64_t>(vb, 1);
+  if (grid > INT32_MAX) return cudaErrorInvalidValue;
+  {
+    const cudaError_t le = tnx_launch(copy_kernel<true>, dim3((unsigned)grid), dim3(CT), 0, st, tasks, chunks, slots,
+                                      ScaleArgs{src, vdst, vn, nchunks, inv, state});
     if (le != cudaSuccess) return le;
   }
   tnx_note_launch(1);

@@ -510,12 +510,14 @@ cudaError_t tnx_launch_lanczos_set_input(double** slot_ptr, const LanczosDev& L,
   return cudaGetLastError();
 }
 
-// The operator has been applied: L.w = H v_j.  One Lanczos step: classical
+// The operator has been applied: L.w = H v_j.  One Lanczos step (without the
+// final v_{j+1} = w / beta_{j+1} when `normalize` is false: the caller then
+// fuses it with the next apply's relayout of the vector): classical
 // Gram-Schmidt against v_0..v_j done twice (the first pass also yields
 // alpha_j = <v_j, H v_j> and removes the three-term recurrence), the norm of
 // the result folded into the second update, then beta_{j+1}, the stopping
 // test and v_{j+1} = w / beta_{j+1}.
-cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, double** next_slot, cudaStream_t st) {
+cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, double** next_slot, cudaStream_t st, bool normalize) {
   const int nb = grid_for(L.n);
   const int m = j + 1;
   const int mb = multidot_blocks(L.n);
@@ -548,11 +550,13 @@ cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, double** next_sl
     if (le != cudaSuccess) return le;
   }
   tnx_note_launch(1);
-  {
-    const cudaError_t le = tnx_launch(lanczos_normalize_kernel, dim3(nb), dim3(RT), 0, st, L, j);
-    if (le != cudaSuccess) return le;
+  if (normalize) {
+    {
+      const cudaError_t le = tnx_launch(lanczos_normalize_kernel, dim3(nb), dim3(RT), 0, st, L, j);
+      if (le != cudaSuccess) return le;
+    }
+    tnx_note_launch(1);
   }
-  tnx_note_launch(1);
   return cudaGetLastError();
 }
 

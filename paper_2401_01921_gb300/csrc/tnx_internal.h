@@ -169,6 +169,12 @@ cudaError_t tnx_launch_match(const MatchArgs& a, cudaStream_t st);
 // one chunk per tile: (header, tile index, -2, 0).
 cudaError_t tnx_launch_copy(const CopyTask* tasks, const int4* chunks, int nchunks, double* const* slots,
                             cudaStream_t st);
+// The same relayout (plain and transposing tasks only) reading src instead of
+// each task's source slot, times *inv, plus vdst[i] = src[i] * *inv for
+// i < vn; nothing is done when state[1] (a Lanczos stop flag) is set.
+cudaError_t tnx_launch_copy_scaled(const CopyTask* tasks, const int4* chunks, int nchunks, double* const* slots,
+                                   const double* src, double* vdst, int64_t vn, const double* inv,
+                                   const int32_t* state, cudaStream_t st);
 // Fused skinny step (k_fused.cu): one CTA per tile of up to 128 rows (p, q),
 // p in [p0, p0 + tP), q in [q0, q0 + tQ), of one row block of A_g (the rows a
 // destination band of the step's relayout fills).  Column c < W (= ldK of the
@@ -237,5 +243,7 @@ struct LanczosDev {
 };
 cudaError_t tnx_launch_lanczos_init(const LanczosDev& L, const double* v0, cudaStream_t st);
 cudaError_t tnx_launch_lanczos_set_input(double** slot_ptr, const LanczosDev& L, int j, cudaStream_t st);
-cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, double** next_slot, cudaStream_t st);
+// normalize = false leaves out v_{j+1} = w / beta_{j+1} (1 / beta_{j+1} is in
+// scratch[3 * nmax + 3]) for the caller to fuse with its next relayout
+cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, double** next_slot, cudaStream_t st, bool normalize);
 cudaError_t tnx_launch_lanczos_finish(const LanczosDev& L, double* evec, cudaStream_t st);

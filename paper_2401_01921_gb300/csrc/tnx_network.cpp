@@ -1510,14 +1510,17 @@ void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB
 // vector).  Operands built only from fixed tensors keep their packed and sliced
 // forms from that previous apply, and a step whose two operands are both fixed
 // keeps its product: neither is recomputed.
-void enqueue_plan(Plan& p, cudaStream_t st, uint64_t fixed = 0) {
+// skip_slot >= 0: the relayout of that input tensor was done already (a Lanczos
+// step fuses it with its normalisation).
+void enqueue_plan(Plan& p, cudaStream_t st, uint64_t fixed = 0, int skip_slot = -1) {
   tnx_ctx* c = p.ctx;
   for (auto& s : p.steps) {
     const bool needA = (s.leavesA & ~fixed) != 0;
     const bool needB = (s.leavesB & ~fixed) != 0;
     if (!needA && !needB) continue;
-    // relayouts of A and B, unless a fused step does them
-    const bool copyA = needA && !s.skipA && !s.nftiles, copyB = needB && !s.skipB;
+    // relayouts of A and B, unless a fused step (or the caller) does them
+    const bool copyA = needA && !s.skipA && !s.nftiles && (skip_slot < 0 || s.A.slot != skip_slot);
+    const bool copyB = needB && !s.skipB && (skip_slot < 0 || s.B.slot != skip_slot);
     if (copyA || copyB) {
       ProfScope ps(c, st, TNX_KC_RELAYOUT,
                    16.0 * (double)((copyA ? s.copyA.total : 0) + (copyB ? s.copyB.total : 0)));
@@ -1897,6 +1900,27 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
   double* evp = evec ? evec->data : nullptr;
   // apply 0 prepares every operand; later applies only those fed by the vector
   const uint64_t fixed = ~((uint64_t)1 << slot);
+  // When exactly one relayout reads the vector (plain tasks only, no fused
+  // step gathering it), v_{j+1} = w / beta_{j+1} and that relayout of v_{j+1}
+  // are one launch at the end of step j, and apply j+1 skips the relayout.
+  const TaskList* vcopy = nullptr;
+  {
+    int readers = 0;
+    for (auto& s : p->steps) {
+      if (s.A.slot == slot) {
+        ++readers;
+        vcopy = s.nftiles ? nullptr : &s.copyA;
+      }
+      if (s.B.slot == slot) {
+        ++readers;
+        vcopy = &s.copyB;
+      }
+    }
+    if (readers != 1) vcopy = nullptr;
+    if (vcopy)
+      for (const CopyTask& t : vcopy->h)
+        if (t.tleg < -1 || t.src_slot != slot) vcopy = nullptr;
+  }
   auto body = [&] {
     {
       ProfScope ps(ctx, st, TNX_KC_VECTOR, 24.0 * (double)n);
@@ -1910,7 +1934,7 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
         const uint32_t prof = ctx->prof;
         if ((prof & TNX_PROF_LAST_APPLY) && j != nsteps - 1) ctx->prof = 0;
         try {
-          enqueue_plan(*p, st, j == 0 ? 0 : fixed);
+          enqueue_plan(*p, st, j == 0 ? 0 : fixed, (j > 0 && vcopy) ? slot : -1);
         } catch (...) {
           ctx->prof = prof;
           throw;
@@ -1920,7 +1944,10 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
       // bytes of one step: two Gram-Schmidt passes over j+1 vectors (dots
       // (j+1)n + n, update (j+1)n + 2n), norm folded in, scale (2n)
       ProfScope ps(ctx, st, TNX_KC_VECTOR, 8.0 * (double)n * (2 * (2.0 * (j + 1) + 3) + 2));
-      CUDA_CHECK(tnx_launch_lanczos_step(L, j, p->d_slots + slot, st));
+      CUDA_CHECK(tnx_launch_lanczos_step(L, j, p->d_slots + slot, st, vcopy == nullptr));
+      if (vcopy)
+        CUDA_CHECK(tnx_launch_copy_scaled(vcopy->d, vcopy->chunks, vcopy->nchunks, p->d_slots, L.w,
+                                          L.V + (int64_t)(j + 1) * n, n, L.scratch + 3 * L.nmax + 3, L.state, st));
     }
     ProfScope ps(ctx, st, TNX_KC_VECTOR, evp ? 8.0 * (double)n * (nsteps + 2) : 0.0);
     CUDA_CHECK(tnx_launch_lanczos_finish(L, evp, st));
