@@ -44,7 +44,7 @@ __device__ __forceinline__ int fdiv(int n, uint32_t magic, uint32_t shift) {
 // along the rows (consecutive rows are consecutive in the destination).
 template <bool SCALED>
 __device__ void copy_transpose(const CopyTask& t, int tile, double* const* __restrict__ slots, double (*sm)[33],
-                               const double* src_base, double scale) {
+                               const double* src_base, double scale, double* vdst_base) {
   const int r = t.rank, S = t.tleg;
   const int ncols = t.shape[S];
   const int nrows = (int)(t.nelem / ncols);
@@ -74,7 +74,13 @@ __device__ void copy_transpose(const CopyTask& t, int tile, double* const* __res
       int so, dof;
       bases(row, so, dof);
       const double x = src ? __ldg(src + so + c * t.sstride[S]) : 0.0;
-      sm[rr][lane] = SCALED ? x * scale : x;
+      if (SCALED) {
+        const double y = x * scale;
+        sm[rr][lane] = y;
+        if (vdst_base) vdst_base[t.src_off + so + c * t.sstride[S]] = y;
+      } else {
+        sm[rr][lane] = x;
+      }
     }
   }
   __syncthreads();
@@ -189,7 +195,7 @@ constexpr int EPT = 2;
 
 template <bool SCALED>
 __device__ __forceinline__ void copy_run(const CopyTask& t, const double* src, double* dst, int e0, int n,
-                                         double scale) {
+                                         double scale, double* vdst) {
   int so, dof;
   offsets(t, e0, so, dof);
   const int last = t.rank - 1;
@@ -197,12 +203,13 @@ __device__ __forceinline__ void copy_run(const CopyTask& t, const double* src, d
   int pos = e0 - fdiv(e0, t.magic[last], t.shift[last]) * ext;
   const int ss = t.sstride[last], ds = t.dstride[last];
   double v[EPT];
-  int d[EPT];
+  int d[EPT], sv[EPT];
 #pragma unroll
   for (int j = 0; j < EPT; ++j) {
     if (j < n) {
       v[j] = src ? __ldg(src + so) : 0.0;
       d[j] = dof;
+      sv[j] = so;
       if (++pos == ext) {
         pos = 0;
         offsets(t, e0 + j + 1, so, dof);
@@ -213,19 +220,31 @@ __device__ __forceinline__ void copy_run(const CopyTask& t, const double* src, d
     }
   }
 #pragma unroll
-  for (int j = 0; j < EPT; ++j)
-    if (j < n) dst[d[j]] = SCALED ? v[j] * scale : v[j];
+  for (int j = 0; j < EPT; ++j) {
+    if (j < n) {
+      if (SCALED) {
+        const double y = v[j] * scale;
+        dst[d[j]] = y;
+        if (vdst) vdst[sv[j]] = y;
+      } else {
+        dst[d[j]] = v[j];
+      }
+    }
+  }
 }
 
 // Scaled relayout (the normalising step of a Lanczos iteration, fused with the
 // next apply's relayout of the vector): every task reads src (instead of its
-// source slot) times *inv, and blocks past the chunks write vdst = src * *inv
-// over vn contiguous entries.  Nothing runs once the solve has stopped.
+// source slot) times *inv.  vdst = src * *inv is written by blocks past the
+// chunks over vn contiguous entries, or, when the tasks read every entry once
+// (full), by the tasks themselves from the product they store.  Nothing runs
+// once the solve has stopped.
 struct ScaleArgs {
   const double* src;
   double* vdst;
   int64_t vn;
   int nchunks;
+  int full;
   const double* inv;
   const int32_t* state;
 };
@@ -261,7 +280,8 @@ __global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ t
   CopyTask* st = (CopyTask*)raw;
   const int4 ch = chunks[blockIdx.x];
   if (ch.z == -1) {
-    copy_transpose<SCALED>(tasks[ch.x], ch.y, slots, (double (*)[33])raw, sa.src, scale);
+    copy_transpose<SCALED>(tasks[ch.x], ch.y, slots, (double (*)[33])raw, sa.src, scale,
+                           SCALED && sa.full ? sa.vdst : nullptr);
     return;
   }
   if (!SCALED && ch.z == -2) {
@@ -279,8 +299,9 @@ __global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ t
     const double* src = SCALED ? sa.src + t.src_off : (t.src_slot >= 0 ? slots[t.src_slot] + t.src_off : nullptr);
     double* dst = slots[t.dst_slot] + t.dst_off;
     const int end = ch.y + ch.w;
+    double* vd = SCALED && sa.full ? sa.vdst + t.src_off : nullptr;
     for (int e = ch.y + threadIdx.x * EPT; e < end; e += CT * EPT)
-      copy_run<SCALED>(t, src, dst, e, min(EPT, end - e), scale);
+      copy_run<SCALED>(t, src, dst, e, min(EPT, end - e), scale, vd);
     return;
   }
   // several small tasks
@@ -312,7 +333,13 @@ __global__ void __launch_bounds__(CT) copy_kernel(const CopyTask* __restrict__ t
     int so, dof;
     offsets(t, e - sstart[lo], so, dof);
     const double x = src ? __ldg(src + so) : 0.0;
-    slots[t.dst_slot][t.dst_off + dof] = SCALED ? x * scale : x;
+    if (SCALED) {
+      const double y = x * scale;
+      slots[t.dst_slot][t.dst_off + dof] = y;
+      if (sa.full) sa.vdst[t.src_off + so] = y;
+    } else {
+      slots[t.dst_slot][t.dst_off + dof] = x;
+    }
   }
 }
 
@@ -323,7 +350,7 @@ cudaError_t tnx_launch_copy(const CopyTask* tasks, const int4* chunks, int nchun
   if (nchunks <= 0) return cudaSuccess;
   {
     const cudaError_t le = tnx_launch(copy_kernel<false>, dim3(nchunks), dim3(CT), 0, st, tasks, chunks, slots,
-                                      ScaleArgs{nullptr, nullptr, 0, nchunks, nullptr, nullptr});
+                                      ScaleArgs{nullptr, nullptr, 0, nchunks, 0, nullptr, nullptr});
     if (le != cudaSuccess) return le;
   }
   tnx_note_launch(1);
@@ -331,15 +358,16 @@ cudaError_t tnx_launch_copy(const CopyTask* tasks, const int4* chunks, int nchun
 }
 
 cudaError_t tnx_launch_copy_scaled(const CopyTask* tasks, const int4* chunks, int nchunks, double* const* slots,
-                                   const double* src, double* vdst, int64_t vn, const double* inv,
+                                   const double* src, double* vdst, int64_t vn, int full, const double* inv,
                                    const int32_t* state, cudaStream_t st) {
-  if (nchunks < 0 || vn < 0) return cudaErrorInvalidValue;
-  const int64_t vb = std::min<int64_t>((vn + CT * 4 - 1) / (CT * 4), 1216);
-  const int64_t grid = (int64_t)nchunks + std::max<int64_t>(vb, 1);
+  if (nchunks < 0 || vn < 0 || (full && nchunks == 0 && vn > 0)) return cudaErrorInvalidValue;
+  const int64_t vb = full ? 0 : std::max<int64_t>(std::min<int64_t>((vn + CT * 4 - 1) / (CT * 4), 1216), 1);
+  const int64_t grid = (int64_t)nchunks + vb;
+  if (grid == 0) return cudaSuccess;
   if (grid > INT32_MAX) return cudaErrorInvalidValue;
   {
     const cudaError_t le = tnx_launch(copy_kernel<true>, dim3((unsigned)grid), dim3(CT), 0, st, tasks, chunks, slots,
-                                      ScaleArgs{src, vdst, vn, nchunks, inv, state});
+                                      ScaleArgs{src, vdst, vn, nchunks, full, inv, state});
     if (le != cudaSuccess) return le;
   }
   tnx_note_launch(1);

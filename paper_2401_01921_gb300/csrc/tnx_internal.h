@@ -171,9 +171,10 @@ cudaError_t tnx_launch_copy(const CopyTask* tasks, const int4* chunks, int nchun
                             cudaStream_t st);
 // The same relayout (plain and transposing tasks only) reading src instead of
 // each task's source slot, times *inv, plus vdst[i] = src[i] * *inv for
-// i < vn; nothing is done when state[1] (a Lanczos stop flag) is set.
+// i < vn (full != 0: the tasks read every such i exactly once and write it
+// themselves); nothing is done when state[1] (a Lanczos stop flag) is set.
 cudaError_t tnx_launch_copy_scaled(const CopyTask* tasks, const int4* chunks, int nchunks, double* const* slots,
-                                   const double* src, double* vdst, int64_t vn, const double* inv,
+                                   const double* src, double* vdst, int64_t vn, int full, const double* inv,
                                    const int32_t* state, cudaStream_t st);
 // Fused skinny step (k_fused.cu): one CTA per tile of up to 128 rows (p, q),
 // p in [p0, p0 + tP), q in [q0, q0 + tQ), of one row block of A_g (the rows a

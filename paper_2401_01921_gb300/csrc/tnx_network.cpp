@@ -1921,6 +1921,18 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
       for (const CopyTask& t : vcopy->h)
         if (t.tleg < -1 || t.src_slot != slot) vcopy = nullptr;
   }
+  // the relayout reads every entry of the vector once (each block of the vector
+  // is one task): it also writes v_{j+1} itself
+  int vfull = 0;
+  if (vcopy) {
+    int64_t cover = 0;
+    std::set<int64_t> starts;
+    for (const CopyTask& t : vcopy->h) {
+      cover += t.nelem;
+      starts.insert(t.src_off);
+    }
+    vfull = cover == n && starts.size() == vcopy->h.size() && vcopy->h.size() == (size_t)v0->nblk ? 1 : 0;
+  }
   auto body = [&] {
     {
       ProfScope ps(ctx, st, TNX_KC_VECTOR, 24.0 * (double)n);
@@ -1947,7 +1959,8 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
       CUDA_CHECK(tnx_launch_lanczos_step(L, j, p->d_slots + slot, st, vcopy == nullptr));
       if (vcopy)
         CUDA_CHECK(tnx_launch_copy_scaled(vcopy->d, vcopy->chunks, vcopy->nchunks, p->d_slots, L.w,
-                                          L.V + (int64_t)(j + 1) * n, n, L.scratch + 3 * L.nmax + 3, L.state, st));
+                                          L.V + (int64_t)(j + 1) * n, n, vfull, L.scratch + 3 * L.nmax + 3, L.state,
+                                          st));
     }
     ProfScope ps(ctx, st, TNX_KC_VECTOR, evp ? 8.0 * (double)n * (nsteps + 2) : 0.0);
     CUDA_CHECK(tnx_launch_lanczos_finish(L, evp, st));
