@@ -1,7 +1,7 @@
 // Fused skinny contraction step: gather, FP64 product, scatter in one kernel.
 //
 // A contraction whose charge groups all have K <= 16 (the MPO step of the
-// two-site H_eff, Sec. 8) is a small FP64 product between two relayouts: its
+// two-site H_eff, Sec. 11) is a small FP64 product between two relayouts: its
 // operand A is gathered from the previous step's output blocks into the packed
 // K-major matrix, and its output C is immediately relaid into the next step's
 // packed operand.  Here one CTA takes a tile of up to 128 rows (p, q) of one row
