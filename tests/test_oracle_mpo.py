@@ -48,7 +48,7 @@ def test_hubbard_two_site_closed_form():
     assert abs(e - (4 - math.sqrt(16 + 16)) / 2) < 1e-12
 
 
-@pytest.mark.parametrize("N", [2, 3])
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
 def test_hubbard_mpo_chain(N):
     m = I.hubbard_mpo()
     H = mpo_chain_dense(m.W, m.left_row, m.right_col, N)
