@@ -110,7 +110,9 @@ tnx_status tnx_sync(tnx_ctx* ctx);
  * (kinds[i] in {TNX_U1, TNX_ZN}, zn[i] = n for Z_n, ignored for U(1)), and nsec
  * sectors in creation order, sector k having charges qnums[k*nsym .. k*nsym+nsym)
  * and degeneracy degs[k] >= 1.  nsym = 0 with dir = TNX_BD_REG makes a plain
- * bond of dimension degs[0] (nsec must be 1).  Arrays are copied. */
+ * bond of dimension degs[0] (nsec must be 1).  Arrays are copied.  Charges
+ * beyond |q| = 2^24 and Z_n moduli above 2^24 give TNX_ERR_UNSUPPORTED (also
+ * for tnx_bond_combine results). */
 tnx_status tnx_bond_create(tnx_ctx* ctx, int dir, int nsym, const int* kinds, const int* zn,
                            int nsec, const int32_t* qnums, const int64_t* degs, tnx_bond** out);
 /* Total dimension (sum of degeneracies). */
@@ -314,9 +316,16 @@ tnx_status tnx_server_stats(tnx_server* s, int64_t* completed, int64_t* eviction
  *  degs (host): degeneracies of every sector of those legs, concatenated.
  *  kcharges (host): [K-leg sector][nsym] charges as they enter A's flux
  *      (negated on OUT legs, reduced mod n for Z_n).
- *  nA, rA, qA (dev, int32 [nA*rA]): A's blocks (sector indices, lexicographic;
- *      every entry must be a valid sector index of its leg: not checked);
- *  kposA[nk], fposA[nfa] (host): A's legs holding the K / free legs; same for B.
+ *  nA, rA, qA (dev, int32 [nA*rA]): A's blocks (sector indices, lexicographic);
+ *      the kernel checks every entry against its leg's sector count before it
+ *      writes anything and returns TNX_ERR_ARG (no table written) if one is
+ *      out of range;
+ *  kposA[nk], fposA[nfa] (host): A's legs holding the K / free legs; together
+ *      they must name each of A's rA legs exactly once (TNX_ERR_ARG otherwise);
+ *      same for B.
+ *  Limits (TNX_ERR_UNSUPPORTED beyond them): sector tuple spaces and the charge
+ *      space of the K legs at most 2^24 entries, |charge| <= 2^24, Z_n moduli
+ *      at most 2^22.
  *  gmax: capacity of the group outputs.
  *  Outputs (dev): ngroups[1], charges[gmax*nsym], mkn[gmax*3],
  *      amap[nA*3], bmap[nB*3] - the same conventions as tnx_network_step_tables.

@@ -39,6 +39,14 @@ __device__ int64_t tuple_id(const int32_t* q, const int32_t* pos, const MatchLeg
   return id;
 }
 
+__device__ bool sectors_in_range(const int32_t* q, const int32_t* pos, const MatchLeg* legs, int nl) {
+  for (int l = 0; l < nl; ++l) {
+    const int32_t v = q[pos[l]];
+    if (v < 0 || v >= legs[l].nsec) return false;
+  }
+  return true;
+}
+
 // charge index of K tuple `id` in the dense charge space (component 0 most significant)
 __device__ int64_t kcharge_index(const MatchArgs& a, int64_t id) {
   int32_t g[TNX_MAXSYM];
@@ -95,7 +103,9 @@ __device__ void group_scan(int64_t n, int G, GrpF grp, WF weight, int64_t* off, 
 __global__ void __launch_bounds__(T) match_kernel(MatchArgs a) {
   const int t = threadIdx.x;
   __shared__ int32_t s_G;
+  __shared__ int32_t s_bad;
   __shared__ int32_t s_scan[T];
+  if (t == 0) s_bad = 0;
 
   // phase 0: clear
   for (int64_t i = t; i < a.kspace; i += T) { a.kpres[i] = 0; a.kgroup[i] = -1; }
@@ -104,16 +114,31 @@ __global__ void __launch_bounds__(T) match_kernel(MatchArgs a) {
   for (int64_t i = t; i < a.cspace; i += T) a.cspres[i] = 0;
   __syncthreads();
 
-  // phase 1: which K tuples occur in A and in B
+  // phase 1: which K tuples occur in A and in B.  Every sector index of a
+  // block is checked against its leg first: an index out of range would
+  // address outside the tuple-space arrays, so such a block is skipped and
+  // the call reports status 3 without writing any table.
   for (int64_t b = t; b < a.nA; b += T) {
-    int64_t k = tuple_id(a.qA + b * a.rA, a.kposA, a.kleg, a.nk);
-    atomicOr(&a.kpres[k], 1);
+    const int32_t* q = a.qA + b * a.rA;
+    if (!sectors_in_range(q, a.kposA, a.kleg, a.nk) || !sectors_in_range(q, a.fposA, a.faleg, a.nfa)) {
+      s_bad = 1;
+      continue;
+    }
+    atomicOr(&a.kpres[tuple_id(q, a.kposA, a.kleg, a.nk)], 1);
   }
   for (int64_t b = t; b < a.nB; b += T) {
-    int64_t k = tuple_id(a.qB + b * a.rB, a.kposB, a.kleg, a.nk);
-    atomicOr(&a.kpres[k], 2);
+    const int32_t* q = a.qB + b * a.rB;
+    if (!sectors_in_range(q, a.kposB, a.kleg, a.nk) || !sectors_in_range(q, a.fposB, a.fbleg, a.nfb)) {
+      s_bad = 1;
+      continue;
+    }
+    atomicOr(&a.kpres[tuple_id(q, a.kposB, a.kleg, a.nk)], 2);
   }
   __syncthreads();
+  if (s_bad) {
+    if (t == 0) { *a.status = 3; *a.ngroups = 0; }
+    return;
+  }
 
   // phase 2: mark the charges of valid K tuples
   for (int64_t k = t; k < a.kspace; k += T)

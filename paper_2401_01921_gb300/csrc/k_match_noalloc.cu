@@ -46,6 +46,18 @@ void set_err(char* err, size_t len, const std::string& msg) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// pos K (nk entries) and pos F (nf entries) together name each of the r legs once
+bool legs_form_permutation(int r, int nk, const int32_t* posK, int nf, const int32_t* posF) {
+  if (nk + nf != r || (nk > 0 && !posK) || (nf > 0 && !posF)) return false;
+  bool seen[TNX_MAXR] = {};
+  for (int i = 0; i < nk + nf; ++i) {
+    const int32_t v = i < nk ? posK[i] : posF[i - nk];
+    if (v < 0 || v >= r || seen[v]) return false;
+    seen[v] = true;
+  }
+  return true;
+}
+
 }  // namespace
 
 extern "C" tnx_status tnx_match_tables_noalloc(void* stream, int nsym, const int32_t* zn, int nk, int nfa, int nfb,
@@ -63,27 +75,18 @@ extern "C" tnx_status tnx_match_tables_noalloc(void* stream, int nsym, const int
     set_err(err, errlen, "tnx_match_tables_noalloc: invalid argument");
     return TNX_ERR_ARG;
   }
-  // ---- set-up: device address of the scratch array, once per device
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    set_err(err, errlen, "tnx_match_tables_noalloc: no usable current CUDA device");
-    return TNX_ERR_CUDA;
+  // The K and free positions of each operand must name every one of its legs
+  // exactly once: the kernel reads each block's sector indices through them.
+  if (!legs_form_permutation(rA, nk, kposA, nfa, fposA) || !legs_form_permutation(rB, nk, kposB, nfb, fposB)) {
+    set_err(err, errlen,
+            "tnx_match_tables_noalloc: the K and free leg positions of an operand must be a permutation of its legs");
+    return TNX_ERR_ARG;
   }
-  unsigned char* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_dev[dev]) {
-      void* p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_match_scratch);
-      if (e != cudaSuccess || !p) {
-        set_err(err, errlen, std::string("tnx_match_tables_noalloc: cudaGetSymbolAddress failed: ") +
-                                 cudaGetErrorString(e));
-        return TNX_ERR_CUDA;
-      }
-      g_scratch_dev[dev] = p;
+  for (int c = 0; c < nsym; ++c)
+    if (zn[c] < 0 || zn[c] > (1 << 22)) {
+      set_err(err, errlen, "tnx_match_tables_noalloc: Z_n modulus outside [1, 2^22] (0 = U(1))");
+      return zn[c] < 0 ? TNX_ERR_ARG : TNX_ERR_UNSUPPORTED;
     }
-    scratch = (unsigned char*)g_scratch_dev[dev];
-  }
 
   // ---- sizes (same conventions as the planner's matching step)
   MatchArgs a;
@@ -123,6 +126,10 @@ extern "C" tnx_status tnx_match_tables_noalloc(void* stream, int nsym, const int
         int32_t mn = 0, mx = 0;
         for (int s = 0; s < nsec[l]; ++s) {
           const int32_t q = kcharges[(base + s) * nsym + c];
+          if (q > TNX_QMAX || q < -TNX_QMAX) {
+            set_err(err, errlen, "tnx_match_tables_noalloc: a K-leg charge magnitude above 2^24");
+            return TNX_ERR_UNSUPPORTED;
+          }
           if (s == 0 || q < mn) mn = q;
           if (s == 0 || q > mx) mx = q;
         }
@@ -138,6 +145,12 @@ extern "C" tnx_status tnx_match_tables_noalloc(void* stream, int nsym, const int
       a.crange[c] = (int32_t)(hi - lo + 1);
     }
     cspace *= a.crange[c];
+    // the same bound as the allocating planner: checked after every factor,
+    // so the product cannot wrap before the scratch layout is sized from it
+    if (cspace > (int64_t(1) << 24)) {
+      set_err(err, errlen, "tnx_match_tables_noalloc: charge space above 2^24");
+      return TNX_ERR_UNSUPPORTED;
+    }
   }
   a.kspace = kspace;
   a.faspace = faspace;
@@ -177,6 +190,28 @@ extern "C" tnx_status tnx_match_tables_noalloc(void* stream, int nsym, const int
                              " bytes (use the allocating network entry points instead)");
     return TNX_ERR_UNSUPPORTED;
   }
+  // ---- set-up: device address of the scratch array, once per device
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    set_err(err, errlen, "tnx_match_tables_noalloc: no usable current CUDA device");
+    return TNX_ERR_CUDA;
+  }
+  unsigned char* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_scratch_dev[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_match_scratch);
+      if (e != cudaSuccess || !p) {
+        set_err(err, errlen, std::string("tnx_match_tables_noalloc: cudaGetSymbolAddress failed: ") +
+                                 cudaGetErrorString(e));
+        return TNX_ERR_CUDA;
+      }
+      g_scratch_dev[dev] = p;
+    }
+    scratch = (unsigned char*)g_scratch_dev[dev];
+  }
+
   a.deg = (const int64_t*)(scratch + o_deg);
   a.kcharge = (const int32_t*)(scratch + o_kq);
   a.kpres = (int32_t*)(scratch + o_kpres);
@@ -217,6 +252,10 @@ extern "C" tnx_status tnx_match_tables_noalloc(void* stream, int nsym, const int
     set_err(err, errlen, "tnx_match_tables_noalloc: " + std::to_string(hs[0]) + " charge groups exceed gmax = " +
                              std::to_string(gmax));
     return TNX_ERR_UNSUPPORTED;
+  }
+  if (hs[1] == 3) {
+    set_err(err, errlen, "tnx_match_tables_noalloc: a block's sector index lies outside its leg (no table written)");
+    return TNX_ERR_ARG;
   }
   if (hs[1] != 0) {
     set_err(err, errlen, "tnx_match_tables_noalloc: a K-leg charge lies outside the given charges");

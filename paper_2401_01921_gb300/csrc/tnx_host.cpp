@@ -306,6 +306,7 @@ extern "C" tnx_status tnx_bond_create(tnx_ctx* ctx, int dir, int nsym, const int
     for (int c = 0; c < nsym; ++c) {
       if (kinds[c] != TNX_U1 && kinds[c] != TNX_ZN) { delete b; fail(TNX_ERR_ARG, "unknown symmetry kind"); }
       if (kinds[c] == TNX_ZN && (!zn || zn[c] < 2)) { delete b; fail(TNX_ERR_ARG, "Z_n needs n >= 2"); }
+      if (kinds[c] == TNX_ZN && zn[c] > TNX_QMAX) { delete b; fail(TNX_ERR_UNSUPPORTED, "Z_n modulus above 2^24"); }
       d.kinds.push_back(kinds[c]);
       d.zn.push_back(kinds[c] == TNX_ZN ? zn[c] : 0);
     }
@@ -315,6 +316,7 @@ extern "C" tnx_status tnx_bond_create(tnx_ctx* ctx, int dir, int nsym, const int
       for (int c = 0; c < nsym; ++c) {
         int32_t q = qnums[(size_t)s * nsym + c];
         if (d.kinds[c] == TNX_ZN) q = ((q % d.zn[c]) + d.zn[c]) % d.zn[c];
+        if (q > TNX_QMAX || q < -TNX_QMAX) { delete b; fail(TNX_ERR_UNSUPPORTED, "charge magnitude above 2^24"); }
         d.qn.push_back(q);
       }
     }
@@ -350,6 +352,7 @@ extern "C" tnx_status tnx_bond_combine(const tnx_bond* a, const tnx_bond* b, tnx
         for (int c = 0; c < x.nsym; ++c) {
           int32_t v = x.qn[(size_t)s * x.nsym + c] + y.qn[(size_t)t * y.nsym + c];
           if (x.kinds[c] == TNX_ZN) v = ((v % x.zn[c]) + x.zn[c]) % x.zn[c];
+          if (v > TNX_QMAX || v < -TNX_QMAX) fail(TNX_ERR_UNSUPPORTED, "combined charge magnitude above 2^24");
           q[c] = v;
         }
         acc[q] += x.deg[s] * y.deg[t];

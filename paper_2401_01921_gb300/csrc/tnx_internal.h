@@ -10,6 +10,7 @@
 
 #define TNX_MAXR 8          // maximum rank of a tensor or an intermediate
 #define TNX_MAXSYM 4        // maximum number of symmetries on a bond
+#define TNX_QMAX (1 << 24)  // largest |charge| of a bond sector (sums over <= 8 legs stay inside int32)
 
 // ---------------------------------------------------------------------------
 // Device task descriptors (plain data, built on the host at plan time).
@@ -120,7 +121,8 @@ struct MatchArgs {
   int64_t* mkn;             // gmax * 3
   int64_t* amap;            // nA * 3
   int64_t* bmap;            // nB * 3
-  int32_t* status;          // [1]: 0 ok, 1 too many groups
+  int32_t* status;          // [1]: 0 ok, 1 too many groups, 2 charge outside [clo, clo + crange),
+                            //      3 a block's sector index outside its leg (nothing written)
 };
 
 // Counts kernel launches made by this library (defined in tnx_host.cpp).

@@ -925,6 +925,7 @@ void run_match(Plan& p, StepPlan& s) {
   CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
   if (hs[1] == 1) fail(TNX_ERR_UNSUPPORTED, "more charge groups than the matching kernel supports");
   if (hs[1] == 2) fail(TNX_ERR_ARG, "internal: charge outside the planned range");
+  if (hs[1] == 3) fail(TNX_ERR_ARG, "internal: a block's sector index lies outside its leg");
   s.G = hs[0];
   s.charges.resize((size_t)s.G * nsym);
   s.mkn.resize((size_t)s.G * 3);

@@ -33,3 +33,16 @@ def rel_fro(lib_blocks: dict, ref: BlockTensor) -> float:
         d = b - (a if a is not None else 0.0)
         num += float(np.sum(d * d))
     return np.sqrt(num / den) if den > 0 else np.sqrt(num)
+
+
+def max_block_rel(lib_blocks: dict, ref: BlockTensor) -> float:
+    """Largest ||lib_b - ref_b||_F / ||ref_b||_F over the stored blocks b with ref_b != 0."""
+    worst = 0.0
+    for k, b in ref.blocks.items():
+        n2 = float(np.sum(b * b))
+        if n2 == 0.0:
+            continue
+        a = lib_blocks.get(k)
+        d = b - (a if a is not None else 0.0)
+        worst = max(worst, np.sqrt(float(np.sum(d * d)) / n2))
+    return worst

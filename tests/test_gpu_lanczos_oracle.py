@@ -1,0 +1,103 @@
+"""GPU parity of the configurations the benchmark times, against the CPU oracle.
+
+- The split-precision (BF16 and FP16 slices) 20-step Lanczos solve at chi = 512
+  in the contraction order the benchmark uses, (L,((psi,R),(W1,W2))), against
+  the oracle's Lanczos in the same order (Sec. 9.3): eigenvalue to 1e-10
+  relative, Ritz vector to 1e-8, and its residual ||H x - lambda x|| computed
+  by the oracle's own apply.
+- The U(1) x U(1) Hubbard Lanczos solve at chi = 128 (FP64 and split BF16).
+- A batch whose instances span the batched configuration's chi range
+  [64, 1024] under the autotuned persistent split-GEMM grid: every instance
+  against the oracle.
+"""
+import numpy as np
+import pytest
+
+import tnx_inputs as I
+from oracle import heff as oheff
+from oracle.lanczos import lanczos as oracle_lanczos
+
+from gpu_harness import lib_heff, oracle_heff, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+BENCH_ORDER = "(L,((psi,R),(W1,W2)))"
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2401_01921_gb300 as tnx
+    from paper_2401_01921_gb300 import build
+    build.build()
+    return tnx.Context(0)
+
+
+def _oracle_solve(wl, order, nsteps):
+    onet, OT = oracle_heff(wl, symmetric=True, order=order)
+    op = oheff.flat_apply(onet, OT["psi"])
+    lam, x, alpha, beta, k = oracle_lanczos(op, OT["psi"].flat(), nsteps)
+    return lam, x, k, op
+
+
+def _check_solve(ctx, wl, prec, order, nsteps, lam_tol, vec_tol):
+    import paper_2401_01921_gb300 as tnx
+    net, T, B = lib_heff(ctx, wl, symmetric=True, order=order, prec=prec)
+    if order:
+        assert net.get_order() == order
+    evec = tnx.Tensor(ctx, B["psi"])
+    lam, k = tnx.lanczos(net, "psi", T["psi"], nsteps, evec)
+    olam, ox, ok, op = _oracle_solve(wl, order, nsteps)
+    assert k == ok
+    x = evec.download()
+    rel = abs(lam - olam) / abs(olam)
+    dvec = float(np.linalg.norm(x - ox))
+    res_lib = float(np.linalg.norm(op(x) - olam * x))
+    res_orc = float(np.linalg.norm(op(ox) - olam * ox))
+    print(f"{wl.name} {prec}: lambda {lam:.15f} oracle {olam:.15f} rel {rel:.2e}; |x - x_oracle| {dvec:.2e}; "
+          f"residual lib {res_lib:.3e} oracle {res_orc:.3e}")
+    assert rel <= lam_tol, rel
+    assert dvec <= vec_tol, dvec
+    # the library's Ritz vector is as good an eigenvector approximation as the oracle's
+    assert res_lib <= res_orc * (1 + 1e-6) + vec_tol * abs(olam), (res_lib, res_orc)
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "split_f16"])
+def test_split_lanczos_chi512_bench_order_vs_oracle(ctx, prec):
+    _check_solve(ctx, I.heisenberg_workload(512, 20), prec, BENCH_ORDER, 20, 1e-10, 1e-8)
+
+
+@pytest.mark.parametrize("prec", ["f64", "split_bf16"])
+def test_hubbard_lanczos_chi128_vs_oracle(ctx, prec):
+    _check_solve(ctx, I.hubbard_workload(128), prec, None, 20, 1e-12 if prec == "f64" else 1e-10, 1e-8)
+
+
+def test_split_lanczos_chi2048_sector_scaled_vs_oracle(ctx):
+    """The benchmark's own solve: chi = 2048, sector-scaled, split BF16, block-sparse search order."""
+    _check_solve(ctx, I.heisenberg_workload(2048, 40, sector_scale=True), "split_bf16", BENCH_ORDER, 20, 1e-10, 1e-8)
+
+
+def test_batch_spanning_chi64_to_1024_vs_oracle(ctx):
+    """Eight Hubbard instances from chi = 64 to 1024 in one batch (split BF16, autotuned persistent
+    grid): each instance's output against the oracle (relative Frobenius <= 1e-10) and against its own
+    single launch (bit-identical)."""
+    import paper_2401_01921_gb300 as tnx
+    order = "(L,(((psi,R),W2),W1))"
+    chis = [64, 96, 160, 256, 384, 600, 800, 1024]
+    wls = [I.hubbard_workload(c, seed_base=1000 + 4 * i) for i, c in enumerate(chis)]
+    built = [lib_heff(ctx, wl, prec="split_bf16", order=order) for wl in wls]
+    outs = [tnx.Tensor(ctx, B["psi"]) for _, _, B in built]
+    batch = tnx.Batch(ctx, [n for n, _, _ in built])
+    choice = batch.autotune(outs)
+    assert choice in (0, 152, 304, 456)
+    batch.launch_into(outs)
+    errs = []
+    for (net, T, B), o, wl in zip(built, outs, wls):
+        onet, _ = oracle_heff(wl, order=order)
+        err = rel_fro(o.block_dict(), onet.launch())
+        errs.append(err)
+        assert err <= 1e-10, (wl.chi, err)
+    print("batch chi64..1024 split rel errors:", ", ".join(f"{c}:{e:.2e}" for c, e in zip(chis, errs)),
+          "grid", choice)
+    for (net, T, B), o in zip(built, outs):
+        single = net.launch(B["psi"]).download()
+        assert np.array_equal(o.download(), single)

@@ -10,7 +10,7 @@ import pytest
 
 import tnx_inputs as I
 
-from gpu_harness import lib_heff, oracle_heff, rel_fro
+from gpu_harness import lib_heff, max_block_rel, oracle_heff, rel_fro
 
 pytestmark = pytest.mark.gpu
 
@@ -97,13 +97,22 @@ def test_split_lanczos(ctx):
     assert abs(lam["f64"] - lam["split_bf16"]) <= 1e-10 * abs(lam["f64"])
 
 
+# Per precision: bound on the relative Frobenius error over all stored elements, and on the largest
+# relative error of a single block (the 10^U(-3,0) sector scaling makes some blocks 1000x smaller than
+# others that share a row or column scale of the split products, which costs those blocks bits).
+SWEEP_BOUNDS = {"f64": (1e-12, 1e-12), "split_bf16": (TOL_SPLIT, 1e-8), "split_f16": (TOL_SPLIT, 1e-8),
+                "f32": (1e-5, 1e-3)}
+
+
 def test_precision_sweep_chi2048(ctx):
     """The C3 sweep: chi=2048 U(1) apply with per-sector 10^U(-3,0) scaling, every precision the
-    library offers against the FP64 oracle (errors printed; FP64 <= 1e-12, split <= 1e-10)."""
-    bounds = {"f64": 1e-12, "split_bf16": TOL_SPLIT, "split_f16": TOL_SPLIT, "f32": 1e-5}
+    library offers against the FP64 oracle (errors printed; global and worst-block bounds above)."""
     ref = reference("u1_chi2048_scaled")
-    for prec, tol in bounds.items():
+    for prec, (tol, tol_blk) in SWEEP_BOUNDS.items():
         net, T, B = lib_heff(ctx, WORKLOADS["u1_chi2048_scaled"](), prec=prec)
-        err = rel_fro(net.launch(B["psi"]).block_dict(), ref)
-        print(f"u1_chi2048_scaled {prec}: rel err {err:.3e}")
+        got = net.launch(B["psi"]).block_dict()
+        err = rel_fro(got, ref)
+        blk = max_block_rel(got, ref)
+        print(f"u1_chi2048_scaled {prec}: rel err {err:.3e}, worst block {blk:.3e}")
         assert err <= tol, (prec, err)
+        assert blk <= tol_blk, (prec, blk)
