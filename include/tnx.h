@@ -223,7 +223,8 @@ tnx_status tnx_network_step_tables(tnx_network* net, int step, int32_t* charges,
  * as the vector, is the linear operator (its TOUT bonds must equal the
  * vector's bonds).  Starting from v0, runs at most nsteps Lanczos steps with
  * full reorthogonalisation (classical Gram-Schmidt, twice), stopping early if
- * the new off-diagonal falls below 1e-14 * max|alpha|; returns the lowest
+ * the new off-diagonal falls below 1e-14 * max(|alpha_i|, beta_i) over the steps so
+ * far; returns the lowest
  * eigenvalue of the tridiagonal matrix (Sturm bisection, FP64) in *eval and,
  * if evec != NULL, the Ritz vector (unit norm, largest-|y| coefficient
  * positive) in evec (same bonds as v0).  *nmatvec (may be NULL) gets the number

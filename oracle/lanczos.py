@@ -10,7 +10,7 @@ Parlett, The Symmetric Eigenvalue Problem, Ch. 13):
 1. v_0 = psi / ||psi||, beta_0 = 0.
 2. for j = 0..K-1: w = H v_j; alpha_j = <v_j, w>; w -= alpha_j v_j + beta_j v_{j-1};
    full reorthogonalisation against v_0..v_j by classical Gram-Schmidt, done
-   twice; beta_{j+1} = ||w||; stop if beta_{j+1} < 1e-14 * max|alpha|;
+   twice; beta_{j+1} = ||w||; stop if beta_{j+1} < 1e-14 * max(|alpha_i|, beta_i);
    v_{j+1} = w / beta_{j+1}.
 3. the lowest eigenvalue of the tridiagonal T (diagonal alpha, off-diagonal
    beta) by Sturm-sequence bisection (count of negative pivots of T - x I)
@@ -100,7 +100,10 @@ def lanczos(apply, v0: np.ndarray, nsteps: int, stop_rel: float = 1e-14):
             for cu, u in zip(c, V):
                 w = w - cu * u
         b = float(np.linalg.norm(w))
-        if j == nsteps - 1 or b < stop_rel * max(abs(x) for x in alpha):
+        # negligible against the scale of T seen so far (max |alpha| and max beta): with
+        # alpha identically zero, as for the XX chain from a Neel state, max |alpha| alone
+        # would never stop an exhausted Krylov space
+        if j == nsteps - 1 or b < stop_rel * max(max(abs(x) for x in alpha), max(beta)):
             break
         beta.append(b)
         V.append(w / b)

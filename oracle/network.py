@@ -55,7 +55,7 @@ def parse_spec(text: str):
     lines = text.replace(";", ",").split("\n") if isinstance(text, str) else list(text)
     for raw in lines:
         line = raw.strip()
-        if not line:
+        if not line or line.startswith("#"):      # comment lines, as in the Sec. 8.4 network file
             continue
         if ":" not in line:
             raise NetworkError(f"line without ':' : {line!r}")
@@ -67,7 +67,7 @@ def parse_spec(text: str):
         elif key == "ORDER":
             order = rest.replace(" ", "")
         else:
-            if key in labels or not re.fullmatch(r"[A-Za-z0-9_\-\.']+", key):
+            if key in labels or not re.fullmatch(r"[A-Za-z0-9_\-\.'*]+", key):
                 raise NetworkError(f"bad or duplicate tensor name {key!r}")
             labs = [x.strip() for x in rest.split(",") if x.strip()]
             if len(set(labs)) != len(labs):
@@ -105,7 +105,7 @@ def parse_order(order: str, names):
                 raise NetworkError("expected ')'")
             pos += 1
             return (left, right)
-        m = re.match(r"[A-Za-z0-9_\-\.']+", order[pos:])
+        m = re.match(r"[A-Za-z0-9_\-\.'*]+", order[pos:])
         if not m:
             raise NetworkError("expected a tensor name")
         pos += m.end()

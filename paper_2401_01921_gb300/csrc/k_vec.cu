@@ -8,7 +8,8 @@
 //   vector: full reorthogonalisation; the first pass's coefficient of v_j is
 //   alpha_j = <v_j, w>, and subtracting all coefficients subsumes the
 //   three-term recurrence);
-//   beta_{j+1} = ||w||; stop if beta_{j+1} < 1e-14 max|alpha|; v_{j+1} = w / beta_{j+1};
+//   beta_{j+1} = ||w||; stop if beta_{j+1} < 1e-14 max(|alpha_i|, beta_i; i <= j);
+//   v_{j+1} = w / beta_{j+1};
 // then Sturm bisection on the tridiagonal T and inverse iteration for its
 // eigenvector, and the Ritz vector V y.
 // Reductions are deterministic: per-block partial sums with a fixed grid and
@@ -297,7 +298,8 @@ __global__ void __launch_bounds__(RT) lanczos_beta_decide_kernel(LanczosDev L, i
   for (int b = threadIdx.x; b < nb; b += RT) acc += L.partial[b];
   if (threadIdx.x < 32) {
     double amax = 0.0;
-    for (int i = threadIdx.x; i <= j; i += 32) amax = fmax(amax, fabs(L.alpha[i]));
+    // the scale of T seen so far: max |alpha_i| and max beta_i (i <= j; beta_0 = 0)
+    for (int i = threadIdx.x; i <= j; i += 32) amax = fmax(amax, fmax(fabs(L.alpha[i]), L.beta[i]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     if (threadIdx.x == 0) s_amax = amax;

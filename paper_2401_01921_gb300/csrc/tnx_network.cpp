@@ -47,7 +47,7 @@ std::string trim(const std::string& s) {
 bool valid_name(const std::string& s) {
   if (s.empty()) return false;
   for (char c : s)
-    if (!(isalnum((unsigned char)c) || c == '_' || c == '-' || c == '.' || c == '\'')) return false;
+    if (!(isalnum((unsigned char)c) || c == '_' || c == '-' || c == '.' || c == '\'' || c == '*')) return false;
   return true;
 }
 
@@ -1648,7 +1648,7 @@ extern "C" tnx_status tnx_network_create(tnx_ctx* ctx, const char* spec, tnx_net
       if (p1 == std::string::npos) p1 = text.size();
       line = trim(text.substr(p0, p1 - p0));
       p0 = p1 + 1;
-      if (line.empty()) continue;
+      if (line.empty() || line[0] == '#') continue;   // comment lines (Sec. 8.4 network file)
       size_t c = line.find(':');
       if (c == std::string::npos) fail(TNX_ERR_NETWORK, "line without ':' : " + line);
       std::string key = trim(line.substr(0, c)), rest = trim(line.substr(c + 1));

@@ -203,3 +203,39 @@ def test_sparse_order_beats_dense_order_on_heff():
         flops[order] = sum(r["flops"] for r in rec)
     assert flops["(L,((psi,R),(W1,W2)))"] < flops["(L,(((psi,R),W2),W1))"]
     assert flops["(L,((psi,R),(W1,W2)))"] <= cost
+
+
+# Sec. 8.4 listing "code:peps_network": the 11-tensor PEPS expectation value (comment line and
+# names with '*' as printed).
+PEPS = """#network file peps_exp_val.net
+b0:  b0-b5,  b0-b1,   b0-t0,  b0-t0*
+b1:  b0-b1,  b1-b2,   b1-t0,  b1-t0*
+b2:  b1-b2,  b2-b3,   b2-t0,  b2-t0*
+b3:  b2-b3,  b3-b4,   b3-t1,  b3-t1*
+b4:  b3-b4,  b4-b5,   b4-t1,  b4-t1*
+b5:  b4-b5,  b0-b5,   b5-t1,  b5-t1*
+t0:  op-t0,  t0-t1,   b0-t0,  b1-t0,  b2-t0
+t0*: op-t0*, t0*-t1*, b0-t0*, b1-t0*, b2-t0*
+t1:  op-t1,  t0-t1,   b3-t1,  b4-t1,  b5-t1
+t1*: op-t1*, t0*-t1*, b3-t1*, b4-t1*, b5-t1*
+op:  op-t0,  op-t0*,  op-t1,  op-t1*
+TOUT:
+ORDER:
+"""
+
+
+def test_peps_network_of_ones_counts_its_edges():
+    """All-ones tensors of dimension 2 (the listing "code:peps_contraction"): the scalar is
+    2^(number of distinct labels), every label being summed over exactly once."""
+    from oracle.symtensor import BlockTensor, Bond
+    names, labels, tout, order = parse_spec(PEPS)
+    assert len(names) == 11 and tout == []
+    edges = {l for n in names for l in labels[n]}
+    assert len(edges) == 24
+    net = Network(PEPS)
+    for n in names:
+        bonds = [Bond.make(0, [((), 2)]) for _ in labels[n]]
+        net.put(n, BlockTensor(bonds, {tuple(0 for _ in bonds): np.ones((2,) * len(bonds))}))
+    net.set_order(True)
+    out = net.launch()
+    assert float(out.blocks[()].reshape(-1)[0]) == 2.0 ** 24

@@ -230,6 +230,37 @@ def heisenberg_mpo(J: float = 1.0) -> MPO:
     return MPO(W=W, channel_charge=charges, bond_sectors=secs, channel_pos=pos, left_row=4, right_col=0)
 
 
+def xx_mpo() -> MPO:
+    """Lower-triangular D=4 MPO of the XX chain H = sum (Sx Sx + Sy Sy) (the paper's DMRG
+    benchmark model, M_D = 4): W[0,0]=I, W[1,0]=S+, W[2,0]=S-, W[3,1]=S-/2, W[3,2]=S+/2,
+    W[3,3]=I; the left edge takes row 3, the right edge column 0.  Grouped MPO bond
+    {0:2, +2:1, -2:1} (2Sz units), channel charges as in ``heisenberg_mpo``."""
+    I = np.eye(2)
+    Sp = np.array([[0.0, 1.0], [0.0, 0.0]])
+    Sm = Sp.T.copy()
+    W = np.zeros((4, 2, 2, 4))
+    W[0, :, :, 0] = I
+    W[1, :, :, 0] = Sp
+    W[2, :, :, 0] = Sm
+    W[3, :, :, 1] = 0.5 * Sm
+    W[3, :, :, 2] = 0.5 * Sp
+    W[3, :, :, 3] = I
+    charges = [(0,), (-2,), (2,), (0,)]
+    want = [(0,), (2,), (-2,)]
+    degs = {q: charges.count(q) for q in want}
+    secs = [(q, degs[q]) for q in want]
+    start, off = {}, 0
+    for q, d in secs:
+        start[q] = off
+        off += d
+    used = {q: 0 for q in want}
+    pos = []
+    for q in charges:
+        pos.append(start[q] + used[q])
+        used[q] += 1
+    return MPO(W=W, channel_charge=charges, bond_sectors=secs, channel_pos=pos, left_row=3, right_col=0)
+
+
 def hubbard_local_ops():
     """Local fermion operators on |0>,|up>,|dn>,|updn> with |updn> = c+_up c+_dn |0>."""
     cup_dag = np.zeros((4, 4))
