@@ -122,6 +122,8 @@ tnx_status tnx_bond_dim(const tnx_bond* b, int64_t* dim);
 tnx_status tnx_bond_combine(const tnx_bond* a, const tnx_bond* b, tnx_bond** out);
 /* Number of sectors, and (optional, may be NULL) their charges and degeneracies. */
 tnx_status tnx_bond_sectors(const tnx_bond* b, int* nsec, int32_t* qnums, int64_t* degs);
+/* Direction and symmetries (any pointer may be NULL; kinds / zn hold nsym entries). */
+tnx_status tnx_bond_info(const tnx_bond* b, int* dir, int* nsym, int* kinds, int* zn);
 tnx_status tnx_bond_destroy(tnx_bond* b);
 
 /* ---------------------------------------------------------------- tensors */
@@ -142,6 +144,8 @@ tnx_status tnx_tensor_block_info(const tnx_tensor* t, int64_t blk, int32_t* qn_i
                                  int64_t* offset);
 /* All blocks at once: qn_idx[nblk*rank], shape[nblk*rank], offset[nblk] (any may be NULL). */
 tnx_status tnx_tensor_blocks(const tnx_tensor* t, int32_t* qn_idx, int64_t* shape, int64_t* offset);
+/* A new bond handle (caller owns) equal to leg `leg` of t. */
+tnx_status tnx_tensor_bond(const tnx_tensor* t, int leg, tnx_bond** out);
 /* Borrowed device pointer to the element buffer and its element count. */
 tnx_status tnx_tensor_data(tnx_tensor* t, double** dev_ptr, int64_t* nelem);
 /* Copy host data into the block with sector indices qn_idx (n = its size);
@@ -159,6 +163,36 @@ tnx_status tnx_tensor_scale(tnx_tensor* t, double alpha);
 tnx_status tnx_tensor_add_scalar(tnx_tensor* t, double alpha);
 /* Two-norm over the stored elements (FP64, device reduction).  Synchronous. */
 tnx_status tnx_tensor_norm(const tnx_tensor* t, double* out);
+/* Sec. 6.4 Dagger: a new tensor (caller owns) with every bond redirected
+ * (IN <-> OUT; REGULAR bonds stay) and the same blocks and data (the elements
+ * are real, so complex conjugation changes nothing).  Asynchronous copy on
+ * the context stream. */
+tnx_status tnx_tensor_dagger(const tnx_tensor* t, tnx_tensor** out);
+
+/* ---------------------------------------------------------- decomposition */
+
+/* Sec. 9.1 / 9.2 Svd and Svd_truncate of a block-sparse tensor.  The first
+ * `rowrank` legs are the row legs (1 <= rowrank < rank); the matrix form has
+ * one dense block per total charge g of the row legs (blocks of S in
+ * ascending order of g).  Every block gets a full SVD on the device (one-sided
+ * Jacobi, FP64); then the singular values of all blocks are sorted together
+ * and the largest keepdim are kept (keepdim <= 0: no limit), values below err
+ * are dropped (err <= 0: none; values are not normalised), and
+ * min_blockdim[i] (nmin = number of blocks of S, or min_blockdim = NULL)
+ * values of block i are kept even if the other rules drop them; those count
+ * towards keepdim.  Equal values are ranked by block, then position.
+ * Outputs (new tensors, caller owns): U with the row legs and a new OUT leg
+ * whose sectors are the kept charges (ascending) with the kept counts; S, a
+ * diagonal [IN, OUT] tensor over the new leg (may be NULL unless absorb == 0);
+ * Vdag with the new IN leg followed by the column legs.  absorb = 1 returns
+ * S * Vdag in Vdag, absorb = 2 returns U * S in U.  trunc_err (may be NULL):
+ * the largest dropped value (0 if none), as return_err = 1; discarded (may be
+ * NULL): the sum of the dropped values squared.  Plain (REGULAR) tensors give
+ * a REGULAR new leg.  TNX_ERR_ARG if nothing is kept or the arguments are
+ * inconsistent.  Synchronous. */
+tnx_status tnx_svd_truncate(tnx_tensor* t, int rowrank, int64_t keepdim, double err, const int64_t* min_blockdim,
+                            int nmin, int absorb, tnx_tensor** U, tnx_tensor** S, tnx_tensor** Vdag,
+                            double* trunc_err, double* discarded);
 
 /* --------------------------------------------------------------- networks */
 
@@ -232,6 +266,34 @@ tnx_status tnx_network_step_tables(tnx_network* net, int step, int32_t* charges,
  * the apply uses the network's precision.  Synchronous. */
 tnx_status tnx_lanczos(tnx_network* net, const char* vec_slot, tnx_tensor* v0, int nsteps,
                        double* eval, tnx_tensor* evec, int* nmatvec);
+
+/* ------------------------------------------------------------------- DMRG */
+
+/* The two-site DMRG sweep of Sec. 11 (the benchmark around Fig. "Hpsi_fig"),
+ * built from the calls above: per bond, the two-site wavefunction A_i A_{i+1}
+ * (a network launch), its lowest eigenvector under H_eff = (L, W, W, R) by
+ * tnx_lanczos, the split by tnx_svd_truncate (S absorbed towards the sweep
+ * direction), and the environment update L.A.W.A^dagger or A.W.R.A^dagger (a
+ * network launch).  W is the uniform MPO [wL IN, s' IN, s OUT, wR OUT] (copied;
+ * REGULAR legs for a plain chain); left_w / right_w are the dense MPO indices
+ * the chain's left / right edges select; states[nsites] is the initial product
+ * state (dense indices into the physical leg), which also fixes the total
+ * charge.  MPS tensors are A_i[a IN, s IN, b OUT].  No counterpart as a call in
+ * the paper (its sweep is a user-guide example). */
+typedef struct tnx_dmrg tnx_dmrg;
+tnx_status tnx_dmrg_create(tnx_ctx* ctx, int nsites, const tnx_tensor* W, int left_w, int right_w,
+                           const int32_t* states, tnx_dmrg** out);
+tnx_status tnx_dmrg_destroy(tnx_dmrg* d);
+/* One sweep (left to right, then right to left) keeping at most maxdim values
+ * per bond and dropping values below cutoff, lanczos_steps steps per update,
+ * H_eff products in precision prec (TNX_PREC_*).  Outputs (any may be NULL):
+ * the last Lanczos eigenvalue, the largest dropped singular value, the largest
+ * bond dimension, and host milliseconds per phase [two-site wavefunction and
+ * Lanczos, SVD, environments, whole sweep].  Synchronous. */
+tnx_status tnx_dmrg_sweep(tnx_dmrg* d, int64_t maxdim, double cutoff, int lanczos_steps, int prec, double* energy,
+                          double* max_trunc_err, int64_t* max_bond, double* phase_ms);
+/* A copy of the MPS tensor of site `site` (caller owns). */
+tnx_status tnx_dmrg_tensor(const tnx_dmrg* d, int site, tnx_tensor** out);
 
 /* ---------------------------------------------------------------- batches */
 

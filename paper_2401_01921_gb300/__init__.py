@@ -60,6 +60,8 @@ _SIGS = {
     "tnx_bond_combine": (C.c_int, [_p, _p, C.POINTER(_p)]),
     "tnx_bond_sectors": (C.c_int, [_p, C.POINTER(C.c_int), _i32p, _i64p]),
     "tnx_bond_destroy": (C.c_int, [_p]),
+    "tnx_bond_info": (C.c_int, [_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "tnx_tensor_bond": (C.c_int, [_p, C.c_int, C.POINTER(_p)]),
     "tnx_tensor_create": (C.c_int, [_p, C.c_int, C.POINTER(_p), C.POINTER(_p)]),
     "tnx_tensor_destroy": (C.c_int, [_p]),
     "tnx_tensor_rank": (C.c_int, [_p, C.POINTER(C.c_int)]),
@@ -74,6 +76,9 @@ _SIGS = {
     "tnx_tensor_scale": (C.c_int, [_p, C.c_double]),
     "tnx_tensor_add_scalar": (C.c_int, [_p, C.c_double]),
     "tnx_tensor_norm": (C.c_int, [_p, C.POINTER(C.c_double)]),
+    "tnx_tensor_dagger": (C.c_int, [_p, C.POINTER(_p)]),
+    "tnx_svd_truncate": (C.c_int, [_p, C.c_int, C.c_int64, C.c_double, _i64p, C.c_int, C.c_int, C.POINTER(_p),
+                                   C.POINTER(_p), C.POINTER(_p), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "tnx_network_create": (C.c_int, [_p, C.c_char_p, C.POINTER(_p)]),
     "tnx_network_destroy": (C.c_int, [_p]),
     "tnx_network_put": (C.c_int, [_p, C.c_char_p, _p, C.c_int, C.POINTER(C.c_char_p)]),
@@ -87,6 +92,11 @@ _SIGS = {
     "tnx_network_step_sizes": (C.c_int, [_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _i64p, _i64p]),
     "tnx_network_step_tables": (C.c_int, [_p, C.c_int, _i32p, _i64p, _i64p, _i64p]),
     "tnx_lanczos": (C.c_int, [_p, C.c_char_p, _p, C.c_int, C.POINTER(C.c_double), _p, C.POINTER(C.c_int)]),
+    "tnx_dmrg_create": (C.c_int, [_p, C.c_int, _p, C.c_int, C.c_int, _i32p, C.POINTER(_p)]),
+    "tnx_dmrg_destroy": (C.c_int, [_p]),
+    "tnx_dmrg_sweep": (C.c_int, [_p, C.c_int64, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), _i64p, C.POINTER(C.c_double)]),
+    "tnx_dmrg_tensor": (C.c_int, [_p, C.c_int, C.POINTER(_p)]),
     "tnx_batch_create": (C.c_int, [_p, C.c_int, C.POINTER(_p), C.POINTER(_p)]),
     "tnx_batch_destroy": (C.c_int, [_p]),
     "tnx_batch_launch_into": (C.c_int, [_p, C.POINTER(_p)]),
@@ -229,6 +239,27 @@ class Bond:
         self.sectors = [(tuple(int(c) for c in qn), int(dg)) for qn, dg in sectors]
         self.nsym = nsym
 
+    @classmethod
+    def from_handle(cls, ctx: Context, h) -> "Bond":
+        """Wraps a bond handle the library created (the wrapper destroys it)."""
+        b = cls.__new__(cls)
+        b.ctx = ctx
+        b.h = h
+        d, ns = C.c_int(), C.c_int()
+        ctx.check(lib().tnx_bond_info(h, C.byref(d), C.byref(ns), None, None))
+        kinds = np.zeros(max(ns.value, 1), dtype=np.int32)
+        zn = np.zeros(max(ns.value, 1), dtype=np.int32)
+        ctx.check(lib().tnx_bond_info(h, None, None, _ptr(kinds, C.c_int), _ptr(zn, C.c_int)))
+        nsec = C.c_int()
+        ctx.check(lib().tnx_bond_sectors(h, C.byref(nsec), None, None))
+        q = np.zeros(max(nsec.value * ns.value, 1), dtype=np.int32)
+        dg = np.zeros(nsec.value, dtype=np.int64)
+        ctx.check(lib().tnx_bond_sectors(h, C.byref(nsec), _ptr(q, C.c_int32), _ptr(dg, C.c_int64)))
+        b.dir = d.value
+        b.nsym = ns.value
+        b.sectors = [(tuple(int(x) for x in q[i * ns.value:(i + 1) * ns.value]), int(dg[i])) for i in range(nsec.value)]
+        return b
+
     @property
     def dim(self) -> int:
         return sum(d for _, d in self.sectors)
@@ -265,6 +296,24 @@ class Tensor:
         ctx.check(lib().tnx_tensor_data(self.h, C.byref(p), C.byref(ne)))
         self.data_ptr = p.value
         self.nelem = ne.value
+
+    @classmethod
+    def from_handle(cls, ctx: Context, h) -> "Tensor":
+        """Wraps a tensor handle the library created (its bonds are read back)."""
+        r = C.c_int()
+        ctx.check(lib().tnx_tensor_rank(h, C.byref(r)))
+        bonds = []
+        for leg in range(r.value):
+            bh = C.c_void_p()
+            ctx.check(lib().tnx_tensor_bond(h, leg, C.byref(bh)))
+            bonds.append(Bond.from_handle(ctx, bh))
+        return cls(ctx, bonds, handle=h)
+
+    def dagger(self) -> "Tensor":
+        """tnx_tensor_dagger: every bond redirected, the same blocks (Sec. 6.4)."""
+        h = C.c_void_p()
+        self.ctx.check(lib().tnx_tensor_dagger(self.h, C.byref(h)))
+        return Tensor.from_handle(self.ctx, h)
 
     def blocks(self):
         """(qn [nblk, rank] int32, shape [nblk, rank] int64, offset [nblk] int64)."""
@@ -501,6 +550,56 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class Dmrg:
+    """tnx_dmrg: two-site DMRG sweeps of a chain with a uniform MPO (Sec. 11)."""
+
+    def __init__(self, ctx: Context, nsites: int, W: Tensor, left_w: int, right_w: int, states):
+        self.ctx = ctx
+        st = np.ascontiguousarray(states, dtype=np.int32)
+        h = C.c_void_p()
+        ctx.check(lib().tnx_dmrg_create(ctx.h, nsites, W.h, left_w, right_w, _ptr(st, C.c_int32), C.byref(h)))
+        self.h = h
+        self.nsites = nsites
+
+    def sweep(self, maxdim: int, cutoff: float = 0.0, lanczos_steps: int = 20, prec="f64") -> dict:
+        e, te = C.c_double(), C.c_double()
+        mb = C.c_int64()
+        ph = (C.c_double * 4)()
+        p = PREC_NAMES[prec] if isinstance(prec, str) else int(prec)
+        self.ctx.check(lib().tnx_dmrg_sweep(self.h, maxdim, cutoff, lanczos_steps, p, C.byref(e), C.byref(te),
+                                            C.byref(mb), ph))
+        return {"energy": e.value, "max_trunc_err": te.value, "max_bond": mb.value,
+                "ms": {"lanczos": ph[0], "svd": ph[1], "env": ph[2], "sweep": ph[3]}}
+
+    def tensor(self, site: int) -> Tensor:
+        h = C.c_void_p()
+        self.ctx.check(lib().tnx_dmrg_tensor(self.h, site, C.byref(h)))
+        return Tensor.from_handle(self.ctx, h)
+
+    def close(self):
+        if self.h:
+            lib().tnx_dmrg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def svd_truncate(t: Tensor, rowrank: int, keepdim: int = 0, err: float = 0.0, min_blockdim=None, absorb: int = 0):
+    """tnx_svd_truncate (Sec. 9.2).  Returns (U, S or None, Vdag, largest dropped value, dropped weight)."""
+    mb = None if min_blockdim is None else np.ascontiguousarray(min_blockdim, dtype=np.int64)
+    U, S, V = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    te, dw = C.c_double(), C.c_double()
+    t.ctx.check(lib().tnx_svd_truncate(t.h, rowrank, keepdim, err, None if mb is None else _ptr(mb, C.c_int64),
+                                       0 if mb is None else len(mb), absorb, C.byref(U),
+                                       C.byref(S) if absorb == 0 else None, C.byref(V), C.byref(te), C.byref(dw)))
+    Sout = Tensor.from_handle(t.ctx, S) if absorb == 0 else None
+    return Tensor.from_handle(t.ctx, U), Sout, Tensor.from_handle(t.ctx, V), te.value, dw.value
 
 
 def lanczos(net: Network, slot: str, v0: Tensor, nsteps: int, evec: Tensor | None = None):

@@ -1,0 +1,244 @@
+// Singular value decomposition of the dense charge blocks of a block-sparse
+// tensor (Sec. 9.2 of arXiv 2401.01921; the paper calls LAPACK / cuSOLVER per
+// block), by one-sided Jacobi (Hestenes 1958; Demmel and Veselic, SIAM J.
+// Matrix Anal. Appl. 13, 1992):
+//
+//  * each block's shorter dimension gives c working vectors x_p of length r
+//    (the columns of M when it has no more columns than rows, else its rows),
+//    stored as the rows of X (c x r, row-major), and an accumulator J (c x c)
+//    starting at the identity;
+//  * a pair (p, q) with alpha = |x_p|^2, beta = |x_q|^2, gamma = x_p . x_q is
+//    rotated by the angle that makes it orthogonal: zeta = (beta - alpha) /
+//    (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 /
+//    sqrt(1 + t^2), s = c t; x_p <- c x_p - s x_q, x_q <- s x_p + c x_q, and
+//    the same on the rows p, q of J;
+//  * a sweep visits every pair once, in the round-robin ("circle") order:
+//    c' - 1 rounds of c'/2 disjoint pairs (c' = c rounded up to even; the
+//    pad index pairs with nobody).  One launch per round over the pairs of
+//    every block; a pair whose |gamma| is below 1e-15 sqrt(alpha beta) is left
+//    as it is; each launch records the largest |gamma| / sqrt(alpha beta) it
+//    met, and the host stops after a sweep whose largest value is small;
+//  * then sigma_p = |x_p|, and X = J M^T (or J M): the singular vectors are
+//    x_p / sigma_p on one side and the rows of J on the other.
+// All arithmetic is FP64.  Block reductions use a fixed order (deterministic).
+#include "tnx_internal.h"
+
+namespace {
+
+constexpr int JT = 256;   // threads per pair
+
+__device__ __forceinline__ double block_sum3(double& a, double& b, double& c, double* sh) {
+  // three sums at once over the CTA, fixed order; results broadcast in a, b, c
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if (lane == 0) {
+    sh[wid] = a;
+    sh[8 + wid] = b;
+    sh[16 + wid] = c;
+  }
+  __syncthreads();
+  a = b = c = 0.0;
+  for (int w = 0; w < JT / 32; ++w) {
+    a += sh[w];
+    b += sh[8 + w];
+    c += sh[16 + w];
+  }
+  __syncthreads();
+  return a;
+}
+
+__global__ void __launch_bounds__(JT) jacobi_round_kernel(const SvdGroup* __restrict__ groups,
+                                                          const int2* __restrict__ slots, int nslots, int round,
+                                                          unsigned long long* maxoff) {
+  tnx_grid_dependency();
+  __shared__ double sh[24];
+  __shared__ double s_cs[2];
+  __shared__ int s_skip;
+  for (int si = blockIdx.x; si < nslots; si += gridDim.x) {
+    const int2 sl = slots[si];
+    const SvdGroup g = groups[sl.x];
+    const int cp = g.c + (g.c & 1);   // c rounded up to even
+    if (cp < 2) continue;
+    const int kk = round % (cp - 1);
+    const int i = sl.y;
+    int p, q;
+    if (i == 0) {
+      p = kk;
+      q = cp - 1;
+    } else {
+      p = (kk + i) % (cp - 1);
+      q = (kk - i + cp - 1) % (cp - 1);
+    }
+    if (p > q) { const int t = p; p = q; q = t; }
+    if (q >= g.c) continue;           // the pad index
+    double* xp = g.X + (int64_t)p * g.r;
+    double* xq = g.X + (int64_t)q * g.r;
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int64_t e = threadIdx.x; e < g.r; e += JT) {
+      const double u = xp[e], v = xq[e];
+      a = fma(u, u, a);
+      b = fma(v, v, b);
+      c = fma(u, v, c);
+    }
+    block_sum3(a, b, c, sh);
+    if (threadIdx.x == 0) {
+      int skip = 1;
+      if (a > 0.0 && b > 0.0) {
+        const double off = fabs(c) / sqrt(a * b);
+        atomicMax(maxoff, (unsigned long long)__double_as_longlong(off));
+        if (off > 1e-15) {
+          skip = 0;
+          const double zeta = (b - a) / (2.0 * c);
+          const double az = fabs(zeta);
+          double t = az > 1e100 ? 0.5 / az : 1.0 / (az + sqrt(1.0 + az * az));
+          if (zeta < 0.0) t = -t;
+          const double cs = 1.0 / sqrt(1.0 + t * t);
+          s_cs[0] = cs;
+          s_cs[1] = cs * t;
+        }
+      }
+      s_skip = skip;
+    }
+    __syncthreads();
+    if (!s_skip) {
+      const double cs = s_cs[0], sn = s_cs[1];
+      for (int64_t e = threadIdx.x; e < g.r; e += JT) {
+        const double u = xp[e], v = xq[e];
+        xp[e] = cs * u - sn * v;
+        xq[e] = sn * u + cs * v;
+      }
+      double* jp = g.J + (int64_t)p * g.c;
+      double* jq = g.J + (int64_t)q * g.c;
+      for (int e = threadIdx.x; e < g.c; e += JT) {
+        const double u = jp[e], v = jq[e];
+        jp[e] = cs * u - sn * v;
+        jq[e] = sn * u + cs * v;
+      }
+    }
+    __syncthreads();   // s_cs / s_skip are rewritten by the next slot
+  }
+}
+
+// J = identity for every group (one CTA per group row block)
+__global__ void jacobi_init_kernel(const SvdGroup* __restrict__ groups, int ngroups) {
+  tnx_grid_dependency();
+  for (int gi = blockIdx.y; gi < ngroups; gi += gridDim.y) {
+    const SvdGroup g = groups[gi];
+    const int64_t n = (int64_t)g.c * g.c;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+      g.J[e] = (e / g.c == e % g.c) ? 1.0 : 0.0;
+  }
+}
+
+// sigma_p = |x_p| for every vector of every group: one warp per vector
+__global__ void vector_norms_kernel(const SvdGroup* __restrict__ groups, const int2* __restrict__ vecs, int nvec) {
+  tnx_grid_dependency();
+  const int lane = threadIdx.x & 31;
+  for (int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < nvec; v += gridDim.x * (blockDim.x >> 5)) {
+    const int2 gv = vecs[v];
+    const SvdGroup g = groups[gv.x];
+    const double* x = g.X + (int64_t)gv.y * g.r;
+    double a = 0.0;
+    for (int64_t e = lane; e < g.r; e += 32) a = fma(x[e], x[e], a);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) g.sigma[gv.y] = sqrt(a);
+  }
+}
+
+// Kept singular triplet k of a group: U column k (m rows, ld = kept) and V^T
+// row k (n columns); the vector x_p / sigma_p goes to one side and the row p of
+// J to the other; scale (sigma or 1) multiplies the U or the V^T side.
+__global__ void svd_extract_kernel(const SvdOut* __restrict__ outs, int nout) {
+  tnx_grid_dependency();
+  for (int oi = blockIdx.x; oi < nout; oi += gridDim.x) {
+    const SvdOut o = outs[oi];
+    const SvdGroup g = o.g;
+    const double sig = g.sigma[o.p];
+    const double inv = sig > 0.0 ? 1.0 / sig : 0.0;
+    const double* x = g.X + (int64_t)o.p * g.r;
+    const double* j = g.J + (int64_t)o.p * g.c;
+    // vectors are the columns of M: U gets x / sigma (length r = m), V^T gets j (length c = n);
+    // vectors are the rows of M:    U gets j (length c = m),         V^T gets x / sigma (length r = n)
+    const double su = o.absorb == 2 ? sig : 1.0;
+    const double sv = o.absorb == 1 ? sig : 1.0;
+    if (o.cols_are_vectors) {
+      for (int64_t e = threadIdx.x; e < g.r; e += blockDim.x) o.U[e * o.ldu + o.k] = x[e] * inv * su;
+      for (int64_t e = threadIdx.x; e < g.c; e += blockDim.x) o.Vt[(int64_t)o.k * o.ldv + e] = j[e] * sv;
+    } else {
+      for (int64_t e = threadIdx.x; e < g.c; e += blockDim.x) o.U[e * o.ldu + o.k] = j[e] * su;
+      for (int64_t e = threadIdx.x; e < g.r; e += blockDim.x) o.Vt[(int64_t)o.k * o.ldv + e] = x[e] * inv * sv;
+    }
+    if (threadIdx.x == 0 && o.S) o.S[(int64_t)o.k * o.lds + o.k] = sig;
+  }
+}
+
+// 2-D block copies: dst[i * dld + j] = src[i * sld + j] (or, transposed,
+// dst[j * dld + i] = src[i * sld + j]) for i < rows, j < cols
+__global__ void copy2d_kernel(const Copy2D* __restrict__ tasks, int ntasks) {
+  tnx_grid_dependency();
+  for (int ti = blockIdx.x; ti < ntasks; ti += gridDim.x) {
+    const Copy2D t = tasks[ti];
+    const int64_t n = (int64_t)t.rows * t.cols;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+      const int64_t i = e / t.cols, j = e % t.cols;
+      const double v = t.src[i * t.sld + j];
+      if (t.trans) t.dst[j * t.dld + i] = v;
+      else t.dst[i * t.dld + j] = v;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t tnx_launch_jacobi_init(const SvdGroup* groups, int ngroups, cudaStream_t st) {
+  if (ngroups <= 0) return cudaSuccess;
+  const cudaError_t le = tnx_launch(jacobi_init_kernel, dim3(64, ngroups < 65535 ? ngroups : 65535), dim3(256), 0, st,
+                                    groups, ngroups);
+  if (le != cudaSuccess) return le;
+  tnx_note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tnx_launch_jacobi_round(const SvdGroup* groups, const int2* slots, int nslots, int round,
+                                    unsigned long long* maxoff, cudaStream_t st) {
+  if (nslots <= 0) return cudaSuccess;
+  const int grid = nslots < 152 * 8 ? nslots : 152 * 8;
+  const cudaError_t le = tnx_launch(jacobi_round_kernel, dim3(grid), dim3(JT), 0, st, groups, slots, nslots, round,
+                                    maxoff);
+  if (le != cudaSuccess) return le;
+  tnx_note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tnx_launch_vector_norms(const SvdGroup* groups, const int2* vecs, int nvec, cudaStream_t st) {
+  if (nvec <= 0) return cudaSuccess;
+  const int grid = (nvec + 7) / 8 < 152 * 8 ? (nvec + 7) / 8 : 152 * 8;
+  const cudaError_t le = tnx_launch(vector_norms_kernel, dim3(grid), dim3(256), 0, st, groups, vecs, nvec);
+  if (le != cudaSuccess) return le;
+  tnx_note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tnx_launch_svd_extract(const SvdOut* outs, int nout, cudaStream_t st) {
+  if (nout <= 0) return cudaSuccess;
+  const int grid = nout < 152 * 8 ? nout : 152 * 8;
+  const cudaError_t le = tnx_launch(svd_extract_kernel, dim3(grid), dim3(128), 0, st, outs, nout);
+  if (le != cudaSuccess) return le;
+  tnx_note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tnx_launch_copy2d(const Copy2D* tasks, int ntasks, cudaStream_t st) {
+  if (ntasks <= 0) return cudaSuccess;
+  const int grid = ntasks < 152 * 8 ? ntasks : 152 * 8;
+  const cudaError_t le = tnx_launch(copy2d_kernel, dim3(grid), dim3(256), 0, st, tasks, ntasks);
+  if (le != cudaSuccess) return le;
+  tnx_note_launch(1);
+  return cudaGetLastError();
+}

@@ -339,6 +339,17 @@ extern "C" tnx_status tnx_bond_sectors(const tnx_bond* b, int* nsec, int32_t* qn
   return TNX_OK;
 }
 
+extern "C" tnx_status tnx_bond_info(const tnx_bond* b, int* dir, int* nsym, int* kinds, int* zn) {
+  if (!b) return TNX_ERR_ARG;
+  if (dir) *dir = b->b.dir;
+  if (nsym) *nsym = b->b.nsym;
+  for (int c = 0; c < b->b.nsym; ++c) {
+    if (kinds) kinds[c] = b->b.kinds[c];
+    if (zn) zn[c] = b->b.zn[c];
+  }
+  return TNX_OK;
+}
+
 extern "C" tnx_status tnx_bond_combine(const tnx_bond* a, const tnx_bond* b, tnx_bond** out) {
   if (!a || !b || !out) return TNX_ERR_ARG;
   tnx_ctx* ctx = a->ctx;
@@ -497,6 +508,17 @@ extern "C" tnx_status tnx_tensor_blocks(const tnx_tensor* t, int32_t* qn_idx, in
   if (shape) std::copy(t->shape.begin(), t->shape.end(), shape);
   if (offset) std::copy(t->off.begin(), t->off.end(), offset);
   return TNX_OK;
+}
+
+extern "C" tnx_status tnx_tensor_bond(const tnx_tensor* t, int leg, tnx_bond** out) {
+  if (!t) return TNX_ERR_ARG;
+  return tnx_guard(t->ctx, [&] {
+    if (!out || leg < 0 || leg >= t->rank) fail(TNX_ERR_ARG, "bad leg");
+    auto* b = new tnx_bond();
+    b->ctx = t->ctx;
+    b->b = t->bonds[leg];
+    *out = b;
+  });
 }
 
 extern "C" tnx_status tnx_tensor_data(tnx_tensor* t, double** dev_ptr, int64_t* nelem) {

@@ -222,6 +222,44 @@ size_t tnx_split_smem_bytes(int nslice, int tn);
 cudaError_t tnx_launch_gemm_tf32(const SplitGroup* groups, const GemmTile* tiles, int ntiles,
                                  double* const* slots, int32_t* status, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// SVD of dense charge blocks by one-sided Jacobi (k_svd.cu).  Per block: c
+// working vectors of length r as the rows of X (c x r, row-major), the
+// rotation accumulator J (c x c), sigma[c].
+struct SvdGroup {
+  double* X;
+  double* J;
+  double* sigma;
+  int32_t c, r;
+};
+// One kept singular triplet: vector p of group g becomes column k of U (row
+// stride ldu) and row k of V^T (row stride ldv); S (may be null) gets sigma at
+// (k, k) with row stride lds.  absorb: 0 none, 1 sigma into V^T, 2 into U.
+// cols_are_vectors: the working vectors are the columns of M (else its rows).
+struct SvdOut {
+  SvdGroup g;
+  int32_t p, k, absorb, cols_are_vectors;
+  double* U;
+  double* Vt;
+  double* S;
+  int64_t ldu, ldv, lds;
+};
+// dst[i * dld + j] = src[i * sld + j] (trans: dst[j * dld + i]) for i < rows, j < cols
+struct Copy2D {
+  const double* src;
+  double* dst;
+  int64_t sld, dld;
+  int32_t rows, cols, trans, pad0;
+};
+cudaError_t tnx_launch_jacobi_init(const SvdGroup* groups, int ngroups, cudaStream_t st);
+// round r of a sweep over slots (group, pair index); maxoff gets the largest
+// |x_p . x_q| / (|x_p| |x_q|) met, as the bits of a non-negative double
+cudaError_t tnx_launch_jacobi_round(const SvdGroup* groups, const int2* slots, int nslots, int round,
+                                    unsigned long long* maxoff, cudaStream_t st);
+cudaError_t tnx_launch_vector_norms(const SvdGroup* groups, const int2* vecs, int nvec, cudaStream_t st);
+cudaError_t tnx_launch_svd_extract(const SvdOut* outs, int nout, cudaStream_t st);
+cudaError_t tnx_launch_copy2d(const Copy2D* tasks, int ntasks, cudaStream_t st);
+
 // vector kernels (FP64, deterministic two-level reductions)
 cudaError_t tnx_launch_scale(double* x, int64_t n, double alpha, cudaStream_t st);
 cudaError_t tnx_launch_add_scalar(double* x, int64_t n, double alpha, cudaStream_t st);
