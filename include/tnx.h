@@ -237,6 +237,10 @@ tnx_status tnx_network_launch_into(tnx_network* net, tnx_tensor* out);
 /* Useful flops of one launch at the current order: 2*m*k*n summed over the
  * matched block pairs of every pairwise contraction (plans if needed). */
 tnx_status tnx_network_flops(tnx_network* net, double* flops);
+/* Device bytes the network holds now (plan buffers and Lanczos workspace);
+ * *plan_bytes (may be NULL) gets the bytes its plan needs at the current
+ * order and bonds, sized without allocating when no plan is built. */
+tnx_status tnx_network_resident(tnx_network* net, size_t* bytes, size_t* plan_bytes);
 /* Number of pairwise contractions in the plan (= number of tensors - 1). */
 tnx_status tnx_network_nsteps(tnx_network* net, int* nsteps);
 /* Fused charge-sector tables of pairwise contraction `step` (post-order of the

@@ -89,6 +89,7 @@ _SIGS = {
     "tnx_network_launch_into": (C.c_int, [_p, _p]),
     "tnx_network_flops": (C.c_int, [_p, C.POINTER(C.c_double)]),
     "tnx_network_nsteps": (C.c_int, [_p, C.POINTER(C.c_int)]),
+    "tnx_network_resident": (C.c_int, [_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "tnx_network_step_sizes": (C.c_int, [_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), _i64p, _i64p]),
     "tnx_network_step_tables": (C.c_int, [_p, C.c_int, _i32p, _i64p, _i64p, _i64p]),
     "tnx_lanczos": (C.c_int, [_p, C.c_char_p, _p, C.c_int, C.POINTER(C.c_double), _p, C.POINTER(C.c_int)]),
@@ -446,6 +447,12 @@ class Network:
         x = C.c_double()
         self.ctx.check(lib().tnx_network_flops(self.h, C.byref(x)))
         return x.value
+
+    def resident(self) -> tuple:
+        """(bytes held now, bytes its plan needs) - tnx_network_resident."""
+        b, pb = C.c_size_t(), C.c_size_t()
+        self.ctx.check(lib().tnx_network_resident(self.h, C.byref(b), C.byref(pb)))
+        return b.value, pb.value
 
     def nsteps(self) -> int:
         x = C.c_int()

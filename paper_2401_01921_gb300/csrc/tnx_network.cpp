@@ -1400,13 +1400,11 @@ void ensure_order(tnx_network* net) {
 
 void build_split_parts(Plan& p, StepPlan& s);
 
-Plan* ensure_plan(tnx_network* net) {
-  ensure_order(net);
-  const std::string order = tree_string(net, net->root);
-  const std::string key = plan_key(net, order);
-  if (net->plan && net->plan->key == key) return net->plan.get();
-  net->plan.reset();
+// Builds the plan of the network's current order and bonds; dry: a sizing
+// pass that allocates no plan buffer (see Plan::dry).
+std::unique_ptr<Plan> build_plan(tnx_network* net, const std::string& key, const std::string& order, bool dry) {
   std::unique_ptr<Plan> p(new Plan());
+  p->dry = dry;
   static uint64_t serial = 0;
   p->serial = ++serial;
   p->ctx = net->ctx;
@@ -1462,7 +1460,8 @@ Plan* ensure_plan(tnx_network* net) {
   OpView root = walk(net->root);
   build_final(*p, root, net->tout);
   fuse_skinny_steps(*p);
-  if (const char* dbg = getenv("TNX_DEBUG_PLAN")) {
+  const char* dbg = dry ? nullptr : getenv("TNX_DEBUG_PLAN");
+  if (dbg) {
     if (*dbg && *dbg != '0') {
       auto stats = [](const TaskList& t) {
         int tr = 0, packed = 0, band = 0;
@@ -1493,7 +1492,16 @@ Plan* ensure_plan(tnx_network* net) {
   p->d_slots = (double**)p->alloc_zero(p->h_slots.size() * sizeof(double*));
   p->h_slots_dev.assign(p->h_slots.size(), nullptr);
   CUDA_CHECK(cudaStreamSynchronize(net->ctx->stream));
-  net->plan = std::move(p);
+  return p;
+}
+
+Plan* ensure_plan(tnx_network* net) {
+  ensure_order(net);
+  const std::string order = tree_string(net, net->root);
+  const std::string key = plan_key(net, order);
+  if (net->plan && net->plan->key == key) return net->plan.get();
+  net->plan.reset();
+  net->plan = build_plan(net, key, order, false);
   return net->plan.get();
 }
 
@@ -1847,6 +1855,22 @@ struct LanczosCache {
 
 tnx_network::~tnx_network() = default;
 
+namespace {
+// Bytes of the Lanczos workspace buffers, in allocation order: V, w, alpha,
+// beta, coef, partial sums, y, scratch, state, eval.
+std::vector<size_t> lanczos_buffer_sizes(int64_t n, int nsteps) {
+  return {(size_t)(nsteps + 1) * n * 8, (size_t)n * 8, (size_t)(nsteps + 1) * 8, (size_t)(nsteps + 2) * 8,
+          (size_t)(nsteps + 2) * 8, (size_t)std::max<int64_t>(1216, (int64_t)608 * (nsteps + 2)) * 8,
+          (size_t)(nsteps + 1) * 8, (size_t)(4 * (nsteps + 1)) * 8, 64, 64};
+}
+}  // namespace
+
+size_t tnx_lanczos_workspace_bytes(int64_t n, int nsteps) {
+  size_t b = 0;
+  for (size_t x : lanczos_buffer_sizes(n, nsteps)) b += std::max<size_t>(x, 256);
+  return b;
+}
+
 // A whole Lanczos solve enqueued on `st`; at its end the eigenvalue and the
 // number of matvecs are copied to host_out[0] (double) and host_out[1] (int32
 // in its first four bytes), which must be pinned host memory.  No sync.
@@ -1878,21 +1902,24 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
     L.n = n;
     L.nmax = nsteps;
     L.nblocks = tnx_reduce_blocks(n);
+    const std::vector<size_t> sz = lanczos_buffer_sizes(n, nsteps);
+    size_t next = 0;
     auto dev = [&](size_t bytes) {
+      if (bytes != sz[next++]) fail(TNX_ERR_ARG, "internal: Lanczos workspace sizes disagree");
       lc->bufs.emplace_back(new DevBuf(ctx, std::max<size_t>(bytes, 256)));
       CUDA_CHECK(cudaMemsetAsync(lc->bufs.back()->p, 0, std::max<size_t>(bytes, 256), st));
       return lc->bufs.back()->p;
     };
-    L.V = (double*)dev((size_t)(nsteps + 1) * n * 8);
-    L.w = (double*)dev((size_t)n * 8);
-    L.alpha = (double*)dev((size_t)(nsteps + 1) * 8);
-    L.beta = (double*)dev((size_t)(nsteps + 2) * 8);
-    L.coef = (double*)dev((size_t)(nsteps + 2) * 8);
-    L.partial = (double*)dev((size_t)std::max<int64_t>(1216, (int64_t)608 * (nsteps + 2)) * 8);
-    L.y = (double*)dev((size_t)(nsteps + 1) * 8);
-    L.scratch = (double*)dev((size_t)(4 * (nsteps + 1)) * 8);
-    L.state = (int32_t*)dev(64);
-    L.eval = (double*)dev(64);
+    L.V = (double*)dev(sz[0]);
+    L.w = (double*)dev(sz[1]);
+    L.alpha = (double*)dev(sz[2]);
+    L.beta = (double*)dev(sz[3]);
+    L.coef = (double*)dev(sz[4]);
+    L.partial = (double*)dev(sz[5]);
+    L.y = (double*)dev(sz[6]);
+    L.scratch = (double*)dev(sz[7]);
+    L.state = (int32_t*)dev(sz[8]);
+    L.eval = (double*)dev(sz[9]);
   }
   LanczosDev& L = lc->L;
   bind_inputs(net, *p);
@@ -1984,6 +2011,30 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
   CUDA_CHECK(cudaMemcpyAsync(host_out + 1, L.state, 8, cudaMemcpyDeviceToHost, st));
 }
 
+size_t tnx_network_plan_bytes(tnx_network* net) {
+  ensure_order(net);
+  const std::string order = tree_string(net, net->root);
+  const std::string key = plan_key(net, order);
+  if (net->plan && net->plan->key == key) {
+    size_t b = 0;
+    for (auto& d : net->plan->bufs) b += d->bytes;
+    return b;
+  }
+  if (net->sized_key != key) {
+    std::unique_ptr<Plan> p = build_plan(net, key, order, true);
+    net->sized_key = key;
+    net->sized_bytes = p->dry_bytes;
+  }
+  return net->sized_bytes;
+}
+
+size_t tnx_network_lanczos_bytes(tnx_network* net) {
+  size_t b = 0;
+  if (net->lanczos)
+    for (auto& d : net->lanczos->bufs) b += d->bytes;
+  return b;
+}
+
 // Device bytes held by the network's plan and Lanczos workspace.
 size_t tnx_network_resident_bytes(tnx_network* net) {
   size_t b = 0;
@@ -2005,6 +2056,17 @@ int tnx_network_slot(tnx_network* net, const char* name) {
   for (size_t i = 0; i < net->ts.size(); ++i)
     if (net->ts[i].name == name) return (int)i;
   return -1;
+}
+
+extern "C" tnx_status tnx_network_resident(tnx_network* net, size_t* bytes, size_t* plan_bytes) {
+  if (!net) return TNX_ERR_ARG;
+  return tnx_guard(net->ctx, [&] {
+    if (bytes) *bytes = tnx_network_resident_bytes(net);
+    if (plan_bytes) {
+      if (!all_put(net)) fail(TNX_ERR_NETWORK, "every tensor must be put before the plan can be sized");
+      *plan_bytes = tnx_network_plan_bytes(net);
+    }
+  });
 }
 
 extern "C" tnx_status tnx_lanczos(tnx_network* net, const char* vec_slot, tnx_tensor* v0, int nsteps, double* eval,

@@ -129,14 +129,27 @@ struct Plan {
   std::string order;
   ~Plan() = default;
 
+  // Sizing pass (dry): the planner runs as usual (the matching kernel included)
+  // but plan buffers are only counted, at stand-in addresses nothing reads.
+  bool dry = false;
+  size_t dry_bytes = 0;
+  uintptr_t dry_next = 4096;
+  void* dry_take(size_t n) {
+    dry_bytes += n;
+    void* p = (void*)dry_next;
+    dry_next += (n + 255) & ~(size_t)255;
+    return p;
+  }
   template <class T>
   T* upload(const std::vector<T>& v) {
     size_t n = std::max<size_t>(v.size(), 1) * sizeof(T);
+    if (dry) return (T*)dry_take(n);
     bufs.emplace_back(new DevBuf(ctx, n));
     if (!v.empty()) CUDA_CHECK(cudaMemcpyAsync(bufs.back()->p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
     return (T*)bufs.back()->p;
   }
   void* alloc_zero(size_t bytes) {
+    if (dry) return dry_take(std::max<size_t>(bytes, 256));
     bufs.emplace_back(new DevBuf(ctx, std::max<size_t>(bytes, 256)));
     CUDA_CHECK(cudaMemsetAsync(bufs.back()->p, 0, std::max<size_t>(bytes, 256), ctx->stream));
     return bufs.back()->p;
@@ -159,6 +172,8 @@ struct tnx_network {
   bool narrow_tiles = true;        // split GEMM steps with few tiles may use 32-wide tiles
   int prec = TNX_PREC_F64;
   std::string order_dims_key;      // dims for which the optimal tree was computed
+  std::string sized_key;           // plan key of the last sizing pass, and its bytes
+  size_t sized_bytes = 0;
   std::unique_ptr<Plan> plan;
   std::unique_ptr<struct LanczosCache> lanczos;
   ~tnx_network();
@@ -181,4 +196,11 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
                          double* host_out);
 int tnx_network_slot(tnx_network* net, const char* name);
 size_t tnx_network_resident_bytes(tnx_network* net);
+// Device bytes the network's plan holds (its current plan, or a sizing pass
+// that allocates nothing but the matching kernel's temporaries), and the bytes
+// of a Lanczos workspace for n-element vectors and nsteps steps.
+size_t tnx_network_plan_bytes(tnx_network* net);
+size_t tnx_lanczos_workspace_bytes(int64_t n, int nsteps);
+// Bytes of the network's current Lanczos workspace (0 if none).
+size_t tnx_network_lanczos_bytes(tnx_network* net);
 void tnx_network_evict(tnx_network* net);

@@ -4,10 +4,13 @@
 // environment tensors stay resident on the device.  A worker thread admits
 // requests from the queue whenever (a) one of the server's stream slots is
 // free, (b) the request's network is not already running another request, and
-// (c) the network's resident memory (plan buffers and Lanczos workspace) fits
-// the HBM budget - idle resident networks are evicted least recently used
-// first to make room.  Admitted requests run on their own CUDA streams, so the
-// work of requests that arrive while others are on the GPU overlaps on the
+// (c) the bytes its network will hold while it runs (plan buffers, sized
+// before anything is allocated, plus the Lanczos workspace) fit the HBM
+// budget next to the bytes already resident - idle resident networks are
+// evicted least recently used first to make room; a request that could not
+// fit even alone fails with TNX_ERR_OOM.  Sizing and planning run with the
+// server's lock released.  Admitted requests run on their own CUDA streams, so
+// the work of requests that arrive while others are on the GPU overlaps on the
 // device; completions are detected with CUDA events and reported to waiters.
 // Latency = completion seen by the worker - submission (host steady clock).
 #include <algorithm>
@@ -39,6 +42,7 @@ struct Request {
   double eval = 0.0;
   int matvecs = 0;
   int stream_slot = -1;
+  size_t need = 0;     // resident bytes of its network while it runs (0 = not sized yet)
   cudaEvent_t done = nullptr;
 };
 
@@ -83,6 +87,8 @@ void account(tnx_server* S, tnx_network* net) {
 }
 
 // Make room for `need` more bytes by evicting idle networks (LRU); true if it fits.
+// An evicted network keeps no plan or workspace; its next request is sized
+// (and planned) again.
 bool make_room(tnx_server* S, size_t need, tnx_network* keep) {
   while (S->used + need > S->budget) {
     tnx_network* victim = nullptr;
@@ -101,32 +107,59 @@ bool make_room(tnx_server* S, size_t need, tnx_network* keep) {
   return true;
 }
 
-// Start request r on stream slot k (worker thread, lock held).
-void start(tnx_server* S, Request& r, int k) {
+// Runs f and turns a failure into (status, message) without touching the
+// context's error string (the caller's thread owns it).
+template <class F>
+int run_caught(F&& f, std::string& err) {
+  try {
+    f();
+    return TNX_OK;
+  } catch (const TnxError& e) {
+    err = e.msg;
+    return e.code;
+  } catch (const std::exception& e) {
+    err = e.what();
+    return TNX_ERR_ARG;
+  }
+}
+
+void bind_vector(Request& r) {
+  NetTensor& nt = r.net->ts[r.slot];
+  nt.t = r.vec;
+  nt.perm.assign(r.vec->rank, 0);
+  for (int j = 0; j < r.vec->rank; ++j) nt.perm[j] = j;
+}
+
+// Device bytes the request's network holds while the request runs: its plan
+// (sized without allocating when it is not resident) and its Lanczos
+// workspace (a solve allocates one for its step count; an apply keeps
+// whatever the network holds).  Worker thread, lock released, network marked
+// busy.
+size_t request_bytes(Request& r) {
+  bind_vector(r);
+  const size_t plan = tnx_network_plan_bytes(r.net);
+  const size_t lz = r.kind == TNX_REQ_LANCZOS ? tnx_lanczos_workspace_bytes(r.vec->nelem, r.nsteps)
+                                              : tnx_network_lanczos_bytes(r.net);
+  return plan + lz;
+}
+
+void finish_failed(tnx_server* S, Request& r, int code, const std::string& err) {
+  r.status = code;
+  r.err = err;
+  r.finished = Clock::now();
+  S->cv_done.notify_all();
+}
+
+// Enqueue request r on stream slot k (worker thread, lock released; the
+// network is marked busy and the slot taken).  Builds the plan if needed.
+int start(tnx_server* S, Request& r, int k, std::string& err) {
   cudaStream_t st = S->streams[k];
-  r.stream_slot = k;
-  r.started = Clock::now();
-  S->busy[r.net] = r.id;
-  S->slot_req[k] = r.id;
-  touch(S, r.net);
-  tnx_status code = tnx_guard(S->ctx, [&] {
-    NetTensor& nt = r.net->ts[r.slot];
-    nt.t = r.vec;
-    nt.perm.assign(r.vec->rank, 0);
-    for (int j = 0; j < r.vec->rank; ++j) nt.perm[j] = j;
+  return run_caught([&] {
+    bind_vector(r);
     if (r.kind == TNX_REQ_APPLY) tnx_apply_enqueue(r.net, r.out, st);
     else tnx_lanczos_enqueue(r.net, r.slot, r.vec, r.nsteps, r.out, st, S->pinned + 2 * k);
     CUDA_CHECK(cudaEventRecord(r.done, st));
-  });
-  account(S, r.net);
-  if (code != TNX_OK) {
-    r.status = code;
-    r.err = S->ctx->err;
-    r.finished = Clock::now();
-    S->busy.erase(r.net);
-    S->slot_req[k] = -1;
-    S->cv_done.notify_all();
-  }
+  }, err);
 }
 
 void worker_loop(tnx_server* S) {
@@ -159,27 +192,72 @@ void worker_loop(tnx_server* S) {
       progress = true;
       S->cv_done.notify_all();
     }
-    // admissions (first fit in arrival order)
-    for (auto it = S->queue.begin(); it != S->queue.end();) {
-      int k = -1;
-      for (int q = 0; q < S->max_slots; ++q)
-        if (S->slot_req[q] < 0) { k = q; break; }
-      if (k < 0) break;
-      Request& r = S->reqs[*it];
-      if (S->busy.count(r.net)) { ++it; continue; }
-      // memory: a network already resident needs nothing new unless its
-      // Lanczos workspace grows; a new one is sized by building it
-      size_t have = S->resident[r.net];
-      if (have == 0) {
-        if (!make_room(S, 0, r.net)) { ++it; continue; }
+    // admissions, first fit in arrival order.  Sizing and starting release
+    // the lock (planning runs kernels and waits for them); the scan restarts
+    // afterwards because submissions may have changed the queue meanwhile.
+    bool rescan = true;
+    while (rescan && !S->stop) {
+      rescan = false;
+      for (auto it = S->queue.begin(); it != S->queue.end();) {
+        int k = -1;
+        for (int q = 0; q < S->max_slots; ++q)
+          if (S->slot_req[q] < 0) { k = q; break; }
+        if (k < 0) break;
+        const int64_t id = *it;
+        Request& r = S->reqs[id];
+        if (S->busy.count(r.net)) { ++it; continue; }
+        if (r.need == 0) {
+          // size it: the network is marked busy so nothing else touches it
+          S->busy[r.net] = id;
+          lock.unlock();
+          std::string err;
+          size_t need = 0;
+          const int code = run_caught([&] { need = request_bytes(r); }, err);
+          lock.lock();
+          S->busy.erase(r.net);
+          if (code != TNX_OK) {
+            S->queue.erase(std::find(S->queue.begin(), S->queue.end(), id));
+            finish_failed(S, r, code, err);
+          } else {
+            r.need = std::max<size_t>(need, 1);
+          }
+          progress = rescan = true;
+          break;
+        }
+        if (r.need > S->budget) {
+          it = S->queue.erase(it);
+          finish_failed(S, r, TNX_ERR_OOM,
+                        "the request needs " + std::to_string(r.need) + " resident bytes, above the server's budget of " +
+                            std::to_string(S->budget));
+          progress = true;
+          continue;
+        }
+        const size_t have = S->resident[r.net];
+        const size_t extra = r.need > have ? r.need - have : 0;
+        if (!make_room(S, extra, r.net)) { ++it; continue; }
+        // admitted: reserve its bytes, take the slot, enqueue without the lock
+        S->used += extra;
+        S->resident[r.net] = have + extra;
+        S->peak_used = std::max(S->peak_used, S->used);
+        S->busy[r.net] = id;
+        S->slot_req[k] = id;
+        r.stream_slot = k;
+        r.started = Clock::now();
+        touch(S, r.net);
+        S->queue.erase(it);
+        lock.unlock();
+        std::string err;
+        const int code = start(S, r, k, err);
+        lock.lock();
+        account(S, r.net);
+        if (code != TNX_OK) {
+          S->busy.erase(r.net);
+          S->slot_req[k] = -1;
+          finish_failed(S, r, code, err);
+        }
+        progress = rescan = true;
+        break;
       }
-      start(S, r, k);
-      if (S->used > S->budget && !make_room(S, 0, r.net)) {
-        // cannot keep it resident next to the others: it still runs now (it is
-        // admitted), and the next admissions wait for room
-      }
-      it = S->queue.erase(it);
-      progress = true;
     }
     if (!progress) S->cv_work.wait_for(lock, std::chrono::microseconds(50));
   }
