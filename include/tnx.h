@@ -70,7 +70,12 @@ enum { TNX_BD_IN = 1, TNX_BD_OUT = -1, TNX_BD_REG = 0 };
  *      2012); slice products on the tcgen05 tensor cores, exact in FP32 over
  *      K chunks, recombined exactly in 64-bit integers, rounded once to FP64.
  *  TNX_PREC_F32       operands rounded to FP32, FP32 products and sums.
- *  TNX_PREC_TF32      operands rounded to TF32 on the tensor cores (one pass). */
+ *  TNX_PREC_TF32      one pass on the tcgen05 tensor cores (kind::tf32): each
+ *      row of A / column of B scaled by a power of two and rounded to TF32
+ *      (11 significant bits, nearest-even), FP32 sums over 640-long K chunks,
+ *      chunks summed in FP64.  Relative error about 2^-11 of the products.
+ *  In every variant, charge groups whose K is at most 16 (the MPO products)
+ *  run as FP64 products. */
 enum { TNX_PREC_F64 = 0, TNX_PREC_SPLIT_BF16 = 1, TNX_PREC_SPLIT_F16 = 2,
        TNX_PREC_F32 = 3, TNX_PREC_TF32 = 4 };
 

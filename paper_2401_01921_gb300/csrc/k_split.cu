@@ -36,6 +36,12 @@
 // no-swizzle K-major core-matrix layout, so a stage is one contiguous copy.
 // Every wait on an mbarrier is bounded (about a second of clock); a wait that
 // runs out records an error code and the CTA winds down without hanging.
+//
+// The same kernel, instantiated with TF = true, is the one-pass TF32 variant:
+// one "slice" per operand holding the entry scaled by its row (column) power of
+// two and rounded to TF32 (10 explicit mantissa bits, nearest-even), 16 K
+// values (64 bytes) per stage and row, tcgen05.mma.kind::tf32 with FP32
+// accumulation per 640-long K chunk, chunks summed in FP64 by the epilogue.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -161,6 +167,21 @@ __device__ __forceinline__ double i64_scaled_fast(long long v, int e) {
   return i64_scaled_to_double(v, e);
 }
 
+// kind::tf32: D f32, A/B tf32 (format 2), both K-major, M = 128, N = n
+__device__ __forceinline__ uint32_t instr_desc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                         uint32_t accumulate) {
   asm volatile(
@@ -185,14 +206,9 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ------------------------------------------------------------ slicing
-__device__ __forceinline__ uint16_t slice_bits(uint32_t s, uint32_t neg, int f16) {
-  // s <= 2^(beta-1) <= 128: exact as float via the 2^23 magic, exact in bf16 / f16
-  const float f = __int_as_float(0x4B000000 | s) - 8388608.0f;
-  uint16_t b;
-  if (f16) b = __half_as_ushort(__float2half_rn(f));
-  else b = (uint16_t)(__float_as_uint(f) >> 16);
-  return (s != 0 && neg) ? (uint16_t)(b | 0x8000) : b;
-}
+// 64 * (1 + 128 + ... + 128^5): added to a signed 42-bit value it makes every
+// base-128 digit non-negative (digit i of the sum is digit i of v plus 64)
+constexpr long long DIGIT_BIAS = 64LL * ((1LL << 42) - 1) / 127;
 
 // Slices of the packed operands, one CTA (8 warps) per work item.  Rows are
 // taken in groups of 8 (rows past an operand's end give zero slices); in a
@@ -204,9 +220,10 @@ __device__ __forceinline__ uint16_t slice_bits(uint32_t s, uint32_t neg, int f16
 // epilogue; then the group's 32-wide K tiles are sliced, 8 entries per lane,
 // 16 bytes per slice per lane written in the tiled core-matrix layout the
 // GEMM copies in.
+template <bool F16>
 __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restrict__ jobs,
-                                                         const int2* __restrict__ items, int64_t total, int nslice,
-                                                         int beta, int f16, double* const* __restrict__ slots) {
+                                                         const int2* __restrict__ items, int64_t total,
+                                                         double* const* __restrict__ slots) {
   tnx_grid_dependency();
   __shared__ unsigned long long s_max[8][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -259,56 +276,65 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restr
     const int64_t tile_bytes = (int64_t)tile_rows * TK * 2;
     char* base = (char*)slots[j.dst_slot] + j.dst_off_bytes;
     const int64_t inner = (int64_t)(rin >> 3) * 512 + kq * 128 + (rin & 7) * 16;
-    for (int kt = shared_group ? wid : 0; kt < KT; kt += shared_group ? 8 : 1) {
-      const int k0 = kt * TK + kq * 8;
-      uint32_t sl[MAXN][4];
+    // Digits of one K tile (8 entries per lane); the loads of the lane's next
+    // tile are issued before the current one is converted.
+    const int kt0 = shared_group ? wid : 0, kts = shared_group ? 8 : 1;
+    unsigned long long cur[8];
 #pragma unroll
-      for (int i = 0; i < MAXN; ++i)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) sl[i][q] = 0;
+    for (int e = 0; e < 8; ++e) {
+      const int k = kt0 * TK + kq * 8 + e;
+      cur[e] = (live && kt0 < KT && k < j.K) ? (unsigned long long)__double_as_longlong(src[k]) : 0ull;
+    }
+    for (int kt = kt0; kt < KT; kt += kts) {
+      unsigned long long nxt[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        const int k = k0 + e;
-        unsigned long long bits = 0;
-        if (live && k < j.K) bits = __double_as_longlong(src[k]);
-        const int eb = (int)((bits >> 52) & 0x7FF);
-        // |x| 2^(F-E-2) rounded half up: m53 * 2^-rs with rs = 54 - F + E_r - E >= 12
-        unsigned long long fix = 0;
-        if (eb != 0 && eb_r != 0) {
-          const unsigned long long m53 = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-          const int rs = 54 - F + (eb_r - eb);
-          fix = rs >= 64 ? 0ull : ((m53 >> (rs - 1)) + 1ull) >> 1;
-        }
-        // balanced base-128 digits of fix <= 2^41 in 32-bit arithmetic: the six
-        // unsigned 7-bit digits, then least significant first a digit >= 64
-        // becomes digit - 128 with a carry into the next; the top digit takes
-        // the rest (at most 64).  The sign of x goes on every digit.
-        const uint32_t lo = (uint32_t)(fix & 0x1FFFFFull), hi = (uint32_t)(fix >> 21);
-        uint32_t u[MAXN];
-        u[5] = lo & 127u;
-        u[4] = (lo >> 7) & 127u;
-        u[3] = lo >> 14;
-        u[2] = hi & 127u;
-        u[1] = (hi >> 7) & 127u;
-        u[0] = hi >> 14;
-        int dg[MAXN];
-        uint32_t carry = 0;
+        const int k = (kt + kts) * TK + kq * 8 + e;
+        nxt[e] = (live && kt + kts < KT && k < j.K) ? (unsigned long long)__double_as_longlong(src[k]) : 0ull;
+      }
+      uint32_t sl[MAXN][4];
 #pragma unroll
-        for (int i = MAXN - 1; i > 0; --i) {
-          const uint32_t t = u[i] + carry;
-          carry = t >= 64u ? 1u : 0u;
-          dg[i] = (int)t - (int)(carry << 7);
-        }
-        dg[0] = (int)(u[0] + carry);
-        if (bits >> 63) {
+      for (int e = 0; e < 8; e += 2) {
+        float f[2][MAXN];
 #pragma unroll
-          for (int i = 0; i < MAXN; ++i) dg[i] = -dg[i];
+        for (int h = 0; h < 2; ++h) {
+          const unsigned long long bits = cur[e + h];
+          const int eb = (int)((bits >> 52) & 0x7FF);
+          // |x| 2^(F-E-2) rounded half up: m53 * 2^-rs with rs = 54 - F + E_r - E >= 12
+          unsigned long long fix = 0;
+          if (eb != 0 && eb_r != 0) {
+            const unsigned long long m53 = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+            const int rs = 54 - F + (eb_r - eb);
+            fix = rs >= 64 ? 0ull : ((m53 >> (rs - 1)) + 1ull) >> 1;
+          }
+          // Balanced base-128 digits of the signed value v (|v| <= 2^41): with
+          // u = v + 64 * sum_i 128^i >= 0, the plain 7-bit digits e_i of u give
+          // d_i = e_i - 64 in [-64, 63] (the top digit takes the rest, at most 64),
+          // and sum_i d_i 128^i = v.
+          const long long v = (bits >> 63) ? -(long long)fix : (long long)fix;
+          const unsigned long long u = (unsigned long long)(v + DIGIT_BIAS);
+          const uint32_t lo = (uint32_t)(u & 0x1FFFFFull), hi = (uint32_t)(u >> 21);
+          uint32_t dg[MAXN];   // e_i of slice i (slice 0 = most significant)
+          dg[5] = lo & 127u;
+          dg[4] = (lo >> 7) & 127u;
+          dg[3] = lo >> 14;
+          dg[2] = hi & 127u;
+          dg[1] = (hi >> 7) & 127u;
+          dg[0] = hi >> 14;
+          // d = e - 64 exactly as FP32: in the binade of 1.5 * 2^23 one unit of the
+          // bit pattern is one unit of value, so (bits 0x4B400000 + d) - 1.5 * 2^23 = d
+#pragma unroll
+          for (int i = 0; i < MAXN; ++i) f[h][i] = __int_as_float(0x4B3FFFC0 + (int)dg[i]) - 12582912.0f;
         }
 #pragma unroll
         for (int i = 0; i < MAXN; ++i) {
-          const int d = dg[i];
-          const uint32_t b = slice_bits((uint32_t)(d < 0 ? -d : d), d < 0 ? 1u : 0u, f16);
-          sl[i][e >> 1] |= (e & 1) ? (b << 16) : b;
+          // |d| <= 64 is exact in BF16 (the top half of the FP32 word) and in FP16
+          if constexpr (F16) {
+            const __half2 hh = __floats2half2_rn(f[0][i], f[1][i]);
+            sl[i][e >> 1] = *(const uint32_t*)&hh;
+          } else {
+            sl[i][e >> 1] = __byte_perm(__float_as_uint(f[0][i]), __float_as_uint(f[1][i]), 0x7632);
+          }
         }
       }
 #pragma unroll
@@ -316,6 +342,80 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restr
         uint4 v = make_uint4(sl[i][0], sl[i][1], sl[i][2], sl[i][3]);
         *(uint4*)(base + ((mt * KT + kt) * MAXN + i) * tile_bytes + inner) = v;
       }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) cur[e] = nxt[e];
+    }
+  }
+}
+
+// TF32 operands of the one-pass variant: one CTA (8 warps) per item of eight
+// 8-row groups, one group per warp; lane = (row in group) * 4 + (4-column
+// group).  A row is scaled by 2^-E (E: unbiased exponent of its largest |x|,
+// stored for the epilogue like the split path's), rounded to 11 significant
+// bits (nearest-even) straight from the FP64 bits, and written as FP32 words
+// in the tiled core-matrix layout, 16 K values (64 bytes) per tile row.
+// Entries more than 2^126 below their row maximum flush to zero.
+__device__ __forceinline__ uint32_t tf32_word(unsigned long long bits, int eb_r) {
+  const int eb = (int)((bits >> 52) & 0x7FF);
+  const uint32_t sign = (uint32_t)(bits >> 63) << 31;
+  if (eb == 0 || eb_r == 0) return sign;
+  int ef = eb - eb_r + 127;
+  unsigned long long keep = ((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> 42;   // 11 bits
+  const unsigned long long rem = bits & ((1ull << 42) - 1), half = 1ull << 41;
+  if (rem > half || (rem == half && (keep & 1ull))) keep += 1;
+  if (keep >> 11) {
+    keep >>= 1;
+    ef += 1;
+  }
+  if (ef <= 0) return sign;
+  return sign | ((uint32_t)ef << 23) | ((uint32_t)(keep & 0x3FFull) << 13);
+}
+
+__global__ void __launch_bounds__(256) tf32_rows_kernel(const SliceJob* __restrict__ jobs,
+                                                        const int2* __restrict__ items, int64_t total,
+                                                        double* const* __restrict__ slots) {
+  tnx_grid_dependency();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int r8 = lane >> 2, kq = lane & 3;
+  constexpr int TKF = 16;   // K values per tile row
+  for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+    const int2 item = items[w];   // (job, first 8-row group)
+    const SliceJob& j = jobs[item.x];
+    const int64_t ngroups = ((int64_t)j.rows + j.tile_rows - 1) / j.tile_rows * (j.tile_rows / 8);
+    const int64_t rg = (int64_t)item.y + wid;
+    if (rg >= ngroups) continue;   // uniform over the warp
+    const int64_t row = rg * 8 + r8;
+    const bool live = row < j.rows;
+    const double* src = slots[j.src_slot] + j.src_off + row * j.ld;
+    unsigned long long mx = 0;
+    if (live)
+      for (int k = kq; k < j.K; k += 4) {
+        const unsigned long long b = __double_as_longlong(src[k]) & 0x7FFFFFFFFFFFFFFFull;
+        mx = b > mx ? b : mx;
+      }
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = v > mx ? v : mx;
+    }
+    const int eb_r = (int)(mx >> 52);
+    if (live && kq == 0) ((int32_t*)slots[j.exp_slot])[j.exp_off + row] = eb_r;
+    const int KT = (j.K + TKF - 1) / TKF;
+    const int tile_rows = j.tile_rows;
+    const int64_t mt = row / tile_rows;
+    const int rin = (int)(row % tile_rows);
+    const int64_t tile_bytes = (int64_t)tile_rows * TKF * 4;
+    char* base = (char*)slots[j.dst_slot] + j.dst_off_bytes;
+    const int64_t inner = (int64_t)(rin >> 3) * 512 + kq * 128 + (rin & 7) * 16;
+    for (int kt = 0; kt < KT; ++kt) {
+      uint32_t o[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int k = kt * TKF + kq * 4 + e;
+        const unsigned long long bits = (live && k < j.K) ? (unsigned long long)__double_as_longlong(src[k]) : 0ull;
+        o[e] = tf32_word(bits, eb_r);
+      }
+      *(uint4*)(base + (mt * KT + kt) * tile_bytes + inner) = make_uint4(o[0], o[1], o[2], o[3]);
     }
   }
 }
@@ -329,11 +429,12 @@ struct SplitShared {
 };
 
 // Persistent over tiles: CTA b takes tiles b, b + gridDim.x, ... of the list
-// (the host orders it longest-K first).  Tensor memory and the barriers are set
+// (the host orders it longest-K first, or lays out a per-CTA schedule whose
+// holes carry group -1).  Tensor memory and the barriers are set
 // up once per CTA; the stage ring and the chunk hand-off between the MMA warp
 // and the epilogue warps continue across tiles, so the producer streams the
 // next tile's slices while the epilogue drains the current one.
-template <int NS, int TNV>
+template <int NS, int TNV, bool TF>
 __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const SplitGroup* __restrict__ groups,
                                                              const GemmTile* __restrict__ tiles, int ntiles, int beta,
                                                              int f16, double* const* __restrict__ slots,
@@ -348,7 +449,9 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
   double (*sh_stage)[4] = (double (*)[4])(ring + STAGES * STAGE_BYTES + ((sizeof(SplitShared) + 15) & ~(size_t)15));
   int* sh_ebc = (int*)(sh_stage + EPI_WARPS * 32);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int KTPC = KC / TK;   // K tiles per exact chunk
+  constexpr int TKE = TF ? 16 : TK;   // K values per stage (64 bytes per row either way)
+  constexpr int KTPC = KC / TKE;      // K tiles per chunk
+  static_assert(!TF || NS == 1, "the TF32 variant has one operand slice");
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -378,8 +481,9 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
       int g = 0;   // global K-tile counter of this CTA
       for (int ti = blockIdx.x; ti < ntiles && !*abort_flag; ti += gridDim.x) {
         const GemmTile tl = tiles[ti];
+        if (tl.group < 0) continue;   // a hole of the per-CTA schedule
         const SplitGroup gr = groups[tl.group];
-        const int KT = (gr.K + TK - 1) / TK;
+        const int KT = (gr.K + TKE - 1) / TKE;
         const char* Ab = (const char*)slots[gr.a_slot] + gr.a_off_bytes + ((int64_t)(tl.m0 / TM) * KT) * NS * ATILE;
         const char* Bb = (const char*)slots[gr.b_slot] + gr.b_off_bytes + ((int64_t)(tl.n0 / TNV) * KT) * NS * BTILE;
         for (int kt = 0; kt < KT; ++kt, ++g) {
@@ -405,8 +509,10 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
       int g = 0, chunk = 0;
       bool ok = true;
       for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
-        const SplitGroup gr = groups[tiles[ti].group];
-        const int KT = (gr.K + TK - 1) / TK;
+        const int tg = tiles[ti].group;
+        if (tg < 0) continue;
+        const SplitGroup gr = groups[tg];
+        const int KT = (gr.K + TKE - 1) / TKE;
         for (int kt = 0; kt < KT; ++kt, ++g) {
           const int s = g % STAGES;
           const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
@@ -427,6 +533,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
           // consecutive TNV-row tiles, so the stack is one taller K-major operand);
           // its output columns are the accumulators of levels i .. NS-1, also
           // consecutive: one MMA (N <= 256, else two) per A slice and K step.
+          // A K step is 32 bytes of every row: 16 values of BF16/FP16, 8 of TF32.
 #pragma unroll
           for (int ks = 0; ks < TK / 16; ++ks) {
 #pragma unroll
@@ -439,7 +546,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
               for (int j0 = 0; j0 < nj; j0 += PER_MMA) {
                 const int cnt = (nj - j0) < PER_MMA ? (nj - j0) : PER_MMA;
                 const uint64_t bd = smem_desc(sb + j0 * BTILE + ks * 256);
-                mma_f16(tmem + (uint32_t)((i + j0) * TNV), ad, bd, instr_desc(f16, cnt * TNV), acc);
+                if constexpr (TF) mma_tf32(tmem + (uint32_t)((i + j0) * TNV), ad, bd, instr_desc_tf32(cnt * TNV), acc);
+                else mma_f16(tmem + (uint32_t)((i + j0) * TNV), ad, bd, instr_desc(f16, cnt * TNV), acc);
               }
             }
           }
@@ -465,8 +573,9 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
     bool ok = true;
     for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
       const GemmTile tl = tiles[ti];
+      if (tl.group < 0) continue;
       const SplitGroup gr = groups[tl.group];
-      const int KT = (gr.K + TK - 1) / TK;
+      const int KT = (gr.K + TKE - 1) / TKE;
       const int nchunks = (KT + KTPC - 1) / KTPC;
       const int row = tl.m0 + sub * 32 + lane;
       // Row and column exponents are fetched before the first accumulator
@@ -480,8 +589,12 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
         if (lane < ECOLS) ebc_s[lane] = col < gr.N ? eb_c[col] : 0;
       }
       long long acc[ECOLS];
+      double accd[ECOLS];   // TF32: FP64 sum of the FP32 chunk sums
 #pragma unroll
-      for (int c = 0; c < ECOLS; ++c) acc[c] = 0;
+      for (int c = 0; c < ECOLS; ++c) {
+        acc[c] = 0;
+        accd[c] = 0.0;
+      }
       for (int ch = 0; ch < nchunks; ++ch, ++chunk) {
         if (!mbar_wait(&sh->accfull, (uint32_t)chunk & 1u, status, 14, abort_flag)) {
           ok = false;
@@ -498,11 +611,15 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
           tmem_wait_ld();
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
-            long long x = 0;
+            if constexpr (TF) {
+              accd[cg * 8 + c] += (double)__uint_as_float(v[0][c]);
+            } else {
+              long long x = 0;
 #pragma unroll
-            for (int t = 0; t < NS; ++t)
-              x += (long long)__float2int_rn(__uint_as_float(v[t][c])) * (1LL << (beta * (NS - 1 - t)));
-            acc[cg * 8 + c] += x;
+              for (int t = 0; t < NS; ++t)
+                x += (long long)__float2int_rn(__uint_as_float(v[t][c])) * (1LL << (beta * (NS - 1 - t)));
+              acc[cg * 8 + c] += x;
+            }
           }
         }
         tc_fence_before();
@@ -521,8 +638,13 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
         for (int c4 = 0; c4 < ECOLS / 4; ++c4) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            const int e = eb_r + ebc_s[c4 * 4 + c] - 2044 - 2 * (NS * beta - 1) + beta * (NS - 1);
-            stg[lane][c ^ ((lane >> 2) & 3)] = i64_scaled_fast(acc[c4 * 4 + c], e);
+            if constexpr (TF) {
+              // operands were scaled by 2^-(E_r) and 2^-(E_c)
+              stg[lane][c ^ ((lane >> 2) & 3)] = ldexp(accd[c4 * 4 + c], eb_r + ebc_s[c4 * 4 + c] - 2046);
+            } else {
+              const int e = eb_r + ebc_s[c4 * 4 + c] - 2044 - 2 * (NS * beta - 1) + beta * (NS - 1);
+              stg[lane][c ^ ((lane >> 2) & 3)] = i64_scaled_fast(acc[c4 * 4 + c], e);
+            }
           }
           __syncwarp();
           const int cc = lane & 3, col = tl.n0 + cb + c4 * 4 + cc;
@@ -551,8 +673,10 @@ cudaError_t tnx_launch_slices(const SliceJob* jobs, const int2* items, int64_t t
   int64_t blocks = total_items;
   if (blocks > 152 * 8) blocks = 152 * 8;
   {
-    const cudaError_t le = tnx_launch(slice_rows_kernel, dim3((int)blocks), dim3(256), 0, st,
-                                      jobs, items, total_items, nslice, beta, f16, slots);
+    const cudaError_t le = f16 ? tnx_launch(slice_rows_kernel<true>, dim3((int)blocks), dim3(256), 0, st,
+                                            jobs, items, total_items, slots)
+                               : tnx_launch(slice_rows_kernel<false>, dim3((int)blocks), dim3(256), 0, st,
+                                            jobs, items, total_items, slots);
     if (le != cudaSuccess) return le;
   }
   tnx_note_launch(1);
@@ -567,20 +691,21 @@ size_t tnx_split_smem_bytes(int nslice, int tn) {
 }
 
 namespace {
-template <int TNV>
+template <int TNV, bool TF>
 cudaError_t launch_split(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int beta, int f16,
                          double* const* slots, int32_t* status, cudaStream_t st, int grid) {
-  const size_t smem = tnx_split_smem_bytes(MAXN, TNV);
+  constexpr int NS = TF ? 1 : MAXN;
+  const size_t smem = tnx_split_smem_bytes(NS, TNV);
   static int attr_dev = -1;   // the opt-in is per device
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (attr_dev != dev) {
-    e = cudaFuncSetAttribute(split_gemm_kernel<MAXN, TNV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(split_gemm_kernel<NS, TNV, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_dev = dev;
   }
-  return tnx_launch(split_gemm_kernel<MAXN, TNV>, dim3(grid), dim3(SPLIT_THREADS), smem, st,
+  return tnx_launch(split_gemm_kernel<NS, TNV, TF>, dim3(grid), dim3(SPLIT_THREADS), smem, st,
                     groups, tiles, ntiles, beta, f16, slots, status);
 }
 }  // namespace
@@ -590,13 +715,33 @@ cudaError_t tnx_launch_gemm_split(const SplitGroup* groups, const GemmTile* tile
   if (ntiles <= 0) return cudaSuccess;
   if (grid <= 0 || grid > ntiles) grid = ntiles;
   if (nslice != MAXN || beta != 7 || (tn != 32 && tn != 64)) return cudaErrorInvalidValue;
-  const cudaError_t le = tn == 32 ? launch_split<32>(groups, tiles, ntiles, beta, f16, slots, status, st, grid)
-                                  : launch_split<64>(groups, tiles, ntiles, beta, f16, slots, status, st, grid);
+  const cudaError_t le = tn == 32 ? launch_split<32, false>(groups, tiles, ntiles, beta, f16, slots, status, st, grid)
+                                  : launch_split<64, false>(groups, tiles, ntiles, beta, f16, slots, status, st, grid);
   if (le != cudaSuccess) return le;
   tnx_note_launch(1);
   return cudaGetLastError();
 }
 
-cudaError_t tnx_launch_gemm_tf32(const SplitGroup*, const GemmTile*, int, double* const*, int32_t*, cudaStream_t) {
-  return cudaErrorNotSupported;
+cudaError_t tnx_launch_tf32_rows(const SliceJob* jobs, const int2* items, int64_t total_items, double* const* slots,
+                                 cudaStream_t st) {
+  if (total_items <= 0) return cudaSuccess;
+  int64_t blocks = total_items;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  const cudaError_t le = tnx_launch(tf32_rows_kernel, dim3((int)blocks), dim3(256), 0, st, jobs, items, total_items,
+                                    slots);
+  if (le != cudaSuccess) return le;
+  tnx_note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tnx_launch_gemm_tf32(const SplitGroup* groups, const GemmTile* tiles, int ntiles, double* const* slots,
+                                 int32_t* status, cudaStream_t st, int grid, int tn) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (grid <= 0 || grid > ntiles) grid = ntiles;
+  if (tn != 32 && tn != 64) return cudaErrorInvalidValue;
+  const cudaError_t le = tn == 32 ? launch_split<32, true>(groups, tiles, ntiles, 0, 0, slots, status, st, grid)
+                                  : launch_split<64, true>(groups, tiles, ntiles, 0, 0, slots, status, st, grid);
+  if (le != cudaSuccess) return le;
+  tnx_note_launch(1);
+  return cudaGetLastError();
 }

@@ -98,6 +98,13 @@ void enqueue_batch(tnx_batch& B, cudaStream_t st) {
       ProfScope ps(c, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
       if (B.prec == TNX_PREC_F64) CUDA_CHECK(tnx_launch_gemm_f64(s.dG, s.dT, s.nt, B.d_slots, st));
       else CUDA_CHECK(tnx_launch_gemm_f32(s.dG, s.dT, s.nt, B.d_slots, st));
+    } else if (B.prec == TNX_PREC_TF32) {
+      if (s.jobs.n) {
+        ProfScope ps(c, st, TNX_KC_SLICE, (double)s.jobs.elems * 20.0);
+        CUDA_CHECK(tnx_launch_tf32_rows(s.jobs.d, s.jobs.items, s.jobs.nitems, B.d_slots, st));
+      }
+      ProfScope ps(c, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
+      CUDA_CHECK(tnx_launch_gemm_tf32(s.dSG, s.dST, s.nst, B.d_slots, c->d_status, st, B.split_grid, 64));
     } else {
       if (s.jobs.n) {
         ProfScope ps(c, st, TNX_KC_SLICE, (double)s.jobs.elems * (16.0 + 2.0 * B.nslice));
@@ -161,7 +168,7 @@ extern "C" tnx_status tnx_batch_create(tnx_ctx* ctx, int n, tnx_network* const* 
     B->d_slots = (double**)B->bufs.back()->p;
     const size_t nst = B->plans[0]->steps.size();
     B->steps.resize(nst);
-    const bool split = B->prec == TNX_PREC_SPLIT_BF16 || B->prec == TNX_PREC_SPLIT_F16;
+    const bool split = B->prec == TNX_PREC_SPLIT_BF16 || B->prec == TNX_PREC_SPLIT_F16 || B->prec == TNX_PREC_TF32;
     for (size_t s = 0; s < nst; ++s) {
       BStep& bs = B->steps[s];
       std::vector<const TaskList*> pa, pb;
@@ -222,7 +229,8 @@ extern "C" tnx_status tnx_batch_create(tnx_ctx* ctx, int n, tnx_network* const* 
           return sg[x.group].K > sg[y.group].K;
         });
         // the merged launch is larger than any instance's: schedule it afresh
-        const std::vector<int2> items = tnx_slice_schedule(jobs);
+        const std::vector<int2> items =
+            B->prec == TNX_PREC_TF32 ? tnx_tf32_schedule(jobs) : tnx_slice_schedule(jobs);
         bs.jobs.n = (int)jobs.size();
         bs.jobs.nitems = (int64_t)items.size();
         bs.jobs.d = B->upload(jobs);

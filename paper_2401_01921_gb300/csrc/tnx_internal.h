@@ -219,8 +219,13 @@ cudaError_t tnx_launch_gemm_split(const SplitGroup* groups, const GemmTile* tile
                                   int beta, int f16, double* const* slots, int32_t* status, cudaStream_t st,
                                   int grid, int tn);
 size_t tnx_split_smem_bytes(int nslice, int tn);
-cudaError_t tnx_launch_gemm_tf32(const SplitGroup* groups, const GemmTile* tiles, int ntiles,
-                                 double* const* slots, int32_t* status, cudaStream_t st);
+// One-pass TF32 variant: tnx_launch_tf32_rows writes each operand row scaled by
+// its power of two and rounded to TF32 (FP32 words, 16 K values per tile row,
+// the same byte layout as one 16-bit slice); the GEMM runs kind::tf32 MMAs.
+cudaError_t tnx_launch_tf32_rows(const SliceJob* jobs, const int2* items, int64_t total_items, double* const* slots,
+                                 cudaStream_t st);
+cudaError_t tnx_launch_gemm_tf32(const SplitGroup* groups, const GemmTile* tiles, int ntiles, double* const* slots,
+                                 int32_t* status, cudaStream_t st, int grid, int tn);
 
 // ---------------------------------------------------------------------------
 // SVD of dense charge blocks by one-sided Jacobi (k_svd.cu).  Per block: c

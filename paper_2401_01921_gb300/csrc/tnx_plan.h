@@ -80,8 +80,9 @@ struct StepPlan {
   GemmTile* dST = nullptr;
   int nstiles = 0;
   int split_tn = 64;            // tile width of the split GEMM (B slices are tiled to match)
+  int split_grid = 0;           // CTAs of the split GEMM; dST holds its per-CTA schedule (holes: group -1)
   std::vector<SplitGroup> hSG;  // host copies
-  std::vector<GemmTile> hST;
+  std::vector<GemmTile> hST;    // tiles longest K first, no holes (batched plans merge them)
   // fused skinny step (k_fused.cu): one launch replaces the relayout of A, the
   // skinny product and (when fscatter is set) the next step's relayout of C
   FusedTile* dFT = nullptr;
@@ -184,6 +185,7 @@ struct tnx_network {
 void tnx_build_split_parts(Plan& p, StepPlan& s);
 void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB);
 std::vector<int2> tnx_slice_schedule(std::vector<SliceJob>& jobs);
+std::vector<int2> tnx_tf32_schedule(std::vector<SliceJob>& jobs);
 
 // relayout chunks (tnx_network.cpp)
 void tnx_make_copy_chunks(const std::vector<CopyTask>& tasks, std::vector<int4>& chunks);

@@ -1,7 +1,10 @@
 // Split-precision planning: per pairwise step, the row-exponent and slicing
 // jobs that turn the packed FP64 operands into tiles of integer-valued 16-bit
-// slices, and the tile list of the tcgen05 split GEMM (k_split.cu).
+// slices, and the tile list of the tcgen05 split GEMM (k_split.cu).  The
+// one-pass TF32 variant uses the same plan with one slice of FP32 words per
+// operand (16 K values, 64 bytes, per tile row: the same bytes per tile).
 #include <algorithm>
+#include <queue>
 
 #include "tnx_plan.h"
 
@@ -33,10 +36,24 @@ std::vector<int2> tnx_slice_schedule(std::vector<SliceJob>& jobs) {
   return items;
 }
 
+// TF32 rows: every job one warp per 8-row group, eight groups per CTA item.
+std::vector<int2> tnx_tf32_schedule(std::vector<SliceJob>& jobs) {
+  std::vector<int2> items;
+  for (size_t q = 0; q < jobs.size(); ++q) {
+    SliceJob& j = jobs[q];
+    j.cta_mode = 0;
+    const int64_t g = ((int64_t)j.rows + j.tile_rows - 1) / j.tile_rows * (j.tile_rows / 8);
+    if (g > INT32_MAX) fail(TNX_ERR_UNSUPPORTED, "TF32 operand above 2^31 row groups");
+    for (int64_t r = 0; r < g; r += 8) items.push_back(make_int2((int)q, (int)r));
+  }
+  return items;
+}
+
 void tnx_build_split_parts(Plan& p, StepPlan& s) {
-  if (p.prec == TNX_PREC_TF32) fail(TNX_ERR_UNSUPPORTED, "TF32 products are not available in this build");
+  const bool tf32 = p.prec == TNX_PREC_TF32;
   const int G = s.G;
-  const int n = p.nslice;
+  const int n = tf32 ? 1 : p.nslice;
+  const int TKE = tf32 ? 16 : TK;   // K values per 64-byte tile row
   std::vector<SliceJob> jobs[2];
   int64_t elems[2] = {0, 0};
   std::vector<int64_t> offSA(G), offSB(G), offEA(G), offEB(G);
@@ -59,7 +76,7 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
       continue;
     }
     if (K > KMAX) fail(TNX_ERR_UNSUPPORTED, "split precision supports K <= 8192 per charge sector");
-    const int64_t KT = (K + TK - 1) / TK, MT = (M + TM - 1) / TM, NT = (N + TN - 1) / TN;
+    const int64_t KT = (K + TKE - 1) / TKE, MT = (M + TM - 1) / TM, NT = (N + TN - 1) / TN;
     offSA[g] = sa;
     offSB[g] = sb;
     offEA[g] = ea;
@@ -96,7 +113,7 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
     }
   }
   auto make = [&](std::vector<SliceJob> js, int64_t el) {
-    const std::vector<int2> items = tnx_slice_schedule(js);
+    const std::vector<int2> items = tf32 ? tnx_tf32_schedule(js) : tnx_slice_schedule(js);
     StepPlan::Jobs J;
     J.n = (int)js.size();
     J.nitems = (int64_t)items.size();
@@ -132,14 +149,48 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
     x.N = (int32_t)s.mkn[3 * g + 2];
     x.ldc = x.N;
     if (s.skinny[g]) continue;
-    for (int m0 = 0; m0 < x.M; m0 += TM)
-      for (int n0 = 0; n0 < x.N; n0 += TN) tiles.push_back(GemmTile{g, m0, n0, 0});
+    // Tiles that run at the same time should share the larger operand panel,
+    // so that the smaller one is what gets re-read (from L2): column-major
+    // order (tiles of one B column panel together) when A is the smaller.
+    if (x.M < x.N) {
+      for (int n0 = 0; n0 < x.N; n0 += TN)
+        for (int m0 = 0; m0 < x.M; m0 += TM) tiles.push_back(GemmTile{g, m0, n0, 0});
+    } else {
+      for (int m0 = 0; m0 < x.M; m0 += TM)
+        for (int n0 = 0; n0 < x.N; n0 += TN) tiles.push_back(GemmTile{g, m0, n0, 0});
+    }
   }
   std::stable_sort(tiles.begin(), tiles.end(),
                    [&](const GemmTile& x, const GemmTile& y) { return sg[x.group].K > sg[y.group].K; });
+  // More tiles than SMs (one CTA fits per SM): a persistent grid of 152 CTAs,
+  // each streaming its next tile's operands while it drains the current one.
+  // Tiles go to CTAs longest first, each to the least loaded CTA (work = K
+  // tiles plus a fixed drain cost); CTA c takes positions c, c + NC, ... of the
+  // device list, and holes (group -1) pad the shorter lists.
+  const int NC = (int)std::min<size_t>(tiles.size(), 152);
+  std::vector<GemmTile> sched = tiles;
+  if (NC > 0 && (size_t)NC < tiles.size()) {
+    std::vector<std::vector<int>> per(NC);
+    typedef std::pair<int64_t, int> Load;   // (work, cta)
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int c = 0; c < NC; ++c) heap.push(Load(0, c));
+    for (size_t t = 0; t < tiles.size(); ++t) {
+      Load l = heap.top();
+      heap.pop();
+      per[l.second].push_back((int)t);
+      l.first += (sg[tiles[t].group].K + TKE - 1) / TKE + 4;
+      heap.push(l);
+    }
+    size_t depth = 0;
+    for (auto& v : per) depth = std::max(depth, v.size());
+    sched.assign((size_t)NC * depth, GemmTile{-1, 0, 0, 0});
+    for (int c = 0; c < NC; ++c)
+      for (size_t k = 0; k < per[c].size(); ++k) sched[c + k * NC] = tiles[per[c][k]];
+  }
   s.dSG = p.upload(sg);
-  s.dST = p.upload(tiles);
-  s.nstiles = (int)tiles.size();
+  s.dST = p.upload(sched);
+  s.nstiles = (int)sched.size();
+  s.split_grid = NC;
   s.hSG = sg;
   s.hST = tiles;
 }
@@ -147,11 +198,21 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
 void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB) {
   const int f16 = p.prec == TNX_PREC_SPLIT_F16 ? 1 : 0;
   const StepPlan::Jobs* J = (needA && needB) ? &s.jobsAll : needA ? &s.jobsA : needB ? &s.jobsB : nullptr;
+  if (p.prec == TNX_PREC_TF32) {
+    if (J && J->n) {
+      ProfScope ps(p.ctx, st, TNX_KC_SLICE, (double)J->elems * (8.0 + 8.0 + 4.0));
+      CUDA_CHECK(tnx_launch_tf32_rows(J->d, J->items, J->nitems, p.d_slots, st));
+    }
+    ProfScope ps(p.ctx, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
+    CUDA_CHECK(tnx_launch_gemm_tf32(s.dSG, s.dST, s.nstiles, p.d_slots, p.ctx->d_status, st, s.split_grid,
+                                    s.split_tn));
+    return;
+  }
   if (J && J->n) {
     ProfScope ps(p.ctx, st, TNX_KC_SLICE, (double)J->elems * (8.0 + 8.0 + 2.0 * p.nslice));
     CUDA_CHECK(tnx_launch_slices(J->d, J->items, J->nitems, p.nslice, p.beta, f16, p.d_slots, st));
   }
   ProfScope ps(p.ctx, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
-  CUDA_CHECK(tnx_launch_gemm_split(s.dSG, s.dST, s.nstiles, p.nslice, p.beta, f16, p.d_slots, p.ctx->d_status, st, 0,
-                                   s.split_tn));
+  CUDA_CHECK(tnx_launch_gemm_split(s.dSG, s.dST, s.nstiles, p.nslice, p.beta, f16, p.d_slots, p.ctx->d_status, st,
+                                   s.split_grid, s.split_tn));
 }

@@ -25,7 +25,7 @@ def instances():
     return [I.hubbard_workload(c, seed_base=1000 + 4 * i) for i, c in enumerate(chis)]
 
 
-@pytest.mark.parametrize("prec", ["f64", "split_bf16"])
+@pytest.mark.parametrize("prec", ["f64", "split_bf16", "tf32"])
 def test_batch_equals_individual_launches(ctx, prec):
     import paper_2401_01921_gb300 as tnx
     wls = instances()
@@ -48,4 +48,4 @@ def test_batch_equals_individual_launches(ctx, prec):
     for (net, T, B), o, wl in zip(built, outs, wls):
         onet, _ = oracle_heff(wl, order="(L,(((psi,R),W2),W1))")
         err = rel_fro(o.block_dict(), onet.launch())
-        assert err <= (1e-12 if prec == "f64" else 1e-10), err
+        assert err <= {"f64": 1e-12, "split_bf16": 1e-10, "tf32": 2e-3}[prec], err

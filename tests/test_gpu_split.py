@@ -3,7 +3,9 @@
 Split BF16 / FP16 (Ozaki-style slices on tcgen05, exact FP32 chunks, int64
 recombination): relative Frobenius error <= 1e-10 on every workload, and
 bit-exact on integer inputs whose slices carry them exactly.  FP32: the error
-is reported, bounded loosely (1e-5).
+is reported, bounded loosely (1e-5).  TF32 (one pass on the tensor cores):
+every output entry within the rounding bound of its products, from the
+oracle's contraction of the absolute values.
 """
 import numpy as np
 import pytest
@@ -62,6 +64,39 @@ def test_f32_error_reported(ctx):
     assert 1e-12 < err < 1e-5
 
 
+def abs_network(wl, order=None):
+    """The oracle's H_eff with every tensor replaced by its entrywise absolute value:
+    sum |L||psi||W||W||R|, the scale of the rounding error of each output entry."""
+    from oracle.symtensor import BlockTensor
+    onet, OT = oracle_heff(wl, order=order)
+    for n, t in OT.items():
+        onet.put(n, BlockTensor(t.bonds, {q: np.abs(b) for q, b in t.blocks.items()}))
+    return onet.launch()
+
+
+@pytest.mark.parametrize("name", ["u1_chi40_ragged", "u1_chi512", "hubbard_chi128"])
+def test_tf32_within_rounding_bound(ctx, name):
+    """TF32 products round each operand to 11 significant bits (relative 2^-12 each) and sum in FP32
+    per K chunk; with two tensor-core products on the path (psi*R-like and L*Y-like steps; the MPO
+    products stay FP64) every entry's error is below 2^-9 * (sum of |terms|), and it is a real TF32
+    error (far above FP32's)."""
+    wl = WORKLOADS[name]()
+    net, T, B = lib_heff(ctx, wl, prec="tf32")
+    order = net.get_order()
+    got = net.launch(B["psi"]).block_dict()
+    onet, _ = oracle_heff(wl, order=order)
+    ref = onet.launch()
+    scale = abs_network(wl, order=order)
+    worst = 0.0
+    for q, b in ref.blocks.items():
+        d = np.abs(got.get(q, 0.0) - b)
+        worst = max(worst, float(np.max(d / np.maximum(scale.blocks[q], 1e-300))))
+    err = rel_fro(got, ref)
+    print(f"{name} tf32: rel err {err:.3e}, worst |err| / sum|terms| {worst:.3e}")
+    assert worst <= 2.0 ** -9, worst
+    assert 1e-6 < err < 2e-3, err
+
+
 @pytest.mark.parametrize("chi,n", [(40, 9), (512, 20)])
 @pytest.mark.parametrize("prec", ["split_bf16", "split_f16"])
 def test_split_exact_on_integers(ctx, prec, chi, n):
@@ -101,7 +136,7 @@ def test_split_lanczos(ctx):
 # relative error of a single block (the 10^U(-3,0) sector scaling makes some blocks 1000x smaller than
 # others that share a row or column scale of the split products, which costs those blocks bits).
 SWEEP_BOUNDS = {"f64": (1e-12, 1e-12), "split_bf16": (TOL_SPLIT, 1e-8), "split_f16": (TOL_SPLIT, 1e-8),
-                "f32": (1e-5, 1e-3)}
+                "f32": (1e-5, 1e-3), "tf32": (2e-3, 2e-2)}
 
 
 def test_precision_sweep_chi2048(ctx):
