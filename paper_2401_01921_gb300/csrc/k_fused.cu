@@ -12,7 +12,8 @@
 //   2. the CTA lists the nonzeros of every column of the packed B_g (the MPO
 //      product is mostly zeros) and two threads form each output row (even and
 //      odd columns), with the same FMA chains as the unfused skinny kernel
-//      (bit-identical);
+//      (bit-identical; a power-of-two first coefficient is applied on the
+//      integer units, tnx_first_term);
 //   3. every output element is stored through the descriptor of its column
 //      straight into the next step's packed operand (consecutive threads take
 //      consecutive p, that operand's contiguous leg), or the rows are written to
@@ -33,6 +34,7 @@ struct FusedSmem {
   FusedCol s_sc[FMAXN];           // output column descriptors
   unsigned char s_k[FMAXN][FMAXK];
   int s_cnt[FMAXN];
+  uint32_t s_p2[FMAXN];           // tnx_pow2_code of each column's first nonzero
 };
 
 __global__ void __launch_bounds__(FT, 6) fused_skinny_kernel(const GemmGroup* __restrict__ groups,
@@ -67,6 +69,7 @@ __global__ void __launch_bounds__(FT, 6) fused_skinny_kernel(const GemmGroup* __
       }
     }
     S.s_cnt[t] = c;
+    S.s_p2[t] = c ? tnx_pow2_code(S.s_v[t][0]) : 0u;
   }
   // gather: row r = t, q fastest; this thread takes columns half, half + 2, ...
   if (t < rows) {
@@ -95,7 +98,8 @@ __global__ void __launch_bounds__(FT, 6) fused_skinny_kernel(const GemmGroup* __
     for (int n = half; n < N; n += 2) {
       double acc = 0.0;
       const int c = S.s_cnt[n];
-      for (int e = 0; e < c; ++e) acc = fma(arow[S.s_k[n][e]], S.s_v[n][e], acc);
+      if (c > 0) acc = tnx_first_term(arow[S.s_k[n][0]], S.s_v[n][0], S.s_p2[n]);
+      for (int e = 1; e < c; ++e) acc = fma(arow[S.s_k[n][e]], S.s_v[n][e], acc);
       crow[n] = acc;
     }
   }

@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(128) gemm_skinny_kernel(const GemmGroup* __res
   __shared__ double s_v[64][SK_MAXK];          // nonzero B entries of each output column
   __shared__ unsigned char s_k[64][SK_MAXK];   // their k
   __shared__ int s_cnt[64];
+  __shared__ uint32_t s_p2[64];                // tnx_pow2_code of the first nonzero
   __shared__ double s_a[128][SK_MAXK + 1];     // the CTA's rows of A (padded: conflict-free)
   const GemmTile tl = tiles[blockIdx.x];
   const GemmGroup g = groups[tl.group];
@@ -109,6 +110,7 @@ __global__ void __launch_bounds__(128) gemm_skinny_kernel(const GemmGroup* __res
       }
     }
     s_cnt[threadIdx.x] = c;
+    s_p2[threadIdx.x] = c ? tnx_pow2_code(s_v[threadIdx.x][0]) : 0u;
   }
   const int m = tl.m0 + threadIdx.x;
   if (m < g.M) {
@@ -127,7 +129,8 @@ __global__ void __launch_bounds__(128) gemm_skinny_kernel(const GemmGroup* __res
   for (int n = 0; n < nn; ++n) {
     double acc = 0.0;
     const int c = s_cnt[n];
-    for (int e = 0; e < c; ++e) acc = fma(arow[s_k[n][e]], s_v[n][e], acc);
+    if (c > 0) acc = tnx_first_term(arow[s_k[n][0]], s_v[n][0], s_p2[n]);
+    for (int e = 1; e < c; ++e) acc = fma(arow[s_k[n][e]], s_v[n][e], acc);
     crow[n] = acc;
   }
 }

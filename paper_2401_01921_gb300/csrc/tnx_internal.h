@@ -136,6 +136,36 @@ struct MatchArgs {
 #ifdef __CUDACC__
 __device__ __forceinline__ void tnx_grid_dependency() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// The skinny (MPO) products list the nonzero entries v of each output column
+// of B and run acc = fma(a_k, v_k, acc) from acc = 0.  Their first term,
+// fma(a, v, 0.0), is an exact scaling when v is a power of two (every MPO
+// entry of the Heisenberg, XX and Hubbard chains is 0 or +-2^k), so it is
+// formed on the integer units: flip the sign, add k to the exponent field.
+// Zero, subnormal, infinite or out-of-range cases take the FMA; the result is
+// bit-identical either way.  code = tnx_pow2_code(v): (sign << 31) | (biased
+// exponent + 1), or 0 when v is not a normal power of two.
+__host__ __device__ __forceinline__ uint32_t tnx_pow2_code(double v) {
+  union {
+    double d;
+    unsigned long long u;
+  } x;
+  x.d = v;
+  const unsigned ex = (unsigned)((x.u >> 52) & 0x7FF);
+  if ((x.u & 0xFFFFFFFFFFFFFull) != 0 || ex == 0 || ex == 0x7FF) return 0u;
+  return (unsigned)(x.u >> 63) << 31 | (ex + 1u);
+}
+__device__ __forceinline__ double tnx_first_term(double a, double v, uint32_t code) {
+  if (code) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    const int e = (int)(code & 0xFFFFu) - 1024;   // unbiased exponent of v
+    if (ex > 0 && ex < 2047 && ex + e > 0 && ex + e < 2047)
+      return __longlong_as_double((long long)((b ^ ((unsigned long long)(code >> 31) << 63)) +
+                                              ((unsigned long long)(long long)e << 52)));
+  }
+  return fma(a, v, 0.0);
+}
+
 template <typename... KArgs, typename... Args>
 cudaError_t tnx_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                        Args&&... args) {
