@@ -20,7 +20,8 @@ beside the same trace served one request at a time in plain FP64;
 ``secondary`` holds the chi = 512 solve.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl tnx|reference]
-                  [--workload chi2048|chi512|dense32|batch256|serve] [--prec auto|split_bf16|f64|...]
+                  [--workload chi2048|chi512|dense32|batch256|serve|env2048|dmrg]
+                  [--prec auto|split_bf16|f64|...]
 
 --impl reference times the plain CPU FP64 oracle on the host (one thread,
 bounded sample) on the same metric.  With N > 1 (torchrun, NCCL) every rank
@@ -55,8 +56,8 @@ SPLIT_TRAFFIC = {
         (9305600, "profiles/split_gemm_heisenberg_u1_chi512.md",
          "1edccaadeb9ebab7b4ab4b062a986006f94f024ad0ed51f81a11861a747bc22f"),
     "heisenberg_u1_chi2048_d2_D5_sectorscaled_lanczos20":
-        (94286976, "profiles/split_gemm_heisenberg_u1_chi2048.md",
-         "1edccaadeb9ebab7b4ab4b062a986006f94f024ad0ed51f81a11861a747bc22f"),
+        (90648192, "profiles/split_gemm_heisenberg_u1_chi2048.md",
+         "d5df9e0149253a7e2d6740904704b9294f6c54a339beccf5d1b23dcdcdfe26d8"),
 }
 
 
@@ -441,6 +442,127 @@ def run_serve(args, torch, dev, tnx, I, build_network, rank, local):
         print(json.dumps(line))
 
 
+# ------------------------------------------------------------------ DMRG environment update (Sec. 11)
+def env_oracle_error(legs, lib_blocks: dict):
+    """Relative Frobenius error of the library's environment update against the oracle's
+    L.A.W.A^dagger on the same seeded inputs (outside every timed region)."""
+    import numpy as np
+
+    import tnx_inputs as I
+    from oracle import dmrg as odmrg
+    from oracle.symtensor import Bond as OB, BlockTensor, Symmetry, U1, fill_from_function
+    syms = (Symmetry(U1),)
+    T = {}
+    for n in I.ENV_NAMES:
+        bt = BlockTensor([OB.make(d, secs, syms) for d, secs in legs[n]])
+        T[n] = fill_from_function(bt, I.env_value_fn(n, legs))
+    ref = odmrg.env_left(T["L"], T["A"], T["W"])
+    num = den = 0.0
+    for k, b in ref.blocks.items():
+        a = lib_blocks.get(k)
+        num += float(np.sum((b - (a if a is not None else 0.0)) ** 2))
+        den += float(np.sum(b * b))
+    return (num / den) ** 0.5
+
+
+def run_env(args, torch, dev, tnx, I, dist, world, rank, local):
+    """The left environment update of a DMRG sweep, L'[b,w',b'] = sum L[a,w,a'] A[a,s,b]
+    W[w,s',s,w'] A^dagger[a',s',b'], at chi = 2048 (Heisenberg U(1): 41 -> 42 sectors), as one
+    network launch per step, in split BF16 and in native FP64; error against the oracle."""
+    from paper_2401_01921_gb300.heff import make_bonds
+    chi, n = 2048, 40
+    legs = I.env_bonds(chi, n)
+    ctx = tnx.Context(local)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    res, errs = {}, {}
+    for prec in ("split_bf16", "f64"):
+        net = tnx.Network(ctx, I.ENV_LEFT_SPEC)
+        T = {}
+        for name in I.ENV_NAMES:
+            T[name] = tnx.Tensor(ctx, make_bonds(ctx, legs[name], 1)).fill(I.env_value_fn(name, legs))
+            net.put(name, T[name])
+        T["Ad"] = T["A"].dagger()
+        net.put("Ad", T["Ad"])
+        net.set_order("sparse")
+        net.set_precision(prec)
+        out = net.launch([T["A"].bonds[2], T["W"].bonds[3], T["Ad"].bonds[2]])
+        flops = net.flops()
+        for _ in range(max(3, args.warmup)):
+            net.launch_into(out)
+        ctx.sync()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        times = []
+        with ClockSampler(local) as clk:
+            for _ in range(args.steps):
+                flush.zero_()
+                torch.cuda.synchronize(dev)
+                s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s_.record(ctx.stream)
+                net.launch_into(out)
+                e_.record(ctx.stream)
+                torch.cuda.synchronize(dev)
+                times.append(s_.elapsed_time(e_))
+        rate, ms = replica_rate(flops * args.steps, sum(times), dist, dev)
+        res[prec] = {"value": rate / 1e12, "ms": ms / args.steps, "flops": flops, "order": net.get_order(),
+                     "clocks": clk.summary()}
+        if rank == 0 and not args.no_accuracy:
+            errs[prec] = env_oracle_error(legs, out.block_dict())
+        del out, net, T
+    r = res["split_bf16"]
+    line = {"metric": "DMRG left-environment update useful TFLOP/s (split BF16 vs plain FP64)",
+            "value": r["value"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 via split_bf16 slices", "data": "synthetic",
+            "config": {"workload": "heisenberg_u1_env_left_chi2048", "chi": chi, "sectors": [41, 42], "D": 5,
+                       "useful_flops": r["flops"], "order": r["order"],
+                       "l2": "flushed (512 MiB write) before each timed step"},
+            "clocks": r["clocks"], "fp64_value": res["f64"]["value"], "fp64_ms_per_step": res["f64"]["ms"],
+            "speedup_vs_fp64": r["value"] / res["f64"]["value"],
+            "accuracy": {f"rel_fro_{k}": v for k, v in errs.items()}, "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ two-site DMRG sweeps (Sec. 11)
+def run_dmrg(args, torch, dev, tnx, I, rank, local):
+    """Two-site DMRG sweeps of the open XX chain (the paper's benchmark model, M_D = 4),
+    N = 40 sites, bond dimension raised 64 -> 128 -> 256 -> 512 (two sweeps each), H_eff
+    products in split BF16; the energy against the free-fermion closed form."""
+    import numpy as np
+
+    from paper_2401_01921_gb300.heff import make_bonds
+    nsites = 40
+    mpo = I.xx_mpo()
+    ctx = tnx.Context(local)
+    legs = [(1, mpo.bond_sectors), (1, I.SPIN_PHYS), (-1, I.SPIN_PHYS), (-1, mpo.bond_sectors)]
+    Wg = mpo.W_grouped()
+    W = tnx.Tensor(ctx, make_bonds(ctx, legs, 1)).fill(lambda c: Wg[c[0], c[1], c[2], c[3]])
+    d = tnx.Dmrg(ctx, nsites, W, mpo.channel_pos[mpo.left_row], mpo.channel_pos[mpo.right_col],
+                 [i % 2 for i in range(nsites)])
+    e = np.cos(np.pi * np.arange(1, nsites + 1) / (nsites + 1))
+    exact = float(np.sum(e[e < 0]))   # free fermions with hopping 1/2: fill the negative levels
+    sweeps = []
+    t0 = time.perf_counter()
+    for dim in (64, 128, 256, 512):
+        for _ in range(2):
+            r = d.sweep(dim, 0.0, LANCZOS_STEPS, "split_bf16")
+            sweeps.append({"maxdim": dim, "energy": r["energy"], "rel_err": abs(r["energy"] - exact) / abs(exact),
+                           "max_bond": r["max_bond"], "max_trunc_err": r["max_trunc_err"], "ms": r["ms"]})
+    total = time.perf_counter() - t0
+    last = sweeps[-1]
+    line = {"metric": "two-site DMRG sweep time (s) at bond dimension 512, XX chain N=40",
+            "value": last["ms"]["sweep"] / 1e3, "unit": "s", "n_gpus": 1, "steps": len(sweeps), "warmup": 0,
+            "ms_per_step": last["ms"]["sweep"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 via split_bf16 slices (H_eff); FP64 Lanczos vectors and SVD", "data": "synthetic",
+            "config": {"workload": "xx_chain_n40_dmrg_chi64to512", "nsites": nsites, "D": 4,
+                       "lanczos_steps": LANCZOS_STEPS, "exact_energy": exact},
+            "sweeps": sweeps, "total_s": total, "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 # ------------------------------------------------------------------ Lanczos solves
 def time_solves(torch, dev, tnx, ctx, net, T, evec, steps, warmup, flush, local, dist=None, prof_gemm=True):
     """Warm-up, then `steps` timed Lanczos solves (L2 flushed, untimed, before each),
@@ -581,6 +703,15 @@ def main():
 
     if args.workload == "serve":
         run_serve(args, torch, dev, tnx, I, build_network, rank, local)
+        return
+    if args.workload == "env2048":
+        run_env(args, torch, dev, tnx, I, dist, world, rank, local)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    if args.workload == "dmrg":
+        run_dmrg(args, torch, dev, tnx, I, rank, local)
         return
     if args.workload == "batch256":
         run_batch(args, torch, dev, tnx, I, build_network, dist, world, rank, local)

@@ -453,3 +453,47 @@ def heff_value_fn(wl: Workload, name: str, symmetric: bool = False):
         return v
 
     return fn
+
+
+# ----------------------------------------------------------------------------
+# The left environment update of a DMRG sweep (Sec. 11): inputs at bond dimension chi
+# ----------------------------------------------------------------------------
+
+ENV_LEFT_SPEC = (
+    "L: a, w, ap\n"
+    "A: a, s, b\n"
+    "W: w, sp, s, wp\n"
+    "Ad: ap, sp, bp\n"
+    "TOUT: b, wp, bp\n"
+)
+ENV_NAMES = ["L", "A", "W"]          # Ad is the Dagger of A (Sec. 6.4), made by each side itself
+ENV_SEEDS = {"L": (21, 1), "A": (22, 5)}
+
+
+def env_bonds(chi: int, n: int) -> dict:
+    """Legs of L[a OUT, w OUT, a' IN], A[a IN, s IN, b OUT] and W (the Heisenberg MPO):
+    a carries the binomial sector list of n (even 2Sz charges), b that of n + 1 (odd
+    charges), both summing to chi, so every block of A has s = +-1 between them."""
+    a = heisenberg_virtual_sectors(chi, n)
+    b = heisenberg_virtual_sectors(chi, n + 1)
+    M = heisenberg_mpo().bond_sectors
+    return {"L": [(OUT, a), (OUT, M), (IN, a)],
+            "A": [(IN, a), (IN, SPIN_PHYS), (OUT, b)],
+            "W": [(IN, M), (IN, SPIN_PHYS), (OUT, SPIN_PHYS), (OUT, M)]}
+
+
+def env_value_fn(name: str, legs: dict):
+    """N(0,1) for L and A from (seed, stream, row-major dense index); W: the grouped MPO."""
+    if name == "W":
+        Wg = heisenberg_mpo().W_grouped()
+        return lambda c: Wg[c[0], c[1], c[2], c[3]]
+    seed, stream = ENV_SEEDS[name]
+    dims = [sum(d for _, d in secs) for _, secs in legs[name]]
+
+    def fn(c):
+        f = np.zeros_like(np.asarray(c[0]), dtype=np.int64)
+        for x, dm in zip(c, dims):
+            f = f * dm + np.asarray(x, dtype=np.int64)
+        return normal_at(seed, stream, f)
+
+    return fn
