@@ -212,64 +212,61 @@ constexpr long long DIGIT_BIAS = 64LL * ((1LL << 42) - 1) / 127;
 
 // Slices of the packed operands, one CTA (8 warps) per work item.  Rows are
 // taken in groups of 8 (rows past an operand's end give zero slices); in a
-// warp, lane = (row in group) * 4 + (8-column group).  A job with long rows
-// (SliceJob::cta_mode) gives one group per item and the 8 warps share the
-// group; otherwise an item is 8 groups, one per warp.  For a group, first the
-// biased exponent of each row's largest |x| (lanes of a row scan every 4th
-// entry, the lanes and then the sharing warps combine), stored for the GEMM
-// epilogue; then the group's 32-wide K tiles are sliced, 8 entries per lane,
-// 16 bytes per slice per lane written in the tiled core-matrix layout the
-// GEMM copies in.
+// warp, lane = (row in group) * 4 + (8-column group).  A job gives each group
+// SliceJob::wpg warps (1, 2, 4 or 8: more for longer rows), so an item is
+// 8 / wpg groups.  For a group, first the biased exponent of each row's
+// largest |x| (lanes of a row scan every 4 * wpg-th entry's exponent field,
+// then the lanes and the group's warps combine), stored for the GEMM epilogue;
+// then the group's 32-wide K tiles are sliced, the warps of the group taking
+// every wpg-th tile, 8 entries per lane, 16 bytes per slice per lane written
+// in the tiled core-matrix layout the GEMM copies in.
 template <bool F16>
 __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restrict__ jobs,
                                                          const int2* __restrict__ items, int64_t total,
                                                          double* const* __restrict__ slots) {
   tnx_grid_dependency();
-  __shared__ unsigned long long s_max[8][8];
+  __shared__ int s_max[8][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int r8 = lane >> 2, kq = lane & 3;
   constexpr int F = MAXN * 7;   // six digits of 7 bits (checked by the launcher)
   for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
     const int2 item = items[w];   // (job, first 8-row group)
     const SliceJob& j = jobs[item.x];
-    const bool shared_group = j.cta_mode != 0;   // uniform over the CTA
+    const int wpg = j.wpg;                        // uniform over the CTA
+    const int sub = wid / wpg, wl = wid - sub * wpg;
     const int64_t ngroups = ((int64_t)j.rows + j.tile_rows - 1) / j.tile_rows * (j.tile_rows / 8);
-    const int64_t rg = shared_group ? item.y : (int64_t)item.y + wid;
+    const int64_t rg = (int64_t)item.y + sub;
     const int KT = (j.K + TK - 1) / TK;
     const int64_t row = rg * 8 + r8;
-    const bool live = row < j.rows;
+    const bool live = rg < ngroups && row < j.rows;
     const double* src = slots[j.src_slot] + j.src_off + row * j.ld;
-    // row exponent
-    const int kstart = shared_group ? wid * 4 + kq : kq, kstep = shared_group ? 32 : 4;
-    // eight independent loads in flight per lane, then a fixed-order max
-    unsigned long long mx = 0;
+    // row exponent: the largest exponent field; eight independent loads of the
+    // high words in flight per lane
+    const uint32_t* src_hi = (const uint32_t*)src + 1;
+    const int kstart = wl * 4 + kq, kstep = 4 * wpg;
+    int mx = 0;
     if (live)
       for (int k0 = kstart; k0 < j.K; k0 += 8 * kstep) {
-        unsigned long long b[8];
+        uint32_t h[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int k = k0 + u * kstep;
-          b[u] = k < j.K ? (__double_as_longlong(src[k]) & 0x7FFFFFFFFFFFFFFFull) : 0ull;
+          h[u] = k < j.K ? src_hi[2 * k] : 0u;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) mx = b[u] > mx ? b[u] : mx;
+        for (int u = 0; u < 8; ++u) mx = max(mx, (int)((h[u] >> 20) & 0x7FFu));
       }
 #pragma unroll
-    for (int o = 1; o < 4; o <<= 1) {
-      const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
-      mx = v > mx ? v : mx;
-    }
-    if (shared_group) {
+    for (int o = 1; o < 4; o <<= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (wpg > 1) {
       if (kq == 0) s_max[wid][r8] = mx;
       __syncthreads();
-      mx = 0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) mx = s_max[q][r8] > mx ? s_max[q][r8] : mx;
+      for (int q = sub * wpg; q < sub * wpg + wpg; ++q) mx = max(mx, s_max[q][r8]);
       __syncthreads();   // s_max is rewritten by the next item
     }
-    if (rg >= ngroups) continue;   // a warp past the job's last group (8-group items)
-    const int eb_r = (int)(mx >> 52);
-    if (live && kq == 0 && (!shared_group || wid == 0)) ((int32_t*)slots[j.exp_slot])[j.exp_off + row] = eb_r;
+    if (rg >= ngroups) continue;   // a group past the job's last one
+    const int eb_r = mx;
+    if (live && kq == 0 && wl == 0) ((int32_t*)slots[j.exp_slot])[j.exp_off + row] = eb_r;
     const int tile_rows = j.tile_rows;
     const int64_t mt = row / tile_rows;
     const int rin = (int)(row % tile_rows);
@@ -278,7 +275,7 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restr
     const int64_t inner = (int64_t)(rin >> 3) * 512 + kq * 128 + (rin & 7) * 16;
     // Digits of one K tile (8 entries per lane); the loads of the lane's next
     // tile are issued before the current one is converted.
-    const int kt0 = shared_group ? wid : 0, kts = shared_group ? 8 : 1;
+    const int kt0 = wl, kts = wpg;
     unsigned long long cur[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {

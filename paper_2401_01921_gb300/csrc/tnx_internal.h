@@ -70,7 +70,7 @@ struct GemmTile {
 // the tcgen05 no-swizzle K-major core-matrix layout, tile by tile.
 struct SliceJob {
   int32_t src_slot, dst_slot;     // dst: byte buffer slot (uint16 slices)
-  int32_t exp_slot, cta_mode;     // int32 row exponents; cta_mode: one 8-row group per CTA (long rows)
+  int32_t exp_slot, wpg;          // int32 row exponents; warps per 8-row group (1, 2, 4 or 8)
   int64_t src_off, dst_off_bytes, exp_off;
   int32_t rows, K, ld, tile_rows; // tile_rows: 128 (A) or 64 (B)
 };
@@ -240,7 +240,7 @@ cudaError_t tnx_launch_gemm_skinny(const GemmGroup* groups, const GemmTile* tile
 cudaError_t tnx_launch_gemm_f32(const GemmGroup* groups, const GemmTile* tiles, int ntiles,
                                 double* const* slots, cudaStream_t st);
 // row exponents, then the slices; items: (job, first 8-row group) per CTA work
-// item (one group when the job's cta_mode is set, else 8 groups)
+// item, which covers 8 / wpg groups of that job
 cudaError_t tnx_launch_slices(const SliceJob* jobs, const int2* items, int64_t total_items, int nslice, int beta,
                               int f16, double* const* slots, cudaStream_t st);
 // grid <= 0 or >= ntiles: one CTA per tile; otherwise a persistent grid of `grid` CTAs.

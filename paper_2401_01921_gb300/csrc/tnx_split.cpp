@@ -14,24 +14,19 @@ constexpr int TM = 128, TK = 32;
 constexpr int64_t KMAX = 8192;   // the 64-bit fixed-point accumulator is exact up to this K
 }
 
-// Work items of one slicing launch (k_split.cu), one CTA each: with few
-// 8-row groups in the launch, every job shares each group among the 8 warps
-// of a CTA (more CTAs, shorter per-warp loops); with many, jobs whose rows
-// span at most 8 K tiles give one group to each warp, 8 groups per item.
+// Work items of one slicing launch (k_split.cu), one CTA (8 warps) each: a
+// job gives each 8-row group 1, 2, 4 or 8 warps by the number of its 32-wide
+// K tiles (a warp then takes about two of them, at most every eighth), and an
+// item holds 8 / wpg consecutive groups of one job.
 std::vector<int2> tnx_slice_schedule(std::vector<SliceJob>& jobs) {
-  auto groups_of = [](const SliceJob& j) {
-    return ((int64_t)j.rows + j.tile_rows - 1) / j.tile_rows * (j.tile_rows / 8);
-  };
-  int64_t groups = 0;
-  for (const SliceJob& j : jobs) groups += groups_of(j);
-  const bool many = groups >= 4 * 8 * 152;
   std::vector<int2> items;
   for (size_t q = 0; q < jobs.size(); ++q) {
     SliceJob& j = jobs[q];
-    j.cta_mode = (!many || (j.K + TK - 1) / TK > 8) ? 1 : 0;
-    const int64_t g = groups_of(j);
+    const int KT = (j.K + TK - 1) / TK;
+    j.wpg = KT >= 16 ? 8 : KT >= 8 ? 4 : KT >= 3 ? 2 : 1;
+    const int64_t g = ((int64_t)j.rows + j.tile_rows - 1) / j.tile_rows * (j.tile_rows / 8);
     if (g > INT32_MAX) fail(TNX_ERR_UNSUPPORTED, "slicing job above 2^31 row groups");
-    for (int64_t r = 0; r < g; r += j.cta_mode ? 1 : 8) items.push_back(make_int2((int)q, (int)r));
+    for (int64_t r = 0; r < g; r += 8 / j.wpg) items.push_back(make_int2((int)q, (int)r));
   }
   return items;
 }
@@ -41,7 +36,7 @@ std::vector<int2> tnx_tf32_schedule(std::vector<SliceJob>& jobs) {
   std::vector<int2> items;
   for (size_t q = 0; q < jobs.size(); ++q) {
     SliceJob& j = jobs[q];
-    j.cta_mode = 0;
+    j.wpg = 1;
     const int64_t g = ((int64_t)j.rows + j.tile_rows - 1) / j.tile_rows * (j.tile_rows / 8);
     if (g > INT32_MAX) fail(TNX_ERR_UNSUPPORTED, "TF32 operand above 2^31 row groups");
     for (int64_t r = 0; r < g; r += 8) items.push_back(make_int2((int)q, (int)r));
