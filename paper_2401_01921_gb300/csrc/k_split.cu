@@ -220,7 +220,17 @@ constexpr long long DIGIT_BIAS = 64LL * ((1LL << 42) - 1) / 127;
 // then the group's 32-wide K tiles are sliced, the warps of the group taking
 // every wpg-th tile, 8 entries per lane, 16 bytes per slice per lane written
 // in the tiled core-matrix layout the GEMM copies in.
-template <bool F16>
+// With KX (K balancing), entry k counts as x * 2^(kx_sign * E_k), E_k the
+// exponent of column k's largest entry in A: A's columns are scaled by 2^-E_k
+// and B's rows by 2^E_k, exactly, so the product is unchanged while a row of
+// A (column of B) whose entries scale differently along K keeps its bits.
+// Only exponents move: the digits of x * 2^s are those of x with the
+// effective exponent E + s.
+__device__ __forceinline__ int kx_shift(int raw, int sign) {
+  return raw > 0 ? sign * (raw - 1023) : 0;   // raw: biased exponent, 0 for a zero column
+}
+
+template <bool F16, bool KX>
 __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restrict__ jobs,
                                                          const int2* __restrict__ items, int64_t total,
                                                          double* const* __restrict__ slots) {
@@ -240,21 +250,32 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restr
     const int64_t row = rg * 8 + r8;
     const bool live = rg < ngroups && row < j.rows;
     const double* src = slots[j.src_slot] + j.src_off + row * j.ld;
-    // row exponent: the largest exponent field; eight independent loads of the
-    // high words in flight per lane
+    // row exponent: the largest (effective) exponent field; eight independent
+    // loads of the high words in flight per lane
     const uint32_t* src_hi = (const uint32_t*)src + 1;
+    const int32_t* kxp = KX ? (const int32_t*)slots[j.kx_slot] + j.kx_off : nullptr;
     const int kstart = wl * 4 + kq, kstep = 4 * wpg;
-    int mx = 0;
+    constexpr int ZROW = KX ? -(1 << 20) : 0;   // no nonzero entry
+    int mx = ZROW;
     if (live)
       for (int k0 = kstart; k0 < j.K; k0 += 8 * kstep) {
         uint32_t h[8];
+        int sx[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int k = k0 + u * kstep;
           h[u] = k < j.K ? src_hi[2 * k] : 0u;
+          if constexpr (KX) sx[u] = k < j.K ? kxp[k] : 0;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) mx = max(mx, (int)((h[u] >> 20) & 0x7FFu));
+        for (int u = 0; u < 8; ++u) {
+          const int eb = (int)((h[u] >> 20) & 0x7FFu);
+          if constexpr (KX) {
+            if (eb != 0) mx = max(mx, eb + kx_shift(sx[u], j.kx_sign));
+          } else {
+            mx = max(mx, eb);
+          }
+        }
       }
 #pragma unroll
     for (int o = 1; o < 4; o <<= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -266,7 +287,8 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restr
     }
     if (rg >= ngroups) continue;   // a group past the job's last one
     const int eb_r = mx;
-    if (live && kq == 0 && wl == 0) ((int32_t*)slots[j.exp_slot])[j.exp_off + row] = eb_r;
+    const bool nonzero_row = eb_r != ZROW;
+    if (live && kq == 0 && wl == 0) ((int32_t*)slots[j.exp_slot])[j.exp_off + row] = nonzero_row ? eb_r : 0;
     const int tile_rows = j.tile_rows;
     const int64_t mt = row / tile_rows;
     const int rin = (int)(row % tile_rows);
@@ -275,19 +297,42 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restr
     const int64_t inner = (int64_t)(rin >> 3) * 512 + kq * 128 + (rin & 7) * 16;
     // Digits of one K tile (8 entries per lane); the loads of the lane's next
     // tile are issued before the current one is converted.
+    // With KX the K-balancing words of the tile come along (each group's region
+    // is padded to whole K tiles and 16-byte aligned).
     const int kt0 = wl, kts = wpg;
     unsigned long long cur[8];
+    int4 ckx[2];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int k = kt0 * TK + kq * 8 + e;
       cur[e] = (live && kt0 < KT && k < j.K) ? (unsigned long long)__double_as_longlong(src[k]) : 0ull;
     }
+    if constexpr (KX) {
+      const bool ok = live && kt0 < KT;
+      ckx[0] = ok ? *(const int4*)(kxp + kt0 * TK + kq * 8) : make_int4(0, 0, 0, 0);
+      ckx[1] = ok ? *(const int4*)(kxp + kt0 * TK + kq * 8 + 4) : make_int4(0, 0, 0, 0);
+    }
     for (int kt = kt0; kt < KT; kt += kts) {
       unsigned long long nxt[8];
+      int4 nkx[2];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int k = (kt + kts) * TK + kq * 8 + e;
         nxt[e] = (live && kt + kts < KT && k < j.K) ? (unsigned long long)__double_as_longlong(src[k]) : 0ull;
+      }
+      if constexpr (KX) {
+        const bool ok = live && kt + kts < KT;
+        nkx[0] = ok ? *(const int4*)(kxp + (kt + kts) * TK + kq * 8) : make_int4(0, 0, 0, 0);
+        nkx[1] = ok ? *(const int4*)(kxp + (kt + kts) * TK + kq * 8 + 4) : make_int4(0, 0, 0, 0);
+      }
+      int sh[8];
+      if constexpr (KX) {
+        const int raw[8] = {ckx[0].x, ckx[0].y, ckx[0].z, ckx[0].w, ckx[1].x, ckx[1].y, ckx[1].z, ckx[1].w};
+#pragma unroll
+        for (int e = 0; e < 8; ++e) sh[e] = kx_shift(raw[e], j.kx_sign);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) sh[e] = 0;
       }
       uint32_t sl[MAXN][4];
 #pragma unroll
@@ -299,9 +344,9 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restr
           const int eb = (int)((bits >> 52) & 0x7FF);
           // |x| 2^(F-E-2) rounded half up: m53 * 2^-rs with rs = 54 - F + E_r - E >= 12
           unsigned long long fix = 0;
-          if (eb != 0 && eb_r != 0) {
+          if (eb != 0 && nonzero_row) {
             const unsigned long long m53 = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-            const int rs = 54 - F + (eb_r - eb);
+            const int rs = 54 - F + (eb_r - (eb + sh[e + h]));
             fix = rs >= 64 ? 0ull : ((m53 >> (rs - 1)) + 1ull) >> 1;
           }
           // Balanced base-128 digits of the signed value v (|v| <= 2^41): with
@@ -341,7 +386,57 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restr
       }
 #pragma unroll
       for (int e = 0; e < 8; ++e) cur[e] = nxt[e];
+      if constexpr (KX) {
+        ckx[0] = nkx[0];
+        ckx[1] = nkx[1];
+      }
     }
+  }
+}
+
+// Zeroes the K-balancing words of every job (whole K tiles), one CTA per job.
+__global__ void kexp_zero_kernel(const KexpJob* __restrict__ jobs, int njobs, double* const* __restrict__ slots) {
+  tnx_grid_dependency();
+  for (int q = blockIdx.x; q < njobs; q += gridDim.x) {
+    const KexpJob& j = jobs[q];
+    int32_t* kx = (int32_t*)slots[j.kx_slot] + j.kx_off;
+    const int n = (j.K + TK - 1) / TK * TK;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) kx[i] = 0;
+  }
+}
+
+// Column maxima of the exponent fields of A: an item is 32 K indices (one per
+// lane) by 64 rows (eight per warp, loads in flight together); the warps
+// combine in shared memory and one atomicMax per K index leaves the CTA.
+__global__ void __launch_bounds__(256) kexp_kernel(const KexpJob* __restrict__ jobs, const int4* __restrict__ items,
+                                                   int64_t nitems, double* const* __restrict__ slots) {
+  tnx_grid_dependency();
+  __shared__ int s_mx[8][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t w = blockIdx.x; w < nitems; w += gridDim.x) {
+    const int4 it = items[w];   // (job, first K index, first row, -)
+    const KexpJob& j = jobs[it.x];
+    const int k = it.y + lane;
+    int mx = 0;
+    if (k < j.K) {
+      const uint32_t* hi = (const uint32_t*)(slots[j.src_slot] + j.src_off) + 1;
+      uint32_t h[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int r = it.z + wid + 8 * u;
+        h[u] = r < j.rows ? hi[2 * ((int64_t)r * j.ld + k)] : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) mx = max(mx, (int)((h[u] >> 20) & 0x7FFu));
+    }
+    s_mx[wid][lane] = mx;
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+      for (int q = 1; q < 8; ++q) mx = max(mx, s_mx[q][lane]);
+      if (k < j.K && mx > 0) atomicMax((int32_t*)slots[j.kx_slot] + j.kx_off + k, mx);
+    }
+    __syncthreads();
   }
 }
 
@@ -630,6 +725,9 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
         // the row-wise writes and the column-wise reads free of bank conflicts.
         __syncwarp();
         double* cbase = slots[gr.c_slot] + gr.c_off;
+        // a folded output relayout: column descriptors, destination = the network's output
+        const FinalCol* fcol = gr.fc_slot >= 0 ? (const FinalCol*)slots[gr.fc_slot] + gr.fc_off : nullptr;
+        double* obase = gr.fc_slot >= 0 ? slots[gr.out_slot] : nullptr;
         const int r0 = tl.m0 + sub * 32;
 #pragma unroll
         for (int c4 = 0; c4 < ECOLS / 4; ++c4) {
@@ -645,10 +743,19 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
           }
           __syncwarp();
           const int cc = lane & 3, col = tl.n0 + cb + c4 * 4 + cc;
+          if (fcol) {
+            const FinalCol d = col < gr.N ? fcol[col] : FinalCol{-1, 0};
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int rr = q * 8 + (lane >> 2), r = r0 + rr;
-            if (r < gr.M && col < gr.N) cbase[(int64_t)r * gr.ldc + col] = stg[rr][cc ^ ((rr >> 2) & 3)];
+            for (int q = 0; q < 4; ++q) {
+              const int rr = q * 8 + (lane >> 2), r = r0 + rr;
+              if (r < gr.M && d.off >= 0) obase[d.off + (int64_t)r * d.stride] = stg[rr][cc ^ ((rr >> 2) & 3)];
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int rr = q * 8 + (lane >> 2), r = r0 + rr;
+              if (r < gr.M && col < gr.N) cbase[(int64_t)r * gr.ldc + col] = stg[rr][cc ^ ((rr >> 2) & 3)];
+            }
           }
           __syncwarp();
         }
@@ -664,19 +771,34 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
 }  // namespace
 
 cudaError_t tnx_launch_slices(const SliceJob* jobs, const int2* items, int64_t total_items, int nslice, int beta,
-                              int f16, double* const* slots, cudaStream_t st) {
+                              int f16, double* const* slots, cudaStream_t st, int use_kx) {
   if (total_items <= 0) return cudaSuccess;
   if (nslice != MAXN || beta != 7) return cudaErrorInvalidValue;   // the digit code is specialised
   int64_t blocks = total_items;
   if (blocks > 152 * 8) blocks = 152 * 8;
   {
-    const cudaError_t le = f16 ? tnx_launch(slice_rows_kernel<true>, dim3((int)blocks), dim3(256), 0, st,
-                                            jobs, items, total_items, slots)
-                               : tnx_launch(slice_rows_kernel<false>, dim3((int)blocks), dim3(256), 0, st,
-                                            jobs, items, total_items, slots);
+    const dim3 g((int)blocks), b(256);
+    const cudaError_t le =
+        f16 ? (use_kx ? tnx_launch(slice_rows_kernel<true, true>, g, b, 0, st, jobs, items, total_items, slots)
+                      : tnx_launch(slice_rows_kernel<true, false>, g, b, 0, st, jobs, items, total_items, slots))
+            : (use_kx ? tnx_launch(slice_rows_kernel<false, true>, g, b, 0, st, jobs, items, total_items, slots)
+                      : tnx_launch(slice_rows_kernel<false, false>, g, b, 0, st, jobs, items, total_items, slots));
     if (le != cudaSuccess) return le;
   }
   tnx_note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tnx_launch_kexp(const KexpJob* jobs, int njobs, const int4* items, int64_t nitems, double* const* slots,
+                            cudaStream_t st) {
+  if (njobs <= 0 || nitems <= 0) return cudaSuccess;
+  cudaError_t le = tnx_launch(kexp_zero_kernel, dim3(njobs < 1024 ? njobs : 1024), dim3(256), 0, st, jobs, njobs,
+                              slots);
+  if (le != cudaSuccess) return le;
+  const int64_t blocks = nitems < 152 * 8 ? nitems : 152 * 8;
+  le = tnx_launch(kexp_kernel, dim3((int)blocks), dim3(256), 0, st, jobs, items, nitems, slots);
+  if (le != cudaSuccess) return le;
+  tnx_note_launch(2);
   return cudaGetLastError();
 }
 

@@ -17,7 +17,9 @@
 //    pad index pairs with nobody).  One launch per round over the pairs of
 //    every block; a pair whose |gamma| is below 1e-15 sqrt(alpha beta) is left
 //    as it is; each launch records the largest |gamma| / sqrt(alpha beta) it
-//    met, and the host stops after a sweep whose largest value is small;
+//    met, and the host stops after a sweep whose largest value is small
+//    (jacobi_coop_kernel runs all rounds and sweeps in one cooperative launch
+//    with grid barriers between rounds, when the device allows it);
 //  * then sigma_p = |x_p|, and X = J M^T (or J M): the singular vectors are
 //    x_p / sigma_p on one side and the rows of J on the other.
 // All arithmetic is FP64.  Block reductions use a fixed order (deterministic).
@@ -124,6 +126,130 @@ __global__ void __launch_bounds__(JT) jacobi_round_kernel(const SvdGroup* __rest
   }
 }
 
+// All sweeps of every block in one cooperative launch (all CTAs resident at
+// once, which the launch checks): each warp of the grid takes pairs of a
+// round across every block (pair i of round k as in jacobi_round_kernel), and
+// a grid barrier separates the rounds.  After each sweep the CTAs read the largest relative
+// off-diagonal of that sweep (offmax[sweep], zeroed by the host) behind a
+// barrier and all stop together once it is at most tol.  The barrier is a
+// counter plus a generation word; every wait on it is bounded (about a second
+// of clock): on expiry the CTA sets *status and leaves, and so do the others
+// at their next barrier.  sweeps_out[0] receives the number of sweeps run.
+constexpr long long BAR_LIMIT = 2000000000LL;
+
+__device__ bool grid_barrier(unsigned int* count, volatile unsigned int* gen, int* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = *(volatile int*)status == 0;
+    const unsigned int g = *gen;
+    __threadfence();
+    if (ok) {
+      if (atomicAdd(count, 1u) == gridDim.x - 1) {
+        *count = 0;
+        __threadfence();
+        atomicAdd((unsigned int*)gen, 1u);
+      } else {
+        const long long t0 = clock64();
+        while (*gen == g) {
+          if (*(volatile int*)status != 0) { ok = 0; break; }
+          if (clock64() - t0 > BAR_LIMIT) {
+            atomicExch(status, 1);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  // butterfly: every lane ends with the same bits (each step adds two partial
+  // sums, which commutes exactly)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(JT) jacobi_coop_kernel(const SvdGroup* __restrict__ groups,
+                                                         const int2* __restrict__ slots, int nslots, int maxcp,
+                                                         int max_sweeps, double tol, unsigned long long* offmax,
+                                                         unsigned int* bar, int* status, int* sweeps_out) {
+  // one warp per pair: the pairs of a round run side by side over the whole grid
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (JT / 32) + (threadIdx.x >> 5), nwarps = gridDim.x * (JT / 32);
+  int sw = 0;
+  bool ok = true;
+  while (ok && sw < max_sweeps) {
+    for (int round = 0; round < maxcp - 1 && ok; ++round) {
+      double off_w = 0.0;
+      for (int si = gw; si < nslots; si += nwarps) {
+        const int2 sl = slots[si];
+        const SvdGroup g = groups[sl.x];
+        const int cp = g.c + (g.c & 1);
+        if (cp < 2) continue;
+        const int kk = round % (cp - 1);
+        const int i = sl.y;
+        int p, q;
+        if (i == 0) {
+          p = kk;
+          q = cp - 1;
+        } else {
+          p = (kk + i) % (cp - 1);
+          q = (kk - i + cp - 1) % (cp - 1);
+        }
+        if (p > q) { const int t = p; p = q; q = t; }
+        if (q >= g.c) continue;         // the pad index
+        double* xp = g.X + (int64_t)p * g.r;
+        double* xq = g.X + (int64_t)q * g.r;
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int64_t e = lane; e < g.r; e += 32) {
+          const double u = xp[e], v = xq[e];
+          a = fma(u, u, a);
+          b = fma(v, v, b);
+          c = fma(u, v, c);
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        c = warp_sum(c);
+        if (!(a > 0.0 && b > 0.0)) continue;
+        const double o = fabs(c) / sqrt(a * b);
+        off_w = fmax(off_w, o);
+        if (o <= 1e-15) continue;
+        const double zeta = (b - a) / (2.0 * c);
+        const double az = fabs(zeta);
+        double t = az > 1e100 ? 0.5 / az : 1.0 / (az + sqrt(1.0 + az * az));
+        if (zeta < 0.0) t = -t;
+        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        for (int64_t e = lane; e < g.r; e += 32) {
+          const double u = xp[e], v = xq[e];
+          xp[e] = cs * u - sn * v;
+          xq[e] = sn * u + cs * v;
+        }
+        double* jp = g.J + (int64_t)p * g.c;
+        double* jq = g.J + (int64_t)q * g.c;
+        for (int e = lane; e < g.c; e += 32) {
+          const double u = jp[e], v = jq[e];
+          jp[e] = cs * u - sn * v;
+          jq[e] = sn * u + cs * v;
+        }
+      }
+      if (lane == 0 && off_w > 0.0) atomicMax(&offmax[sw], (unsigned long long)__double_as_longlong(off_w));
+      ok = grid_barrier(bar, bar + 1, status);
+    }
+    if (!ok) break;
+    const double off = __longlong_as_double((long long)*(volatile unsigned long long*)&offmax[sw]);
+    ++sw;
+    if (off <= tol) break;   // every warp reads the same value behind the last barrier
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) sweeps_out[0] = sw;
+}
+
 // J = identity for every group (one CTA per group row block)
 __global__ void jacobi_init_kernel(const SvdGroup* __restrict__ groups, int ngroups) {
   tnx_grid_dependency();
@@ -214,6 +340,28 @@ cudaError_t tnx_launch_jacobi_round(const SvdGroup* groups, const int2* slots, i
   if (le != cudaSuccess) return le;
   tnx_note_launch(1);
   return cudaGetLastError();
+}
+
+cudaError_t tnx_launch_jacobi_coop(const SvdGroup* groups, const int2* slots, int nslots, int maxcp, int max_sweeps,
+                                   double tol, unsigned long long* offmax, unsigned int* bar, int* status,
+                                   int* sweeps_out, cudaStream_t st) {
+  if (nslots <= 0 || maxcp < 2) return cudaSuccess;
+  int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel, JT, 0);
+  if (e != cudaSuccess) return e;
+  if (!coop || per_sm < 1) return cudaErrorNotSupported;
+  int grid = nsm * (per_sm < 4 ? per_sm : 4);
+  const int need = (nslots + JT / 32 - 1) / (JT / 32);   // one warp per pair of a round
+  if (grid > need) grid = need;
+  void* args[] = {(void*)&groups, (void*)&slots, (void*)&nslots, (void*)&maxcp, (void*)&max_sweeps, (void*)&tol,
+                  (void*)&offmax, (void*)&bar, (void*)&status, (void*)&sweeps_out};
+  e = cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, dim3(grid), dim3(JT), args, 0, st);
+  if (e != cudaSuccess) return e;
+  tnx_note_launch(1);
+  return cudaSuccess;
 }
 
 cudaError_t tnx_launch_vector_norms(const SvdGroup* groups, const int2* vecs, int nvec, cudaStream_t st) {

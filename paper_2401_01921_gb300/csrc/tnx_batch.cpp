@@ -24,6 +24,10 @@ struct BStep {
   GemmTile *dT = nullptr, *dTs = nullptr;
   int nt = 0, nts = 0;
   StepPlan::Jobs jobs;
+  KexpJob* dKJ = nullptr;       // K balancing of the split steps (every launch: all operands are new)
+  int nkj = 0;
+  int4* dKI = nullptr;
+  int64_t nki = 0;
   SplitGroup* dSG = nullptr;
   GemmTile* dST = nullptr;
   int nst = 0;
@@ -108,7 +112,8 @@ void enqueue_batch(tnx_batch& B, cudaStream_t st) {
     } else {
       if (s.jobs.n) {
         ProfScope ps(c, st, TNX_KC_SLICE, (double)s.jobs.elems * (16.0 + 2.0 * B.nslice));
-        CUDA_CHECK(tnx_launch_slices(s.jobs.d, s.jobs.items, s.jobs.nitems, B.nslice, B.beta, f16, B.d_slots, st));
+        CUDA_CHECK(tnx_launch_kexp(s.dKJ, s.nkj, s.dKI, s.nki, B.d_slots, st));
+        CUDA_CHECK(tnx_launch_slices(s.jobs.d, s.jobs.items, s.jobs.nitems, B.nslice, B.beta, f16, B.d_slots, st, 1));
       }
       ProfScope ps(c, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
       CUDA_CHECK(tnx_launch_gemm_split(s.dSG, s.dST, s.nst, B.nslice, B.beta, f16, B.d_slots, c->d_status, st,
@@ -181,6 +186,7 @@ extern "C" tnx_status tnx_batch_create(tnx_ctx* ctx, int n, tnx_network* const* 
       std::vector<GemmGroup> gg;
       std::vector<GemmTile> tt, ts;
       std::vector<SliceJob> jobs;
+      std::vector<KexpJob> kjobs;
       std::vector<SplitGroup> sg;
       std::vector<GemmTile> st;
       for (size_t i = 0; i < B->plans.size(); ++i) {
@@ -204,7 +210,13 @@ extern "C" tnx_status tnx_batch_create(tnx_ctx* ctx, int n, tnx_network* const* 
             j.src_slot = shift_slot(j.src_slot, b);
             j.dst_slot = shift_slot(j.dst_slot, b);
             j.exp_slot = shift_slot(j.exp_slot, b);
+            j.kx_slot = shift_slot(j.kx_slot, b);
             jobs.push_back(j);
+          }
+          for (KexpJob k : sp.hKJ) {
+            k.src_slot = shift_slot(k.src_slot, b);
+            k.kx_slot = shift_slot(k.kx_slot, b);
+            kjobs.push_back(k);
           }
           bs.jobs.elems += sp.jobsAll.elems;
           for (SplitGroup g : sp.hSG) {
@@ -235,6 +247,11 @@ extern "C" tnx_status tnx_batch_create(tnx_ctx* ctx, int n, tnx_network* const* 
         bs.jobs.nitems = (int64_t)items.size();
         bs.jobs.d = B->upload(jobs);
         bs.jobs.items = B->upload(items);
+        const std::vector<int4> kitems = tnx_kexp_items(kjobs);
+        bs.dKJ = B->upload(kjobs);
+        bs.nkj = (int)kjobs.size();
+        bs.dKI = B->upload(kitems);
+        bs.nki = (int64_t)kitems.size();
         bs.dSG = B->upload(sg);
         bs.dST = B->upload(st);
         bs.nst = (int)st.size();

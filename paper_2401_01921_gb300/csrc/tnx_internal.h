@@ -73,15 +73,34 @@ struct SliceJob {
   int32_t exp_slot, wpg;          // int32 row exponents; warps per 8-row group (1, 2, 4 or 8)
   int64_t src_off, dst_off_bytes, exp_off;
   int32_t rows, K, ld, tile_rows; // tile_rows: 128 (A) or 64 (B)
+  int32_t kx_slot, kx_sign;       // K balancing: int32 per K index (biased exponent of the
+  int64_t kx_off;                 // column maximum of A), applied as 2^(kx_sign * E)
+};
+
+// K balancing of a split product: for every K index k of a charge group, the
+// largest exponent field over the rows of the packed A (atomicMax into
+// zeroed int32 words).  Items: (job, first K index, first row), 32 K indices
+// by 64 rows each.
+struct KexpJob {
+  int32_t src_slot, kx_slot;
+  int64_t src_off, kx_off;
+  int32_t rows, K, ld, pad0;
 };
 
 // Split GEMM group: slices of A (tile_rows 128) and B (tile_rows 64) plus
 // per-row / per-column exponents; output FP64 row-major.
 struct SplitGroup {
   int32_t a_slot, b_slot, c_slot, ea_slot;
-  int32_t eb_slot, pad0, pad1, pad2;
+  int32_t eb_slot, out_slot, fc_slot, fc_off;   // fc_slot >= 0: the epilogue writes the network's output
   int64_t a_off_bytes, b_off_bytes, c_off, ea_off, eb_off;
   int32_t M, N, K, ldc;
+};
+
+// Output relayout folded into the last product's epilogue: column c of a
+// charge group goes to out[off + r * stride] for its rows r (off < 0: the
+// column is not part of the output).
+struct FinalCol {
+  int64_t off, stride;
 };
 
 // ---------------------------------------------------------------------------
@@ -242,7 +261,10 @@ cudaError_t tnx_launch_gemm_f32(const GemmGroup* groups, const GemmTile* tiles, 
 // row exponents, then the slices; items: (job, first 8-row group) per CTA work
 // item, which covers 8 / wpg groups of that job
 cudaError_t tnx_launch_slices(const SliceJob* jobs, const int2* items, int64_t total_items, int nslice, int beta,
-                              int f16, double* const* slots, cudaStream_t st);
+                              int f16, double* const* slots, cudaStream_t st, int use_kx = 0);
+// zero the K-balancing words of every job, then their column maxima
+cudaError_t tnx_launch_kexp(const KexpJob* jobs, int njobs, const int4* items, int64_t nitems, double* const* slots,
+                            cudaStream_t st);
 // grid <= 0 or >= ntiles: one CTA per tile; otherwise a persistent grid of `grid` CTAs.
 // tn: tile width (B rows per tile), 64 or 32; the B slices must be tiled with the same width.
 cudaError_t tnx_launch_gemm_split(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int nslice,
@@ -289,6 +311,11 @@ struct Copy2D {
 cudaError_t tnx_launch_jacobi_init(const SvdGroup* groups, int ngroups, cudaStream_t st);
 // round r of a sweep over slots (group, pair index); maxoff gets the largest
 // |x_p . x_q| / (|x_p| |x_q|) met, as the bits of a non-negative double
+// every round and sweep in one cooperative launch; offmax[max_sweeps], bar[2]
+// and status zeroed by the caller; cudaErrorNotSupported without cooperative launch
+cudaError_t tnx_launch_jacobi_coop(const SvdGroup* groups, const int2* slots, int nslots, int maxcp, int max_sweeps,
+                                   double tol, unsigned long long* offmax, unsigned int* bar, int* status,
+                                   int* sweeps_out, cudaStream_t st);
 cudaError_t tnx_launch_jacobi_round(const SvdGroup* groups, const int2* slots, int nslots, int round,
                                     unsigned long long* maxoff, cudaStream_t st);
 cudaError_t tnx_launch_vector_norms(const SvdGroup* groups, const int2* vecs, int nvec, cudaStream_t st);

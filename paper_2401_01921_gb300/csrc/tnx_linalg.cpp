@@ -170,12 +170,36 @@ void tnx_svd_run(tnx_tensor* t, int rowrank, int64_t keepdim, double err, const 
   CUDA_CHECK(cudaMemsetAsync(dX, 0, (size_t)std::max<int64_t>(nX, 1) * 8, st));
   CUDA_CHECK(tnx_launch_copy2d(dgather, (int)gather.size(), st));
   CUDA_CHECK(tnx_launch_jacobi_init(dg, ngr, st));
-  // ---- sweeps until the largest relative off-diagonal met in a sweep is small
-  unsigned long long* dmax = (unsigned long long*)MO.p;
-  unsigned long long* hmax = (unsigned long long*)ctx->pinned;
+  // ---- sweeps until the largest relative off-diagonal met in a sweep is small:
+  // one cooperative launch for everything; without it, one launch per round
+  constexpr int MAX_SWEEPS = 60;
   const int rounds = maxcp - 1;
   int sweeps = 0;
-  for (; rounds > 0 && sweeps < 60; ++sweeps) {
+  bool done = rounds <= 0;
+  if (!done) {
+    // [offmax per sweep (8 B each) | barrier count, generation | status | sweeps]
+    std::vector<uint64_t> zero(MAX_SWEEPS + 2, 0);
+    unsigned long long* w = (unsigned long long*)up(zero.data(), zero.size() * 8);
+    unsigned int* bar = (unsigned int*)(w + MAX_SWEEPS);
+    int* cstat = (int*)(w + MAX_SWEEPS + 1);
+    const cudaError_t ce = tnx_launch_jacobi_coop(dg, dslots, (int)slots.size(), maxcp, MAX_SWEEPS, 1e-13, w, bar,
+                                                  cstat, cstat + 1, st);
+    if (ce == cudaSuccess) {
+      int hs[2] = {0, 0};
+      CUDA_CHECK(cudaMemcpyAsync(hs, cstat, sizeof(hs), cudaMemcpyDeviceToHost, st));
+      CUDA_CHECK(cudaStreamSynchronize(st));
+      if (hs[0] != 0) fail(TNX_ERR_TIMEOUT, "SVD: a grid barrier of the Jacobi sweeps timed out");
+      sweeps = hs[1];
+      done = true;
+    } else if (ce == cudaErrorNotSupported || ce == cudaErrorCooperativeLaunchTooLarge) {
+      (void)cudaGetLastError();   // the per-round path below
+    } else {
+      CUDA_CHECK(ce);
+    }
+  }
+  unsigned long long* dmax = (unsigned long long*)MO.p;
+  unsigned long long* hmax = (unsigned long long*)ctx->pinned;
+  for (; !done && sweeps < MAX_SWEEPS; ++sweeps) {
     CUDA_CHECK(cudaMemsetAsync(dmax, 0, 8, st));
     for (int k = 0; k < rounds; ++k)
       CUDA_CHECK(tnx_launch_jacobi_round(dg, dslots, (int)slots.size(), k, dmax, st));

@@ -1199,6 +1199,92 @@ void build_final(Plan& p, const OpView& root, const std::vector<std::string>& to
   p.fin = upload_tasks(p, tasks);
 }
 
+// The output relayout folded into the last product: when that product runs
+// entirely on the split (or TF32) GEMM and every column of each of its charge
+// groups lands, over the group's rows r, at out[off + r * stride] (the usual
+// case: the GEMM's rows are one leg of the output, e.g. a' of psi'), the GEMM's
+// epilogue stores there through a per-column table and the relayout launch is
+// skipped.  The table is derived from the relayout's own tasks, element by
+// element, and checked: every column is either absent from the output or
+// present for all of its group's rows, with one consistent stride.
+void fold_final(Plan& p) {
+  if (p.steps.empty() || p.fin.h.empty()) return;
+  StepPlan& s = p.steps.back();
+  const bool split = p.prec == TNX_PREC_SPLIT_BF16 || p.prec == TNX_PREC_SPLIT_F16 || p.prec == TNX_PREC_TF32;
+  if (!split || s.nstiles == 0 || s.nstiles_skinny != 0 || s.nftiles != 0 || s.hSG.empty()) return;
+  const int G = s.G;
+  std::vector<int64_t> fbase(G + 1, 0);
+  std::vector<std::pair<int64_t, int>> starts;   // (C offset, group)
+  for (int g = 0; g < G; ++g) {
+    if (s.skinny[g]) return;
+    fbase[g + 1] = fbase[g] + s.mkn[3 * g + 2];
+    if (s.mkn[3 * g] > 0 && s.mkn[3 * g + 2] > 0) starts.push_back({s.offC[g], g});
+  }
+  std::sort(starts.begin(), starts.end());
+  const int64_t ncol = fbase[G];
+  std::vector<int64_t> r0(ncol, -1), d0(ncol, 0), st(ncol, INT64_MIN), cnt(ncol, 0);
+  for (const CopyTask& t : p.fin.h) {
+    if (t.src_slot != s.slotC || t.dst_slot != p.out_slot || t.tleg < -1) return;
+    std::vector<int64_t> idx(t.rank, 0);
+    for (int64_t e = 0; e < t.nelem; ++e) {
+      int64_t so = t.src_off, dd = t.dst_off;
+      for (int l = 0; l < t.rank; ++l) {
+        so += idx[l] * t.sstride[l];
+        dd += idx[l] * t.dstride[l];
+      }
+      for (int l = t.rank - 1; l >= 0; --l) {   // next index, last leg fastest
+        if (++idx[l] < t.shape[l]) break;
+        idx[l] = 0;
+      }
+      auto it = std::upper_bound(starts.begin(), starts.end(), std::make_pair(so, INT32_MAX));
+      if (it == starts.begin()) return;
+      const int g = (--it)->second;
+      const int64_t M = s.mkn[3 * g], N = s.mkn[3 * g + 2], rel = so - s.offC[g];
+      if (rel >= M * N) return;
+      const int64_t r = rel / N, k = fbase[g] + rel % N;
+      if (r0[k] < 0) {
+        r0[k] = r;
+        d0[k] = dd;
+      } else {
+        const int64_t dr = r - r0[k], dv = dd - d0[k];
+        if (dr == 0) return;
+        if (st[k] == INT64_MIN) {
+          if (dv % dr != 0) return;
+          st[k] = dv / dr;
+        } else if (dv != st[k] * dr) {
+          return;
+        }
+      }
+      ++cnt[k];
+    }
+  }
+  std::vector<FinalCol> fc(std::max<int64_t>(ncol, 1));
+  const int64_t out_elems = p.slot_elems[p.out_slot];
+  for (int g = 0; g < G; ++g) {
+    const int64_t M = s.mkn[3 * g];
+    for (int64_t k = fbase[g]; k < fbase[g + 1]; ++k) {
+      if (cnt[k] == 0) {
+        fc[k] = FinalCol{-1, 0};
+        continue;
+      }
+      if (cnt[k] != M) return;
+      const int64_t stride = st[k] == INT64_MIN ? 0 : st[k];
+      const int64_t off = d0[k] - r0[k] * stride, last = off + (M - 1) * stride;
+      if (off < 0 || off >= out_elems || last < 0 || last >= out_elems) return;
+      fc[k] = FinalCol{off, stride};
+    }
+  }
+  const int fslot = p.new_slot((double*)p.upload(fc), (int64_t)fc.size() * 2);
+  std::vector<SplitGroup> sg = s.hSG;   // the host copy stays unfolded (batches keep their relayout)
+  for (int g = 0; g < G; ++g) {
+    sg[g].out_slot = p.out_slot;
+    sg[g].fc_slot = fslot;
+    sg[g].fc_off = (int32_t)fbase[g];
+  }
+  s.dSG = p.upload(sg);
+  p.fin_folded = true;
+}
+
 // Fuses every step whose charge groups are all skinny (K <= 16, N <= 64) and
 // whose operand A is relaid entirely by destination bands: one kernel gathers
 // each band's A rows from their sources, forms the product and writes the
@@ -1460,6 +1546,7 @@ std::unique_ptr<Plan> build_plan(tnx_network* net, const std::string& key, const
   OpView root = walk(net->root);
   build_final(*p, root, net->tout);
   fuse_skinny_steps(*p);
+  fold_final(*p);
   const char* dbg = dry ? nullptr : getenv("TNX_DEBUG_PLAN");
   if (dbg) {
     if (*dbg && *dbg != '0') {
@@ -1512,7 +1599,7 @@ void sync_slots(Plan& p, cudaStream_t st) {
 }
 
 
-void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB);
+void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB, bool balance);
 
 // Enqueue one apply.  `fixed`: network tensors whose data has not changed since
 // the previous apply of this plan (a Lanczos solve marks every tensor but the
@@ -1521,7 +1608,12 @@ void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB
 // keeps its product: neither is recomputed.
 // skip_slot >= 0: the relayout of that input tensor was done already (a Lanczos
 // step fuses it with its normalisation).
-void enqueue_plan(Plan& p, cudaStream_t st, uint64_t fixed = 0, int skip_slot = -1) {
+// vary: network tensors that may change between the applies of a sequence
+// (a Lanczos solve: the vector).  A split step is K-balanced from its A
+// operand unless A varies while B stays fixed (B's slices would then need A's
+// exponents of every apply); the choice is the same for every apply of the
+// sequence, so slices kept from a previous apply stay consistent.
+void enqueue_plan(Plan& p, cudaStream_t st, uint64_t fixed = 0, int skip_slot = -1, uint64_t vary = ~(uint64_t)0) {
   tnx_ctx* c = p.ctx;
   for (auto& s : p.steps) {
     const bool needA = (s.leavesA & ~fixed) != 0;
@@ -1554,9 +1646,14 @@ void enqueue_plan(Plan& p, cudaStream_t st, uint64_t fixed = 0, int skip_slot = 
         CUDA_CHECK(tnx_launch_gemm_f32(s.dG, s.dT, s.ntiles, p.d_slots, st));
         break;
       }
-      default: enqueue_split(p, s, st, needA, needB); break;
+      default: {
+        const bool balance = !((s.leavesA & vary) != 0 && (s.leavesB & vary) == 0);
+        enqueue_split(p, s, st, needA, needB, balance);
+        break;
+      }
     }
   }
+  if (p.fin_folded) return;   // the last product's epilogue wrote the output
   ProfScope ps(c, st, TNX_KC_FINAL, 16.0 * (double)p.fin.total);
   CUDA_CHECK(tnx_launch_copy(p.fin.d, p.fin.chunks, p.fin.nchunks, p.d_slots, st));
 }
@@ -1602,8 +1699,8 @@ void check_out_bonds(const Plan& p, const tnx_tensor* out) {
 
 namespace {
 void build_split_parts(Plan& p, StepPlan& s) { tnx_build_split_parts(p, s); }
-void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB) {
-  tnx_enqueue_split(p, s, st, needA, needB);
+void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB, bool balance) {
+  tnx_enqueue_split(p, s, st, needA, needB, balance);
 }
 }  // namespace
 
@@ -1974,7 +2071,7 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
         const uint32_t prof = ctx->prof;
         if ((prof & TNX_PROF_LAST_APPLY) && j != nsteps - 1) ctx->prof = 0;
         try {
-          enqueue_plan(*p, st, j == 0 ? 0 : fixed, (j > 0 && vcopy) ? slot : -1);
+          enqueue_plan(*p, st, j == 0 ? 0 : fixed, (j > 0 && vcopy) ? slot : -1, ~fixed);
         } catch (...) {
           ctx->prof = prof;
           throw;

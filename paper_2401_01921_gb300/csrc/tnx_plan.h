@@ -67,6 +67,12 @@ struct StepPlan {
   double flops_skinny = 0;      // useful flops of the skinny groups
   // split precision
   int slotSA = -1, slotSB = -1, slotEA = -1, slotEB = -1;
+  int slotKX = -1;              // K balancing words (int32, whole K tiles per group)
+  KexpJob* dKJ = nullptr;       // their jobs (one per split group) and work items
+  int nkj = 0;
+  int4* dKI = nullptr;
+  int64_t nki = 0;
+  std::vector<KexpJob> hKJ;     // host copy (batched plans merge them)
   struct Jobs {             // one slicing launch: its jobs and work items
     SliceJob* d = nullptr;
     int n = 0;
@@ -122,6 +128,7 @@ struct Plan {
   std::vector<BondD> out_bonds;
   std::vector<std::string> out_labels;
   TaskList fin;
+  bool fin_folded = false;       // the last split product writes the output itself (fin unused)
   int prec = TNX_PREC_F64;
   int nslice = 6, beta = 7;
   bool narrow_tiles = true;       // from the network (a batch needs the same tile width in every plan)
@@ -183,7 +190,9 @@ struct tnx_network {
 
 // split-precision planning and launch (tnx_split.cpp)
 void tnx_build_split_parts(Plan& p, StepPlan& s);
-void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB);
+// balance: K-balanced slicing (A's column exponents), recomputed when A is
+std::vector<int4> tnx_kexp_items(const std::vector<KexpJob>& jobs);
+void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB, bool balance);
 std::vector<int2> tnx_slice_schedule(std::vector<SliceJob>& jobs);
 std::vector<int2> tnx_tf32_schedule(std::vector<SliceJob>& jobs);
 

@@ -51,8 +51,8 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
   const int TKE = tf32 ? 16 : TK;   // K values per 64-byte tile row
   std::vector<SliceJob> jobs[2];
   int64_t elems[2] = {0, 0};
-  std::vector<int64_t> offSA(G), offSB(G), offEA(G), offEB(G);
-  int64_t sa = 0, sb = 0, ea = 0, eb = 0;
+  std::vector<int64_t> offSA(G), offSB(G), offEA(G), offEB(G), offKX(G, 0);
+  int64_t sa = 0, sb = 0, ea = 0, eb = 0, kx = 0;
   // Tile width: 32 columns when the 32-wide tiles of the step fit in one wave
   // on the 152 SMs (the CTAs then take half the columns each, which halves
   // their drain and conversion), else 64.
@@ -76,6 +76,8 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
     offSB[g] = sb;
     offEA[g] = ea;
     offEB[g] = eb;
+    offKX[g] = kx;
+    kx += KT * TKE;
     sa += MT * KT * n * (int64_t)(TM * TK * 2);
     sb += NT * KT * n * (int64_t)(TN * TK * 2);
     ea += M;
@@ -85,6 +87,7 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
   s.slotSB = p.new_slot(p.alloc_zero((size_t)sb), sb / 8);
   s.slotEA = p.new_slot(p.alloc_zero((size_t)std::max<int64_t>(ea, 1) * 4), ea / 2);
   s.slotEB = p.new_slot(p.alloc_zero((size_t)std::max<int64_t>(eb, 1) * 4), eb / 2);
+  if (!tf32) s.slotKX = p.new_slot(p.alloc_zero((size_t)std::max<int64_t>(kx, 1) * 4), kx / 2);
   for (int side = 0; side < 2; ++side) {
     for (int g = 0; g < G; ++g) {
       if (s.skinny[g]) continue;
@@ -103,6 +106,9 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
       j.K = (int32_t)K;
       j.ld = (int32_t)s.ldK[g];
       j.tile_rows = tr;
+      j.kx_slot = tf32 ? -1 : s.slotKX;
+      j.kx_off = offKX[g];
+      j.kx_sign = side == 0 ? -1 : 1;   // A's columns scaled down, B's rows up
       jobs[side].push_back(j);
       elems[side] += rows * K;
     }
@@ -118,6 +124,28 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
     J.h = js;
     return J;
   };
+  if (!tf32) {
+    std::vector<KexpJob> kj;
+    for (int g = 0; g < G; ++g) {
+      if (s.skinny[g]) continue;
+      KexpJob k;
+      memset(&k, 0, sizeof(k));
+      k.src_slot = s.slotA;
+      k.src_off = s.offA[g];
+      k.kx_slot = s.slotKX;
+      k.kx_off = offKX[g];
+      k.rows = (int32_t)s.mkn[3 * g];
+      k.K = (int32_t)s.mkn[3 * g + 1];
+      k.ld = (int32_t)s.ldK[g];
+      kj.push_back(k);
+    }
+    const std::vector<int4> ki = tnx_kexp_items(kj);
+    s.dKJ = p.upload(kj);
+    s.nkj = (int)kj.size();
+    s.dKI = p.upload(ki);
+    s.nki = (int64_t)ki.size();
+    s.hKJ = kj;
+  }
   std::vector<SliceJob> all = jobs[0];
   all.insert(all.end(), jobs[1].begin(), jobs[1].end());
   s.jobsA = make(jobs[0], elems[0]);
@@ -133,6 +161,8 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
     x.b_slot = s.slotSB;
     x.c_slot = s.slotC;
     x.ea_slot = s.slotEA;
+    x.out_slot = -1;
+    x.fc_slot = -1;
     x.eb_slot = s.slotEB;
     x.a_off_bytes = offSA[g];
     x.b_off_bytes = offSB[g];
@@ -190,7 +220,18 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
   s.hST = tiles;
 }
 
-void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB) {
+// Work items of the K-balancing pass: 32 K indices by 64 rows each.
+std::vector<int4> tnx_kexp_items(const std::vector<KexpJob>& jobs) {
+  std::vector<int4> items;
+  for (size_t q = 0; q < jobs.size(); ++q)
+    for (int k0 = 0; k0 < jobs[q].K; k0 += 32)
+      for (int r0 = 0; r0 < jobs[q].rows; r0 += 64) items.push_back(make_int4((int)q, k0, r0, 0));
+  return items;
+}
+
+// balance: slice with K balancing.  The exponents come from A, so they are
+// recomputed whenever A is re-prepared; a B re-prepared alone reuses them.
+void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB, bool balance) {
   const int f16 = p.prec == TNX_PREC_SPLIT_F16 ? 1 : 0;
   const StepPlan::Jobs* J = (needA && needB) ? &s.jobsAll : needA ? &s.jobsA : needB ? &s.jobsB : nullptr;
   if (p.prec == TNX_PREC_TF32) {
@@ -205,7 +246,8 @@ void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool n
   }
   if (J && J->n) {
     ProfScope ps(p.ctx, st, TNX_KC_SLICE, (double)J->elems * (8.0 + 8.0 + 2.0 * p.nslice));
-    CUDA_CHECK(tnx_launch_slices(J->d, J->items, J->nitems, p.nslice, p.beta, f16, p.d_slots, st));
+    if (balance && needA) CUDA_CHECK(tnx_launch_kexp(s.dKJ, s.nkj, s.dKI, s.nki, p.d_slots, st));
+    CUDA_CHECK(tnx_launch_slices(J->d, J->items, J->nitems, p.nslice, p.beta, f16, p.d_slots, st, balance ? 1 : 0));
   }
   ProfScope ps(p.ctx, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
   CUDA_CHECK(tnx_launch_gemm_split(s.dSG, s.dST, s.nstiles, p.nslice, p.beta, f16, p.d_slots, p.ctx->d_status, st,
