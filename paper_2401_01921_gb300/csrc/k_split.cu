@@ -526,7 +526,7 @@ struct SplitShared {
 // up once per CTA; the stage ring and the chunk hand-off between the MMA warp
 // and the epilogue warps continue across tiles, so the producer streams the
 // next tile's slices while the epilogue drains the current one.
-template <int NS, int TNV, bool TF>
+template <int NS, int TNV, bool TF, bool FOLD>
 __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const SplitGroup* __restrict__ groups,
                                                              const GemmTile* __restrict__ tiles, int ntiles, int beta,
                                                              int f16, double* const* __restrict__ slots,
@@ -687,6 +687,11 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
         acc[c] = 0;
         accd[c] = 0.0;
       }
+      // A tile whose K is at most 160 bounds every level sum by 6 * 160 * 64^2 <
+      // 2^22, inside the range where the FP32 -> int conversion is an exact
+      // add of 1.5 * 2^23 (full-rate ALU instead of the conversion unit), and
+      // adjacent levels combine in 32-bit integers before the 64-bit sum.
+      const bool small_chunks = KT * TKE <= 160;
       for (int ch = 0; ch < nchunks; ++ch, ++chunk) {
         if (!mbar_wait(&sh->accfull, (uint32_t)chunk & 1u, status, 14, abort_flag)) {
           ok = false;
@@ -705,6 +710,12 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
           for (int c = 0; c < 8; ++c) {
             if constexpr (TF) {
               accd[cg * 8 + c] += (double)__uint_as_float(v[0][c]);
+            } else if (NS == 6 && small_chunks) {
+              int d[NS];
+#pragma unroll
+              for (int t = 0; t < NS; ++t) d[t] = __float_as_int(__uint_as_float(v[t][c]) + 12582912.0f) - 0x4B400000;
+              const int lo = d[5] + d[4] * 128, mid = d[3] + d[2] * 128, hi = d[1] + d[0] * 128;   // |.| < 2^30
+              acc[cg * 8 + c] += ((long long)hi << 28) + ((long long)mid << 14) + (long long)lo;
             } else {
               long long x = 0;
 #pragma unroll
@@ -726,8 +737,9 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
         __syncwarp();
         double* cbase = slots[gr.c_slot] + gr.c_off;
         // a folded output relayout: column descriptors, destination = the network's output
-        const FinalCol* fcol = gr.fc_slot >= 0 ? (const FinalCol*)slots[gr.fc_slot] + gr.fc_off : nullptr;
-        double* obase = gr.fc_slot >= 0 ? slots[gr.out_slot] : nullptr;
+        // (FOLD: an instantiation of its own, so the plain store path keeps its registers)
+        const FinalCol* fcol = FOLD ? (const FinalCol*)slots[gr.fc_slot] + gr.fc_off : nullptr;
+        double* obase = FOLD ? slots[gr.out_slot] : nullptr;
         const int r0 = tl.m0 + sub * 32;
 #pragma unroll
         for (int c4 = 0; c4 < ECOLS / 4; ++c4) {
@@ -743,7 +755,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
           }
           __syncwarp();
           const int cc = lane & 3, col = tl.n0 + cb + c4 * 4 + cc;
-          if (fcol) {
+          if constexpr (FOLD) {
             const FinalCol d = col < gr.N ? fcol[col] : FinalCol{-1, 0};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -810,9 +822,9 @@ size_t tnx_split_smem_bytes(int nslice, int tn) {
 }
 
 namespace {
-template <int TNV, bool TF>
-cudaError_t launch_split(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int beta, int f16,
-                         double* const* slots, int32_t* status, cudaStream_t st, int grid) {
+template <int TNV, bool TF, bool FOLD>
+cudaError_t launch_split_t(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int beta, int f16,
+                           double* const* slots, int32_t* status, cudaStream_t st, int grid) {
   constexpr int NS = TF ? 1 : MAXN;
   const size_t smem = tnx_split_smem_bytes(NS, TNV);
   static int attr_dev = -1;   // the opt-in is per device
@@ -820,22 +832,32 @@ cudaError_t launch_split(const SplitGroup* groups, const GemmTile* tiles, int nt
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (attr_dev != dev) {
-    e = cudaFuncSetAttribute(split_gemm_kernel<NS, TNV, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(split_gemm_kernel<NS, TNV, TF, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
     attr_dev = dev;
   }
-  return tnx_launch(split_gemm_kernel<NS, TNV, TF>, dim3(grid), dim3(SPLIT_THREADS), smem, st,
+  return tnx_launch(split_gemm_kernel<NS, TNV, TF, FOLD>, dim3(grid), dim3(SPLIT_THREADS), smem, st,
                     groups, tiles, ntiles, beta, f16, slots, status);
+}
+
+template <int TNV, bool TF>
+cudaError_t launch_split(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int beta, int f16,
+                         double* const* slots, int32_t* status, cudaStream_t st, int grid, int fold) {
+  return fold ? launch_split_t<TNV, TF, true>(groups, tiles, ntiles, beta, f16, slots, status, st, grid)
+              : launch_split_t<TNV, TF, false>(groups, tiles, ntiles, beta, f16, slots, status, st, grid);
 }
 }  // namespace
 
 cudaError_t tnx_launch_gemm_split(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int nslice, int beta,
-                                  int f16, double* const* slots, int32_t* status, cudaStream_t st, int grid, int tn) {
+                                  int f16, double* const* slots, int32_t* status, cudaStream_t st, int grid, int tn,
+                                  int fold) {
   if (ntiles <= 0) return cudaSuccess;
   if (grid <= 0 || grid > ntiles) grid = ntiles;
   if (nslice != MAXN || beta != 7 || (tn != 32 && tn != 64)) return cudaErrorInvalidValue;
-  const cudaError_t le = tn == 32 ? launch_split<32, false>(groups, tiles, ntiles, beta, f16, slots, status, st, grid)
-                                  : launch_split<64, false>(groups, tiles, ntiles, beta, f16, slots, status, st, grid);
+  const cudaError_t le =
+      tn == 32 ? launch_split<32, false>(groups, tiles, ntiles, beta, f16, slots, status, st, grid, fold)
+               : launch_split<64, false>(groups, tiles, ntiles, beta, f16, slots, status, st, grid, fold);
   if (le != cudaSuccess) return le;
   tnx_note_launch(1);
   return cudaGetLastError();
@@ -854,12 +876,12 @@ cudaError_t tnx_launch_tf32_rows(const SliceJob* jobs, const int2* items, int64_
 }
 
 cudaError_t tnx_launch_gemm_tf32(const SplitGroup* groups, const GemmTile* tiles, int ntiles, double* const* slots,
-                                 int32_t* status, cudaStream_t st, int grid, int tn) {
+                                 int32_t* status, cudaStream_t st, int grid, int tn, int fold) {
   if (ntiles <= 0) return cudaSuccess;
   if (grid <= 0 || grid > ntiles) grid = ntiles;
   if (tn != 32 && tn != 64) return cudaErrorInvalidValue;
-  const cudaError_t le = tn == 32 ? launch_split<32, true>(groups, tiles, ntiles, 0, 0, slots, status, st, grid)
-                                  : launch_split<64, true>(groups, tiles, ntiles, 0, 0, slots, status, st, grid);
+  const cudaError_t le = tn == 32 ? launch_split<32, true>(groups, tiles, ntiles, 0, 0, slots, status, st, grid, fold)
+                                  : launch_split<64, true>(groups, tiles, ntiles, 0, 0, slots, status, st, grid, fold);
   if (le != cudaSuccess) return le;
   tnx_note_launch(1);
   return cudaGetLastError();

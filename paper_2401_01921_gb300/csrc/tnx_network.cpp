@@ -1282,6 +1282,7 @@ void fold_final(Plan& p) {
     sg[g].fc_off = (int32_t)fbase[g];
   }
   s.dSG = p.upload(sg);
+  s.split_fold = true;
   p.fin_folded = true;
 }
 

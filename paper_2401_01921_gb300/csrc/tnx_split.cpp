@@ -241,7 +241,7 @@ void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool n
     }
     ProfScope ps(p.ctx, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
     CUDA_CHECK(tnx_launch_gemm_tf32(s.dSG, s.dST, s.nstiles, p.d_slots, p.ctx->d_status, st, s.split_grid,
-                                    s.split_tn));
+                                    s.split_tn, s.split_fold ? 1 : 0));
     return;
   }
   if (J && J->n) {
@@ -251,5 +251,5 @@ void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool n
   }
   ProfScope ps(p.ctx, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
   CUDA_CHECK(tnx_launch_gemm_split(s.dSG, s.dST, s.nstiles, p.nslice, p.beta, f16, p.d_slots, p.ctx->d_status, st,
-                                   s.split_grid, s.split_tn));
+                                   s.split_grid, s.split_tn, s.split_fold ? 1 : 0));
 }
