@@ -687,11 +687,6 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
         acc[c] = 0;
         accd[c] = 0.0;
       }
-      // A tile whose K is at most 160 bounds every level sum by 6 * 160 * 64^2 <
-      // 2^22, inside the range where the FP32 -> int conversion is an exact
-      // add of 1.5 * 2^23 (full-rate ALU instead of the conversion unit), and
-      // adjacent levels combine in 32-bit integers before the 64-bit sum.
-      const bool small_chunks = KT * TKE <= 160;
       for (int ch = 0; ch < nchunks; ++ch, ++chunk) {
         if (!mbar_wait(&sh->accfull, (uint32_t)chunk & 1u, status, 14, abort_flag)) {
           ok = false;
@@ -710,12 +705,6 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
           for (int c = 0; c < 8; ++c) {
             if constexpr (TF) {
               accd[cg * 8 + c] += (double)__uint_as_float(v[0][c]);
-            } else if (NS == 6 && small_chunks) {
-              int d[NS];
-#pragma unroll
-              for (int t = 0; t < NS; ++t) d[t] = __float_as_int(__uint_as_float(v[t][c]) + 12582912.0f) - 0x4B400000;
-              const int lo = d[5] + d[4] * 128, mid = d[3] + d[2] * 128, hi = d[1] + d[0] * 128;   // |.| < 2^30
-              acc[cg * 8 + c] += ((long long)hi << 28) + ((long long)mid << 14) + (long long)lo;
             } else {
               long long x = 0;
 #pragma unroll
