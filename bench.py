@@ -56,8 +56,8 @@ SPLIT_TRAFFIC = {
         (9305600, "profiles/split_gemm_heisenberg_u1_chi512.md",
          "1edccaadeb9ebab7b4ab4b062a986006f94f024ad0ed51f81a11861a747bc22f"),
     "heisenberg_u1_chi2048_d2_D5_sectorscaled_lanczos20":
-        (90648192, "profiles/split_gemm_heisenberg_u1_chi2048.md",
-         "d5df9e0149253a7e2d6740904704b9294f6c54a339beccf5d1b23dcdcdfe26d8"),
+        (90154752, "profiles/split_gemm_heisenberg_u1_chi2048.md",
+         "f7c07b0c158f1c6f16da1ad4931acfb1f325dfa973bb1cac92aff522c9b36aaf"),
 }
 
 
@@ -276,7 +276,8 @@ def run_batch(args, torch, dev, tnx, I, build_network, dist, world, rank, local)
     count = 256
     chis = I.batched_hubbard_chis(count)
     ctx = tnx.Context(local)
-    order = "(L,(((psi,R),W2),W1))"
+    # contraction order: the block-sparse search (per instance) unless --order names another
+    order = {"sparse": "sparse", "dense": None}.get(args.order, args.order)
     res = {}
     prof_all = {}
     for prec in (["split_bf16", "f64"] if args.prec == "auto" else [args.prec]):
@@ -291,6 +292,7 @@ def run_batch(args, torch, dev, tnx, I, build_network, dist, world, rank, local)
             keep.append((T, B))
         batch = tnx.Batch(ctx, nets)
         flops = batch.flops()
+        orders = sorted(set(n.get_order() for n in nets))
         choice = batch.autotune(outs) if prec != "f64" else None
         for _ in range(max(3, args.warmup)):
             batch.launch_into(outs)
@@ -322,7 +324,8 @@ def run_batch(args, torch, dev, tnx, I, build_network, dist, world, rank, local)
         ctx.profile(False)
         rate, slow_ms = replica_rate(flops * args.steps, sum(times), dist, dev)
         res[prec] = {"value": rate / 1e12, "ms": slow_ms / args.steps,
-                     "flops": flops, "schedule": choice, "clocks": clk.summary(), "launches": launches}
+                     "flops": flops, "schedule": choice, "clocks": clk.summary(), "launches": launches,
+                     "orders": orders}
         del batch, nets, outs, keep
     main_prec = "split_bf16" if "split_bf16" in res else args.prec
     r = res[main_prec]
@@ -337,6 +340,7 @@ def run_batch(args, torch, dev, tnx, I, build_network, dist, world, rank, local)
             "dtype": "f64 via split_bf16 slices" if main_prec != "f64" else "f64", "data": "synthetic",
             "config": {"workload": "hubbard_u1u1_batch256_chi64to1024", "instances": count, "d": 4, "D": 6,
                        "apply_useful_flops": r["flops"], "split_schedule_grid": r["schedule"],
+                       "orders": r["orders"],
                        "l2": "flushed (512 MiB write) before each timed step",
                        "other_precisions": {k: {"value": v["value"], "ms_per_step": v["ms"]} for k, v in res.items()}},
             "clocks": r["clocks"], "gpu_launches": r["launches"],
