@@ -499,8 +499,10 @@ void finish_task(CopyTask& t, std::vector<int64_t> shape, std::vector<int64_t> s
     leg_magic(d, t.magic[l], t.shift[l]);
   }
   // transposing task: the source's unit-stride leg is not the destination's
+  // (small blocks stay plain tasks: a 32 x 32 tile per CTA would mostly idle,
+  // while packed with their neighbours they share one CTA)
   t.tleg = -1;
-  if (t.src_slot >= 0 && t.rank >= 2) {
+  if (t.src_slot >= 0 && t.rank >= 2 && t.nelem >= 256) {
     int S = -1;
     for (int l = 0; l < t.rank; ++l)
       if (t.sstride[l] == 1 && t.shape[l] > 1) S = l;
