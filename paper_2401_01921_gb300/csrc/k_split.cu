@@ -526,7 +526,7 @@ struct SplitShared {
 // up once per CTA; the stage ring and the chunk hand-off between the MMA warp
 // and the epilogue warps continue across tiles, so the producer streams the
 // next tile's slices while the epilogue drains the current one.
-template <int NS, int TNV, bool TF, bool FOLD>
+template <int NS, int TNV, bool TF, int MODE>
 __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const SplitGroup* __restrict__ groups,
                                                              const GemmTile* __restrict__ tiles, int ntiles, int beta,
                                                              int f16, double* const* __restrict__ slots,
@@ -705,6 +705,16 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
           for (int c = 0; c < 8; ++c) {
             if constexpr (TF) {
               accd[cg * 8 + c] += (double)__uint_as_float(v[0][c]);
+            } else if constexpr (MODE == 2) {
+              // MODE 2: every tile of the launch has K <= 160, so each level sum is
+              // below 6 * 160 * 64^2 < 2^22, where the FP32 -> int conversion is an
+              // exact add of 1.5 * 2^23 on the full-rate ALU, and adjacent levels
+              // combine in 32-bit integers before the 64-bit sum
+              int d[NS];
+#pragma unroll
+              for (int t = 0; t < NS; ++t) d[t] = __float_as_int(__uint_as_float(v[t][c]) + 12582912.0f) - 0x4B400000;
+              const int lo = d[5] + d[4] * 128, mid = d[3] + d[2] * 128, hi = d[1] + d[0] * 128;   // |.| < 2^30
+              acc[cg * 8 + c] += ((long long)hi << 28) + ((long long)mid << 14) + (long long)lo;
             } else {
               long long x = 0;
 #pragma unroll
@@ -726,9 +736,10 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
         __syncwarp();
         double* cbase = slots[gr.c_slot] + gr.c_off;
         // a folded output relayout: column descriptors, destination = the network's output
-        // (FOLD: an instantiation of its own, so the plain store path keeps its registers)
-        const FinalCol* fcol = FOLD ? (const FinalCol*)slots[gr.fc_slot] + gr.fc_off : nullptr;
-        double* obase = FOLD ? slots[gr.out_slot] : nullptr;
+        // (MODE 1, the folded output relayout: an instantiation of its own, so the
+        // plain store path keeps its registers)
+        const FinalCol* fcol = MODE == 1 ? (const FinalCol*)slots[gr.fc_slot] + gr.fc_off : nullptr;
+        double* obase = MODE == 1 ? slots[gr.out_slot] : nullptr;
         const int r0 = tl.m0 + sub * 32;
 #pragma unroll
         for (int c4 = 0; c4 < ECOLS / 4; ++c4) {
@@ -744,7 +755,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1) split_gemm_kernel(const Spli
           }
           __syncwarp();
           const int cc = lane & 3, col = tl.n0 + cb + c4 * 4 + cc;
-          if constexpr (FOLD) {
+          if constexpr (MODE == 1) {
             const FinalCol d = col < gr.N ? fcol[col] : FinalCol{-1, 0};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -811,7 +822,7 @@ size_t tnx_split_smem_bytes(int nslice, int tn) {
 }
 
 namespace {
-template <int TNV, bool TF, bool FOLD>
+template <int TNV, bool TF, int MODE>
 cudaError_t launch_split_t(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int beta, int f16,
                            double* const* slots, int32_t* status, cudaStream_t st, int grid) {
   constexpr int NS = TF ? 1 : MAXN;
@@ -821,32 +832,37 @@ cudaError_t launch_split_t(const SplitGroup* groups, const GemmTile* tiles, int 
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (attr_dev != dev) {
-    e = cudaFuncSetAttribute(split_gemm_kernel<NS, TNV, TF, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(split_gemm_kernel<NS, TNV, TF, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
     attr_dev = dev;
   }
-  return tnx_launch(split_gemm_kernel<NS, TNV, TF, FOLD>, dim3(grid), dim3(SPLIT_THREADS), smem, st,
+  return tnx_launch(split_gemm_kernel<NS, TNV, TF, MODE>, dim3(grid), dim3(SPLIT_THREADS), smem, st,
                     groups, tiles, ntiles, beta, f16, slots, status);
 }
 
+// mode: 0 plain stores, 1 folded output relayout, 2 plain stores with the
+// short-K level combine (split BF16/FP16 only)
 template <int TNV, bool TF>
 cudaError_t launch_split(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int beta, int f16,
-                         double* const* slots, int32_t* status, cudaStream_t st, int grid, int fold) {
-  return fold ? launch_split_t<TNV, TF, true>(groups, tiles, ntiles, beta, f16, slots, status, st, grid)
-              : launch_split_t<TNV, TF, false>(groups, tiles, ntiles, beta, f16, slots, status, st, grid);
+                         double* const* slots, int32_t* status, cudaStream_t st, int grid, int mode) {
+  if (mode == 1) return launch_split_t<TNV, TF, 1>(groups, tiles, ntiles, beta, f16, slots, status, st, grid);
+  if constexpr (!TF) {
+    if (mode == 2) return launch_split_t<TNV, TF, 2>(groups, tiles, ntiles, beta, f16, slots, status, st, grid);
+  }
+  return launch_split_t<TNV, TF, 0>(groups, tiles, ntiles, beta, f16, slots, status, st, grid);
 }
 }  // namespace
 
 cudaError_t tnx_launch_gemm_split(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int nslice, int beta,
                                   int f16, double* const* slots, int32_t* status, cudaStream_t st, int grid, int tn,
-                                  int fold) {
+                                  int mode) {
   if (ntiles <= 0) return cudaSuccess;
   if (grid <= 0 || grid > ntiles) grid = ntiles;
   if (nslice != MAXN || beta != 7 || (tn != 32 && tn != 64)) return cudaErrorInvalidValue;
   const cudaError_t le =
-      tn == 32 ? launch_split<32, false>(groups, tiles, ntiles, beta, f16, slots, status, st, grid, fold)
-               : launch_split<64, false>(groups, tiles, ntiles, beta, f16, slots, status, st, grid, fold);
+      tn == 32 ? launch_split<32, false>(groups, tiles, ntiles, beta, f16, slots, status, st, grid, mode)
+               : launch_split<64, false>(groups, tiles, ntiles, beta, f16, slots, status, st, grid, mode);
   if (le != cudaSuccess) return le;
   tnx_note_launch(1);
   return cudaGetLastError();

@@ -31,6 +31,7 @@ struct BStep {
   SplitGroup* dSG = nullptr;
   GemmTile* dST = nullptr;
   int nst = 0;
+  int kmax = 0;                 // largest K of the merged split groups
   double flops = 0, flops_skinny = 0;
 };
 
@@ -117,7 +118,7 @@ void enqueue_batch(tnx_batch& B, cudaStream_t st) {
       }
       ProfScope ps(c, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
       CUDA_CHECK(tnx_launch_gemm_split(s.dSG, s.dST, s.nst, B.nslice, B.beta, f16, B.d_slots, c->d_status, st,
-                                       B.split_grid, 64));
+                                       B.split_grid, 64, s.kmax <= 160 ? 2 : 0));
     }
   }
   ProfScope ps(c, st, TNX_KC_FINAL, 16.0 * (double)B.fin.total);
@@ -255,6 +256,7 @@ extern "C" tnx_status tnx_batch_create(tnx_ctx* ctx, int n, tnx_network* const* 
         bs.dSG = B->upload(sg);
         bs.dST = B->upload(st);
         bs.nst = (int)st.size();
+        for (const GemmTile& t : st) bs.kmax = std::max(bs.kmax, (int)sg[t.group].K);
       }
     }
     std::vector<const TaskList*> pf;

@@ -269,7 +269,7 @@ cudaError_t tnx_launch_kexp(const KexpJob* jobs, int njobs, const int4* items, i
 // tn: tile width (B rows per tile), 64 or 32; the B slices must be tiled with the same width.
 cudaError_t tnx_launch_gemm_split(const SplitGroup* groups, const GemmTile* tiles, int ntiles, int nslice,
                                   int beta, int f16, double* const* slots, int32_t* status, cudaStream_t st,
-                                  int grid, int tn, int fold = 0);
+                                  int grid, int tn, int mode = 0);   // mode: 0 plain, 1 folded output, 2 every K <= 160
 size_t tnx_split_smem_bytes(int nslice, int tn);
 // One-pass TF32 variant: tnx_launch_tf32_rows writes each operand row scaled by
 // its power of two and rounded to TF32 (FP32 words, 16 K values per tile row,

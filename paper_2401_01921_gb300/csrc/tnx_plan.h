@@ -88,6 +88,7 @@ struct StepPlan {
   int split_tn = 64;            // tile width of the split GEMM (B slices are tiled to match)
   int split_grid = 0;           // CTAs of the split GEMM; dST holds its per-CTA schedule (holes: group -1)
   bool split_fold = false;      // its epilogue writes the network's output (the folded output relayout)
+  int split_kmax = 0;           // largest K of its split groups
   std::vector<SplitGroup> hSG;  // host copies
   std::vector<GemmTile> hST;    // tiles longest K first, no holes (batched plans merge them)
   // fused skinny step (k_fused.cu): one launch replaces the relayout of A, the

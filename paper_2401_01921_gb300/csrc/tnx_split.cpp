@@ -71,6 +71,7 @@ void tnx_build_split_parts(Plan& p, StepPlan& s) {
       continue;
     }
     if (K > KMAX) fail(TNX_ERR_UNSUPPORTED, "split precision supports K <= 8192 per charge sector");
+    s.split_kmax = (int)std::max<int64_t>(s.split_kmax, K);
     const int64_t KT = (K + TKE - 1) / TKE, MT = (M + TM - 1) / TM, NT = (N + TN - 1) / TN;
     offSA[g] = sa;
     offSB[g] = sb;
@@ -251,5 +252,5 @@ void tnx_enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool n
   }
   ProfScope ps(p.ctx, st, TNX_KC_GEMM, s.flops - s.flops_skinny);
   CUDA_CHECK(tnx_launch_gemm_split(s.dSG, s.dST, s.nstiles, p.nslice, p.beta, f16, p.d_slots, p.ctx->d_status, st,
-                                   s.split_grid, s.split_tn, s.split_fold ? 1 : 0));
+                                   s.split_grid, s.split_tn, s.split_fold ? 1 : s.split_kmax <= 160 ? 2 : 0));
 }
