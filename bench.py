@@ -56,8 +56,8 @@ SPLIT_TRAFFIC = {
         (9305600, "profiles/split_gemm_heisenberg_u1_chi512.md",
          "1edccaadeb9ebab7b4ab4b062a986006f94f024ad0ed51f81a11861a747bc22f"),
     "heisenberg_u1_chi2048_d2_D5_sectorscaled_lanczos20":
-        (90154752, "profiles/split_gemm_heisenberg_u1_chi2048.md",
-         "f7c07b0c158f1c6f16da1ad4931acfb1f325dfa973bb1cac92aff522c9b36aaf"),
+        (90454144, "profiles/split_gemm_heisenberg_u1_chi2048.md",
+         "e1550ed725a44f91c70454252de5a020931028b96de062f913da4d6922d99265"),
 }
 
 
