@@ -4,10 +4,9 @@
 // vector (a LinOp).  Everything except that action runs here, in FP64, with
 // no host round trip inside the loop (so a whole solve can be captured in one
 // CUDA graph):
-//   twice: c = V^T w, w -= V c   (classical Gram-Schmidt against every previous
-//   vector: full reorthogonalisation; the first pass's coefficient of v_j is
-//   alpha_j = <v_j, w>, and subtracting all coefficients subsumes the
-//   three-term recurrence);
+//   alpha_j = <v_j, w>; w -= alpha_j v_j + beta_j v_{j-1} (three-term step);
+//   c = V^T w, w -= V c   (one classical Gram-Schmidt pass against every
+//   previous vector: full reorthogonalisation);
 //   beta_{j+1} = ||w||; stop if beta_{j+1} < 1e-14 max(|alpha_i|, beta_i; i <= j);
 //   v_{j+1} = w / beta_{j+1};
 // then Sturm bisection on the tridiagonal T and inverse iteration for its
@@ -123,6 +122,7 @@ int multidot_blocks(int64_t n) {
 template <int NG>
 __device__ __forceinline__ void multidot_group(const LanczosDev& L, int g0, int64_t c0, int64_t c1,
                                                double (*sh)[MD_T + 1]) {
+  // g0 is the basis row of the group's first vector
   double acc[NG];
 #pragma unroll
   for (int i = 0; i < NG; ++i) acc[i] = 0.0;
@@ -148,27 +148,29 @@ __device__ __forceinline__ void multidot_group(const LanczosDev& L, int g0, int6
   for (int i = 0; i < NG; ++i) sh[i][threadIdx.x] = acc[i];
 }
 
-// Dots of this block's chunk [c0, c1) against V_0 .. V_{m-1} into partial[b*m + i].
-__device__ void block_multidot(const LanczosDev& L, int m, int64_t c0, int64_t c1, double (*sh)[MD_T + 1]) {
+// Dots of this block's chunk [c0, c1) against V_vb .. V_{vb+m-1} into partial[b*m + i].
+__device__ void block_multidot(const LanczosDev& L, int m, int64_t c0, int64_t c1, double (*sh)[MD_T + 1],
+                               int vb = 0) {
   for (int g0 = 0; g0 < m; g0 += 16) {
     const int ng = m - g0 < 16 ? m - g0 : 16;
+    const int r0 = vb + g0;
     switch (ng) {
-      case 1: multidot_group<1>(L, g0, c0, c1, sh); break;
-      case 2: multidot_group<2>(L, g0, c0, c1, sh); break;
-      case 3: multidot_group<3>(L, g0, c0, c1, sh); break;
-      case 4: multidot_group<4>(L, g0, c0, c1, sh); break;
-      case 5: multidot_group<5>(L, g0, c0, c1, sh); break;
-      case 6: multidot_group<6>(L, g0, c0, c1, sh); break;
-      case 7: multidot_group<7>(L, g0, c0, c1, sh); break;
-      case 8: multidot_group<8>(L, g0, c0, c1, sh); break;
-      case 9: multidot_group<9>(L, g0, c0, c1, sh); break;
-      case 10: multidot_group<10>(L, g0, c0, c1, sh); break;
-      case 11: multidot_group<11>(L, g0, c0, c1, sh); break;
-      case 12: multidot_group<12>(L, g0, c0, c1, sh); break;
-      case 13: multidot_group<13>(L, g0, c0, c1, sh); break;
-      case 14: multidot_group<14>(L, g0, c0, c1, sh); break;
-      case 15: multidot_group<15>(L, g0, c0, c1, sh); break;
-      default: multidot_group<16>(L, g0, c0, c1, sh); break;
+      case 1: multidot_group<1>(L, r0, c0, c1, sh); break;
+      case 2: multidot_group<2>(L, r0, c0, c1, sh); break;
+      case 3: multidot_group<3>(L, r0, c0, c1, sh); break;
+      case 4: multidot_group<4>(L, r0, c0, c1, sh); break;
+      case 5: multidot_group<5>(L, r0, c0, c1, sh); break;
+      case 6: multidot_group<6>(L, r0, c0, c1, sh); break;
+      case 7: multidot_group<7>(L, r0, c0, c1, sh); break;
+      case 8: multidot_group<8>(L, r0, c0, c1, sh); break;
+      case 9: multidot_group<9>(L, r0, c0, c1, sh); break;
+      case 10: multidot_group<10>(L, r0, c0, c1, sh); break;
+      case 11: multidot_group<11>(L, r0, c0, c1, sh); break;
+      case 12: multidot_group<12>(L, r0, c0, c1, sh); break;
+      case 13: multidot_group<13>(L, r0, c0, c1, sh); break;
+      case 14: multidot_group<14>(L, r0, c0, c1, sh); break;
+      case 15: multidot_group<15>(L, r0, c0, c1, sh); break;
+      default: multidot_group<16>(L, r0, c0, c1, sh); break;
     }
     __syncthreads();
     // thread t sums 16 consecutive entries of row t/8, then 8 partners combine
@@ -185,53 +187,43 @@ __device__ void block_multidot(const LanczosDev& L, int m, int64_t c0, int64_t c
   }
 }
 
-__global__ void __launch_bounds__(MD_T) multidot_kernel(LanczosDev L, int m) {
+__global__ void __launch_bounds__(MD_T) multidot_kernel(LanczosDev L, int m, int vb) {
   tnx_grid_dependency();
   __shared__ double sh[16][MD_T + 1];
   if (stopped(L.state)) return;
   const int64_t chunk = (L.n + gridDim.x - 1) / gridDim.x;
   const int64_t c0 = chunk * blockIdx.x, c1 = min(L.n, c0 + chunk);
-  block_multidot(L, m, c0, c1, sh);
+  block_multidot(L, m, c0, c1, sh, vb);
 }
 
-// The first Gram-Schmidt update and the second pass's dots in one launch: each
-// block updates its own chunk (w -= sum_i coef[i] V_i, in the same order as the
-// separate update kernel) and then forms the chunk's dots of the new w, every
-// thread reading back only the entries it wrote.
-__global__ void __launch_bounds__(MD_T) update_multidot_kernel(LanczosDev L, int m) {
+// The three-term step fused with the Gram-Schmidt dots: each block forms
+// w <- (w - alpha_j v_j) - beta_j v_{j-1} on its own chunk (v_{-1} absent), then
+// the chunk's dots of the new w against v_0 .. v_{m-1}, every thread reading
+// back only the entries it wrote.
+__global__ void __launch_bounds__(MD_T) three_term_multidot_kernel(LanczosDev L, int m, int j) {
   tnx_grid_dependency();
   __shared__ double sh[16][MD_T + 1];
-  __shared__ double c[512];
   if (stopped(L.state)) return;
-  for (int i = threadIdx.x; i < m; i += MD_T) c[i] = L.coef[i];
-  __syncthreads();
+  const double a = L.alpha[j], b = j > 0 ? L.beta[j] : 0.0;
+  const double* vj = L.V + (int64_t)j * L.n;
+  const double* vp = L.V + (int64_t)(j > 0 ? j - 1 : 0) * L.n;
   const int64_t chunk = (L.n + gridDim.x - 1) / gridDim.x;
   const int64_t c0 = chunk * blockIdx.x, c1 = min(L.n, c0 + chunk);
-  int64_t x = c0 + threadIdx.x;
-  for (; x + MD_T < c1; x += 2 * MD_T) {
-    double w0 = L.w[x], w1 = L.w[x + MD_T];
-#pragma unroll 4
-    for (int i = 0; i < m; ++i) {
-      const double* vi = L.V + (int64_t)i * L.n;
-      const double a0 = vi[x], a1 = vi[x + MD_T];
-      w0 -= c[i] * a0;
-      w1 -= c[i] * a1;
+  if (j > 0) {
+    for (int64_t x = c0 + threadIdx.x; x < c1; x += MD_T) {
+      const double w = L.w[x] - a * vj[x];
+      L.w[x] = w - b * vp[x];
     }
-    L.w[x] = w0;
-    L.w[x + MD_T] = w1;
-  }
-  if (x < c1) {
-    double w = L.w[x];
-#pragma unroll 8
-    for (int i = 0; i < m; ++i) w -= c[i] * L.V[(int64_t)i * L.n + x];
-    L.w[x] = w;
+  } else {
+    for (int64_t x = c0 + threadIdx.x; x < c1; x += MD_T) L.w[x] = L.w[x] - a * vj[x];
   }
   block_multidot(L, m, c0, c1, sh);
 }
 
 // coef[i] = sum_b partial[b*m + i]   (one block per i, fixed order);
-// on the first pass, the coefficient of v_j is alpha_j = <v_j, H v_j>.
-__global__ void __launch_bounds__(RT) multidot_finalize_kernel(LanczosDev L, int m, int nb, int alpha_j) {
+// the sum of row alpha_i (if >= 0) is also alpha_j = <v_j, H v_j>.
+__global__ void __launch_bounds__(RT) multidot_finalize_kernel(LanczosDev L, int m, int nb, int alpha_i,
+                                                               int alpha_j) {
   tnx_grid_dependency();
   __shared__ double sh[32];
   if (stopped(L.state)) return;
@@ -241,7 +233,7 @@ __global__ void __launch_bounds__(RT) multidot_finalize_kernel(LanczosDev L, int
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) {
     L.coef[i] = acc;
-    if (i == alpha_j) L.alpha[alpha_j] = acc;
+    if (i == alpha_i) L.alpha[alpha_j] = acc;
   }
 }
 
@@ -514,31 +506,34 @@ cudaError_t tnx_launch_lanczos_set_input(double** slot_ptr, const LanczosDev& L,
 
 // The operator has been applied: L.w = H v_j.  One Lanczos step (without the
 // final v_{j+1} = w / beta_{j+1} when `normalize` is false: the caller then
-// fuses it with the next apply's relayout of the vector): classical
-// Gram-Schmidt against v_0..v_j done twice (the first pass also yields
-// alpha_j = <v_j, H v_j> and removes the three-term recurrence), the norm of
-// the result folded into the second update, then beta_{j+1}, the stopping
-// test and v_{j+1} = w / beta_{j+1}.
+// fuses it with the next apply's relayout of the vector): alpha_j = <v_j, w>;
+// the three-term step w <- w - alpha_j v_j - beta_j v_{j-1} fused with the dots
+// c = V^T w against v_0..v_j; one classical Gram-Schmidt update w <- w - V c
+// with the norm's partial sums; then beta_{j+1}, the stopping test and
+// v_{j+1} = w / beta_{j+1}.  The three-term step removes the large components
+// of H v_j, so the Gram-Schmidt pass removes only rounding-level ones and
+// leaves w orthogonal to the basis to working precision; a second pass would
+// change w by about eps |w| (the "twice is enough" criterion: a repeat is due
+// only when a pass shrinks |w| by more than about 1/sqrt(2)).  FP64 work per
+// entry: 2 (j + 1) + 3 fused multiply-adds.
 cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, double** next_slot, cudaStream_t st, bool normalize) {
   const int nb = grid_for(L.n);
   const int m = j + 1;
   const int mb = multidot_blocks(L.n);
-  // pass 1 dots and coefficients; the pass 1 update fused with the pass 2 dots;
-  // pass 2 coefficients; the pass 2 update with the norm's partial sums
   {
-    const cudaError_t le = tnx_launch(multidot_kernel, dim3(mb), dim3(MD_T), 0, st, L, m);
+    const cudaError_t le = tnx_launch(multidot_kernel, dim3(mb), dim3(MD_T), 0, st, L, 1, j);
     if (le != cudaSuccess) return le;
   }
   {
-    const cudaError_t le = tnx_launch(multidot_finalize_kernel, dim3(m), dim3(RT), 0, st, L, m, mb, j);
+    const cudaError_t le = tnx_launch(multidot_finalize_kernel, dim3(1), dim3(RT), 0, st, L, 1, mb, 0, j);
     if (le != cudaSuccess) return le;
   }
   {
-    const cudaError_t le = tnx_launch(update_multidot_kernel, dim3(mb), dim3(MD_T), 0, st, L, m);
+    const cudaError_t le = tnx_launch(three_term_multidot_kernel, dim3(mb), dim3(MD_T), 0, st, L, m, j);
     if (le != cudaSuccess) return le;
   }
   {
-    const cudaError_t le = tnx_launch(multidot_finalize_kernel, dim3(m), dim3(RT), 0, st, L, m, mb, -1);
+    const cudaError_t le = tnx_launch(multidot_finalize_kernel, dim3(m), dim3(RT), 0, st, L, m, mb, -1, 0);
     if (le != cudaSuccess) return le;
   }
   {
