@@ -129,9 +129,12 @@ __global__ void __launch_bounds__(JT) jacobi_round_kernel(const SvdGroup* __rest
 // All sweeps of every block in one cooperative launch (all CTAs resident at
 // once, which the launch checks): each warp of the grid takes pairs of a
 // round across every block (pair i of round k as in jacobi_round_kernel), and
-// a grid barrier separates the rounds.  After each sweep the CTAs read the largest relative
-// off-diagonal of that sweep (offmax[sweep], zeroed by the host) behind a
-// barrier and all stop together once it is at most tol.  The barrier is a
+// a grid barrier separates the rounds.  One warp per CTA: the FP64 pipe
+// (about two fused multiply-adds per clock per SM on this part) bounds a
+// round, so its pairs go to as many SMs as there are pairs.  After each sweep
+// the CTAs read the largest squared relative off-diagonal of that sweep
+// (offmax[sweep], zeroed by the host) behind a barrier and all stop together
+// once it is at most tol2 (the launcher squares tol).  The barrier is a
 // counter plus a generation word; every wait on it is bounded (about a second
 // of clock): on expiry the CTA sets *status and leaves, and so do the others
 // at their next barrier.  sweeps_out[0] receives the number of sweeps run.
@@ -176,13 +179,16 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-__global__ void __launch_bounds__(JT) jacobi_coop_kernel(const SvdGroup* __restrict__ groups,
+constexpr int CJT = 32;   // threads per CTA of the cooperative kernel: one pair-warp per CTA, so that the
+                          // pairs of a round spread over as many SMs (and FP64 pipes) as there are pairs
+
+__global__ void __launch_bounds__(CJT) jacobi_coop_kernel(const SvdGroup* __restrict__ groups,
                                                          const int2* __restrict__ slots, int nslots, int maxcp,
-                                                         int max_sweeps, double tol, unsigned long long* offmax,
+                                                         int max_sweeps, double tol2, unsigned long long* offmax,
                                                          unsigned int* bar, int* status, int* sweeps_out) {
   // one warp per pair: the pairs of a round run side by side over the whole grid
   const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * (JT / 32) + (threadIdx.x >> 5), nwarps = gridDim.x * (JT / 32);
+  const int gw = blockIdx.x * (CJT / 32) + (threadIdx.x >> 5), nwarps = gridDim.x * (CJT / 32);
   int sw = 0;
   bool ok = true;
   while (ok && sw < max_sweeps) {
@@ -218,14 +224,23 @@ __global__ void __launch_bounds__(JT) jacobi_coop_kernel(const SvdGroup* __restr
         b = warp_sum(b);
         c = warp_sum(c);
         if (!(a > 0.0 && b > 0.0)) continue;
-        const double o = fabs(c) / sqrt(a * b);
-        off_w = fmax(off_w, o);
-        if (o <= 1e-15) continue;
-        const double zeta = (b - a) / (2.0 * c);
-        const double az = fabs(zeta);
-        double t = az > 1e100 ? 0.5 / az : 1.0 / (az + sqrt(1.0 + az * az));
-        if (zeta < 0.0) t = -t;
-        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        // squared relative off-diagonal; the same tests as |gamma| / sqrt(alpha beta)
+        // against 1e-15 and tol, with one FP64 division instead of a root and two
+        const double ab = a * b, c2 = c * c;
+        off_w = fmax(off_w, c2 / ab);
+        if (c2 <= 1e-30 * ab) continue;
+        // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) with zeta = d / (2 gamma), d = beta - alpha,
+        // multiplied through by 2 |gamma|: one root, one division and one reciprocal root
+        const double d = b - a;
+        double t;
+        if (fabs(d) < 1e150 && fabs(c) < 1e150) {
+          t = 2.0 * c / (d + copysign(sqrt(fma(d, d, 4.0 * c2)), d));
+        } else {   // squares out of range: the quotient form
+          const double zeta = d / (2.0 * c), az = fabs(zeta);
+          t = az > 1e100 ? 0.5 / az : 1.0 / (az + sqrt(1.0 + az * az));
+          if (zeta < 0.0) t = -t;
+        }
+        const double cs = rsqrt(fma(t, t, 1.0)), sn = cs * t;
         for (int64_t e = lane; e < g.r; e += 32) {
           const double u = xp[e], v = xq[e];
           xp[e] = cs * u - sn * v;
@@ -245,7 +260,7 @@ __global__ void __launch_bounds__(JT) jacobi_coop_kernel(const SvdGroup* __restr
     if (!ok) break;
     const double off = __longlong_as_double((long long)*(volatile unsigned long long*)&offmax[sw]);
     ++sw;
-    if (off <= tol) break;   // every warp reads the same value behind the last barrier
+    if (off <= tol2) break;   // every warp reads the same value behind the last barrier
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) sweeps_out[0] = sw;
 }
@@ -350,15 +365,16 @@ cudaError_t tnx_launch_jacobi_coop(const SvdGroup* groups, const int2* slots, in
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel, JT, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel, CJT, 0);
   if (e != cudaSuccess) return e;
   if (!coop || per_sm < 1) return cudaErrorNotSupported;
   int grid = nsm * (per_sm < 4 ? per_sm : 4);
-  const int need = (nslots + JT / 32 - 1) / (JT / 32);   // one warp per pair of a round
+  const int need = (nslots + CJT / 32 - 1) / (CJT / 32);   // one warp per pair of a round
   if (grid > need) grid = need;
-  void* args[] = {(void*)&groups, (void*)&slots, (void*)&nslots, (void*)&maxcp, (void*)&max_sweeps, (void*)&tol,
+  double tol2 = tol * tol;   // the kernel compares squared relative off-diagonals
+  void* args[] = {(void*)&groups, (void*)&slots, (void*)&nslots, (void*)&maxcp, (void*)&max_sweeps, (void*)&tol2,
                   (void*)&offmax, (void*)&bar, (void*)&status, (void*)&sweeps_out};
-  e = cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, dim3(grid), dim3(JT), args, 0, st);
+  e = cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, dim3(grid), dim3(CJT), args, 0, st);
   if (e != cudaSuccess) return e;
   tnx_note_launch(1);
   return cudaSuccess;

@@ -252,3 +252,18 @@ def test_svd_err_threshold_and_nothing_kept(ctx):
     with pytest.raises(tnx.TnxError) as e:
         tnx.svd_truncate(to_lib(ctx, T), 2, 0, 10.0)
     assert e.value.name == "TNX_ERR_ARG"
+
+
+@pytest.mark.parametrize("m,n", [(90, 60), (250, 200), (320, 300), (600, 400), (400, 600)])
+def test_svd_graded_dense_block(ctx, m, n):
+    """One dense block whose singular values fall from 1 to 1e-20 (below rounding, as in a DMRG
+    wavefunction), tall and wide, up to 400 vectors of length 600; all values kept, so the
+    vectors of the values below rounding must come out orthonormal too."""
+    rng = np.random.default_rng(m * 1000 + n)
+    k = min(m, n)
+    s = 10.0 ** (-20.0 * np.arange(k) / k)
+    q1, _ = np.linalg.qr(rng.standard_normal((m, k)))
+    q2, _ = np.linalg.qr(rng.standard_normal((n, k)))
+    M = (q1 * s) @ q2.T
+    T = BlockTensor([OB.make(0, [((), m)]), OB.make(0, [((), n)])], {(0, 0): M})
+    _check_svd(ctx, T, 1)
