@@ -264,10 +264,15 @@ tnx_status tnx_network_step_tables(tnx_network* net, int step, int32_t* charges,
 
 /* Sec. 9.3 Lanczos on a LinOp: the network, with the tensor named `vec_slot`
  * as the vector, is the linear operator (its TOUT bonds must equal the
- * vector's bonds).  Starting from v0, runs at most nsteps Lanczos steps with
- * full reorthogonalisation (classical Gram-Schmidt, twice), stopping early if
- * the new off-diagonal falls below 1e-14 * max(|alpha_i|, beta_i) over the steps so
- * far; returns the lowest
+ * vector's bonds), which must be Hermitian.  Starting from v0, runs at most
+ * nsteps Lanczos steps (three-term recurrence) that keep the basis orthogonal
+ * to 1e-10 or better: each step estimates the loss of orthogonality by
+ * Simon's recurrence (partial reorthogonalisation) and takes a classical
+ * Gram-Schmidt pass against all earlier vectors when an estimate exceeds
+ * 1e-10 (and at the next step too); in TNX_PREC_F32 and TNX_PREC_TF32, whose
+ * rounded operator is far from symmetric, every step takes the pass.  Stops
+ * early if the new off-diagonal falls below 1e-14 * max(|alpha_i|, beta_i) over
+ * the steps so far; returns the lowest
  * eigenvalue of the tridiagonal matrix (Sturm bisection, FP64) in *eval and,
  * if evec != NULL, the Ritz vector (unit norm, largest-|y| coefficient
  * positive) in evec (same bonds as v0).  *nmatvec (may be NULL) gets the number

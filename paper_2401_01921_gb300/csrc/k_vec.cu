@@ -41,6 +41,12 @@ __device__ double block_sum(double v, double* sh) {
 
 __device__ __forceinline__ bool stopped(const int32_t* state) { return *(volatile const int32_t*)(state + 1) != 0; }
 
+// A gated launch of the Gram-Schmidt pass does nothing unless this step's
+// decision asked for the pass.
+__device__ __forceinline__ bool gated_off(const int32_t* state, int gate) {
+  return gate && *(volatile const int32_t*)(state + 2) == 0;
+}
+
 __global__ void scale_kernel(double* x, int64_t n, double a) {
   tnx_grid_dependency();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -88,7 +94,10 @@ __global__ void lanczos_init_kernel(LanczosDev L, const double* v0) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     L.state[0] = 0;
     L.state[1] = 0;
+    L.state[2] = 0;
+    L.state[3] = 0;
     L.beta[0] = 0.0;
+    L.omega[0] = 1.0;   // <v_0, v_0>; the row before it is empty
   }
 }
 
@@ -187,46 +196,22 @@ __device__ void block_multidot(const LanczosDev& L, int m, int64_t c0, int64_t c
   }
 }
 
-__global__ void __launch_bounds__(MD_T) multidot_kernel(LanczosDev L, int m, int vb) {
+__global__ void __launch_bounds__(MD_T) multidot_kernel(LanczosDev L, int m, int vb, int gate) {
   tnx_grid_dependency();
   __shared__ double sh[16][MD_T + 1];
-  if (stopped(L.state)) return;
+  if (stopped(L.state) || gated_off(L.state, gate)) return;
   const int64_t chunk = (L.n + gridDim.x - 1) / gridDim.x;
   const int64_t c0 = chunk * blockIdx.x, c1 = min(L.n, c0 + chunk);
   block_multidot(L, m, c0, c1, sh, vb);
 }
 
-// The three-term step fused with the Gram-Schmidt dots: each block forms
-// w <- (w - alpha_j v_j) - beta_j v_{j-1} on its own chunk (v_{-1} absent), then
-// the chunk's dots of the new w against v_0 .. v_{m-1}, every thread reading
-// back only the entries it wrote.
-__global__ void __launch_bounds__(MD_T) three_term_multidot_kernel(LanczosDev L, int m, int j) {
-  tnx_grid_dependency();
-  __shared__ double sh[16][MD_T + 1];
-  if (stopped(L.state)) return;
-  const double a = L.alpha[j], b = j > 0 ? L.beta[j] : 0.0;
-  const double* vj = L.V + (int64_t)j * L.n;
-  const double* vp = L.V + (int64_t)(j > 0 ? j - 1 : 0) * L.n;
-  const int64_t chunk = (L.n + gridDim.x - 1) / gridDim.x;
-  const int64_t c0 = chunk * blockIdx.x, c1 = min(L.n, c0 + chunk);
-  if (j > 0) {
-    for (int64_t x = c0 + threadIdx.x; x < c1; x += MD_T) {
-      const double w = L.w[x] - a * vj[x];
-      L.w[x] = w - b * vp[x];
-    }
-  } else {
-    for (int64_t x = c0 + threadIdx.x; x < c1; x += MD_T) L.w[x] = L.w[x] - a * vj[x];
-  }
-  block_multidot(L, m, c0, c1, sh);
-}
-
 // coef[i] = sum_b partial[b*m + i]   (one block per i, fixed order);
 // the sum of row alpha_i (if >= 0) is also alpha_j = <v_j, H v_j>.
 __global__ void __launch_bounds__(RT) multidot_finalize_kernel(LanczosDev L, int m, int nb, int alpha_i,
-                                                               int alpha_j) {
+                                                               int alpha_j, int gate) {
   tnx_grid_dependency();
   __shared__ double sh[32];
-  if (stopped(L.state)) return;
+  if (stopped(L.state) || gated_off(L.state, gate)) return;
   const int i = blockIdx.x;
   double acc = 0.0;
   for (int b = threadIdx.x; b < nb; b += RT) acc += L.partial[(int64_t)b * m + i];
@@ -239,11 +224,11 @@ __global__ void __launch_bounds__(RT) multidot_finalize_kernel(LanczosDev L, int
 
 // w -= sum_i coef[i] V_i; with norm != 0 also partial[b] = sum of the new w^2
 // over this block's grid-stride share (fixed order).
-__global__ void __launch_bounds__(RT) gs_update_kernel(LanczosDev L, int m, int norm) {
+__global__ void __launch_bounds__(RT) gs_update_kernel(LanczosDev L, int m, int norm, int gate) {
   tnx_grid_dependency();
   __shared__ double c[512];
   __shared__ double sh[32];
-  if (stopped(L.state)) return;
+  if (stopped(L.state) || gated_off(L.state, gate)) return;
   for (int i = threadIdx.x; i < m; i += RT) c[i] = L.coef[i];
   __syncthreads();
   double nrm = 0.0;
@@ -281,11 +266,11 @@ __global__ void __launch_bounds__(RT) gs_update_kernel(LanczosDev L, int m, int 
 // beta_{j+1} = sqrt(sum of the norm partials); decide stop; record k; point
 // the next apply's input slot at v_{j+1} (which the next kernel writes)
 __global__ void __launch_bounds__(RT) lanczos_beta_decide_kernel(LanczosDev L, int j, int nb, int last,
-                                                                 double** next_slot) {
+                                                                 double** next_slot, int gate) {
   tnx_grid_dependency();
   __shared__ double sh[32];
   __shared__ double s_amax;
-  if (stopped(L.state)) return;
+  if (stopped(L.state) || gated_off(L.state, gate)) return;
   double acc = 0.0;
   for (int b = threadIdx.x; b < nb; b += RT) acc += L.partial[b];
   if (threadIdx.x < 32) {
@@ -305,6 +290,131 @@ __global__ void __launch_bounds__(RT) lanczos_beta_decide_kernel(LanczosDev L, i
     if (last || beta < 1e-14 * s_amax) L.state[1] = 1;
     else *next_slot = L.V + (int64_t)(j + 1) * L.n;
   }
+}
+
+// The three-term step w <- (w - alpha_j v_j) - beta_j v_{j-1} (beta_0 = 0), with
+// partial[b] = this block's share of the new |w|^2 (fixed order).
+__global__ void __launch_bounds__(RT) three_term_norm_kernel(LanczosDev L, int j) {
+  tnx_grid_dependency();
+  __shared__ double sh[32];
+  if (stopped(L.state)) return;
+  const double a = L.alpha[j], b = j > 0 ? L.beta[j] : 0.0;
+  const double* vj = L.V + (int64_t)j * L.n;
+  const double* vp = L.V + (int64_t)(j > 0 ? j - 1 : 0) * L.n;
+  double nrm = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * RT;
+  int64_t x = (int64_t)blockIdx.x * RT + threadIdx.x;
+  for (; x + stride < L.n; x += 2 * stride) {
+    const double w0 = L.w[x], w1 = L.w[x + stride];
+    const double a0 = vj[x], a1 = vj[x + stride];
+    const double p0 = vp[x], p1 = vp[x + stride];
+    const double u0 = (w0 - a * a0) - b * p0, u1 = (w1 - a * a1) - b * p1;
+    L.w[x] = u0;
+    L.w[x + stride] = u1;
+    nrm = fma(u0, u0, nrm);
+    nrm = fma(u1, u1, nrm);
+  }
+  if (x < L.n) {
+    const double u = (L.w[x] - a * vj[x]) - b * vp[x];
+    L.w[x] = u;
+    nrm = fma(u, u, nrm);
+  }
+  nrm = block_sum(nrm, sh);
+  if (threadIdx.x == 0) L.partial[blockIdx.x] = nrm;
+}
+
+// Partial reorthogonalisation (Simon, Math. Comp. 42, 1984): omega_{j,k}
+// estimates <v_j, v_k> through the recurrence that the Lanczos relation gives,
+//   beta_{j+1} omega_{j+1,k} = beta_{k+1} omega_{j,k+1} + (alpha_k - alpha_j) omega_{j,k}
+//                              + beta_k omega_{j,k-1} - beta_j omega_{j-1,k} + rounding,
+// with the rounding term taken as sign(.) eps1 |T| (eps1 = sqrt(n) eps / 2, |T|
+// bounded by max_i |alpha_i| + beta_i + beta_{i+1}) and omega_{j+1,j} =
+// eps1 |T| / beta_{j+1}.  After the three-term step this kernel forms
+// beta_{j+1} = |w| and the estimates of row j+1; the step takes a full
+// Gram-Schmidt pass against v_0..v_j when the largest estimate exceeds
+// tau (1e-10; a negative tau: every step), and so does the step after it (the error that v_j carries reaches
+// v_{j+2} too); after a pass the estimates restart at eps1.  Without a pass
+// this kernel also does what the beta kernel does (beta_{j+1}, the stopping
+// test, the next input slot); with one, the gated launches after it do.
+constexpr int PRO_MAX = 514;   // rows of at most 500 steps + 2
+
+__global__ void __launch_bounds__(RT) pro_decide_kernel(LanczosDev L, int j, int nb, int last, double** next_slot,
+                                                        double tau) {
+  tnx_grid_dependency();
+  __shared__ double sh[32];
+  __shared__ double s_om[PRO_MAX];
+  __shared__ double s_b, s_amax, s_anorm, s_mx[RT / 32];
+  __shared__ int s_pass;
+  if (stopped(L.state)) return;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += RT) acc += L.partial[b];
+  if (threadIdx.x < 32) {
+    double amax = 0.0, an = 0.0;
+    for (int i = threadIdx.x; i <= j; i += 32) {
+      amax = fmax(amax, fmax(fabs(L.alpha[i]), L.beta[i]));
+      an = fmax(an, fabs(L.alpha[i]) + L.beta[i] + (i < j ? L.beta[i + 1] : 0.0));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      an = fmax(an, __shfl_xor_sync(0xffffffffu, an, o));
+    }
+    if (threadIdx.x == 0) {
+      s_amax = amax;
+      s_anorm = an;
+    }
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) s_b = sqrt(acc);
+  __syncthreads();
+  const double bn = s_b;
+  const double anorm = fmax(s_anorm, fabs(L.alpha[j]) + (j > 0 ? L.beta[j] : 0.0) + bn);
+  const double eps1 = sqrt((double)L.n) * 0.5 * 2.220446049250313e-16;
+  const double* om = L.omega;                  // row j: k = 0..j
+  const double* omp = L.omega + (L.nmax + 2);  // row j-1: k = 0..j-1
+  double mx = 0.0;
+  for (int k = threadIdx.x; k <= j; k += RT) {
+    double e;
+    if (k < j) {
+      double t = L.beta[k + 1] * om[k + 1] + (L.alpha[k] - L.alpha[j]) * om[k] - L.beta[j] * omp[k];
+      if (k > 0) t += L.beta[k] * om[k - 1];
+      e = (t + copysign(eps1 * anorm, t)) / bn;
+    } else {
+      e = eps1 * anorm / bn;
+    }
+    s_om[k] = e;
+    // beta_{j+1} = 0 or an overflowing estimate counts as lost orthogonality
+    mx = (fabs(e) <= 1e300) ? fmax(mx, fabs(e)) : INFINITY;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < RT / 32; ++w) m = fmax(m, s_mx[w]);
+    const int forced = L.state[3];
+    const int pass = forced || !(m <= tau);
+    s_pass = pass;
+    L.state[2] = pass;
+    L.state[3] = pass && !forced;
+    if (!pass) {
+      L.beta[j + 1] = bn;
+      L.scratch[3 * L.nmax + 3] = 1.0 / bn;   // for the normalising kernel
+      L.state[0] = j + 1;
+      if (last || bn < 1e-14 * s_amax) L.state[1] = 1;
+      else *next_slot = L.V + (int64_t)(j + 1) * L.n;
+    }
+  }
+  __syncthreads();
+  // shift the rows: row j becomes row j-1, the new estimates row j+1
+  double* cur = L.omega;
+  double* prev = L.omega + (L.nmax + 2);
+  for (int k = threadIdx.x; k <= j; k += RT) {
+    prev[k] = cur[k];
+    cur[k] = s_pass ? eps1 : s_om[k];
+  }
+  if (threadIdx.x == 0) cur[j + 1] = 1.0;
 }
 
 __global__ void lanczos_normalize_kernel(LanczosDev L, int j) {
@@ -507,46 +617,54 @@ cudaError_t tnx_launch_lanczos_set_input(double** slot_ptr, const LanczosDev& L,
 // The operator has been applied: L.w = H v_j.  One Lanczos step (without the
 // final v_{j+1} = w / beta_{j+1} when `normalize` is false: the caller then
 // fuses it with the next apply's relayout of the vector): alpha_j = <v_j, w>;
-// the three-term step w <- w - alpha_j v_j - beta_j v_{j-1} fused with the dots
-// c = V^T w against v_0..v_j; one classical Gram-Schmidt update w <- w - V c
-// with the norm's partial sums; then beta_{j+1}, the stopping test and
-// v_{j+1} = w / beta_{j+1}.  The three-term step removes the large components
-// of H v_j, so the Gram-Schmidt pass removes only rounding-level ones and
-// leaves w orthogonal to the basis to working precision; a second pass would
-// change w by about eps |w| (the "twice is enough" criterion: a repeat is due
-// only when a pass shrinks |w| by more than about 1/sqrt(2)).  FP64 work per
-// entry: 2 (j + 1) + 3 fused multiply-adds.
-cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, double** next_slot, cudaStream_t st, bool normalize) {
+// the three-term step w <- w - alpha_j v_j - beta_j v_{j-1} with |w|; the
+// orthogonality estimates, which decide whether this step takes a classical
+// Gram-Schmidt pass c = V^T w, w <- w - V c against v_0..v_j (the gated
+// launches: a step without the pass returns from them at once); then
+// beta_{j+1}, the stopping test and v_{j+1} = w / beta_{j+1}.  FP64 work per
+// entry: 3 fused multiply-adds, plus 2 (j + 1) + 1 in a step with the pass.
+cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, double** next_slot, cudaStream_t st, bool normalize,
+                                    bool always_pass) {
+  if (j + 2 > PRO_MAX) return cudaErrorInvalidValue;
+  const double tau = always_pass ? -1.0 : 1e-10;
   const int nb = grid_for(L.n);
   const int m = j + 1;
   const int mb = multidot_blocks(L.n);
+  const int last = j == L.nmax - 1;
   {
-    const cudaError_t le = tnx_launch(multidot_kernel, dim3(mb), dim3(MD_T), 0, st, L, 1, j);
+    const cudaError_t le = tnx_launch(multidot_kernel, dim3(mb), dim3(MD_T), 0, st, L, 1, j, 0);
     if (le != cudaSuccess) return le;
   }
   {
-    const cudaError_t le = tnx_launch(multidot_finalize_kernel, dim3(1), dim3(RT), 0, st, L, 1, mb, 0, j);
+    const cudaError_t le = tnx_launch(multidot_finalize_kernel, dim3(1), dim3(RT), 0, st, L, 1, mb, 0, j, 0);
     if (le != cudaSuccess) return le;
   }
   {
-    const cudaError_t le = tnx_launch(three_term_multidot_kernel, dim3(mb), dim3(MD_T), 0, st, L, m, j);
+    const cudaError_t le = tnx_launch(three_term_norm_kernel, dim3(nb), dim3(RT), 0, st, L, j);
     if (le != cudaSuccess) return le;
   }
   {
-    const cudaError_t le = tnx_launch(multidot_finalize_kernel, dim3(m), dim3(RT), 0, st, L, m, mb, -1, 0);
+    const cudaError_t le = tnx_launch(pro_decide_kernel, dim3(1), dim3(RT), 0, st, L, j, nb, last, next_slot, tau);
     if (le != cudaSuccess) return le;
   }
   {
-    const cudaError_t le = tnx_launch(gs_update_kernel, dim3(nb), dim3(RT), 0, st, L, m, 1);
+    const cudaError_t le = tnx_launch(multidot_kernel, dim3(mb), dim3(MD_T), 0, st, L, m, 0, 1);
     if (le != cudaSuccess) return le;
   }
-  tnx_note_launch(5);
+  {
+    const cudaError_t le = tnx_launch(multidot_finalize_kernel, dim3(m), dim3(RT), 0, st, L, m, mb, -1, 0, 1);
+    if (le != cudaSuccess) return le;
+  }
+  {
+    const cudaError_t le = tnx_launch(gs_update_kernel, dim3(nb), dim3(RT), 0, st, L, m, 1, 1);
+    if (le != cudaSuccess) return le;
+  }
   {
     const cudaError_t le = tnx_launch(lanczos_beta_decide_kernel, dim3(1), dim3(RT), 0, st,
-                                      L, j, nb, j == L.nmax - 1, next_slot);
+                                      L, j, nb, last, next_slot, 1);
     if (le != cudaSuccess) return le;
   }
-  tnx_note_launch(1);
+  tnx_note_launch(8);
   if (normalize) {
     {
       const cudaError_t le = tnx_launch(lanczos_normalize_kernel, dim3(nb), dim3(RT), 0, st, L, j);

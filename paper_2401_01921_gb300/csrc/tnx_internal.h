@@ -338,7 +338,9 @@ struct LanczosDev {
   double* partial;    // [nblocks * (nmax+1)]
   double* y;          // [nmax]    Ritz coefficients
   double* scratch;    // [4*nmax]
-  int32_t* state;     // [0] = active steps done (k), [1] = stopped flag
+  int32_t* state;     // [0] = active steps done (k), [1] = stopped flag, [2] = this step reorthogonalises,
+                      // [3] = the next step must reorthogonalise too
+  double* omega;      // [2][nmax+2] estimates of <v_j, v_k> (row j, then row j-1)
   double* eval;       // [1]
   int64_t n;
   int nmax;
@@ -347,6 +349,8 @@ struct LanczosDev {
 cudaError_t tnx_launch_lanczos_init(const LanczosDev& L, const double* v0, cudaStream_t st);
 cudaError_t tnx_launch_lanczos_set_input(double** slot_ptr, const LanczosDev& L, int j, cudaStream_t st);
 // normalize = false leaves out v_{j+1} = w / beta_{j+1} (1 / beta_{j+1} is in
-// scratch[3 * nmax + 3]) for the caller to fuse with its next relayout
-cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, double** next_slot, cudaStream_t st, bool normalize);
+// scratch[3 * nmax + 3]) for the caller to fuse with its next relayout;
+// always_pass: a Gram-Schmidt pass in every step (an operator far from symmetric)
+cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, double** next_slot, cudaStream_t st, bool normalize,
+                                    bool always_pass);
 cudaError_t tnx_launch_lanczos_finish(const LanczosDev& L, double* evec, cudaStream_t st);

@@ -1957,11 +1957,11 @@ tnx_network::~tnx_network() = default;
 
 namespace {
 // Bytes of the Lanczos workspace buffers, in allocation order: V, w, alpha,
-// beta, coef, partial sums, y, scratch, state, eval.
+// beta, coef, partial sums, y, scratch, state, eval, omega.
 std::vector<size_t> lanczos_buffer_sizes(int64_t n, int nsteps) {
   return {(size_t)(nsteps + 1) * n * 8, (size_t)n * 8, (size_t)(nsteps + 1) * 8, (size_t)(nsteps + 2) * 8,
           (size_t)(nsteps + 2) * 8, (size_t)std::max<int64_t>(1216, (int64_t)608 * (nsteps + 2)) * 8,
-          (size_t)(nsteps + 1) * 8, (size_t)(4 * (nsteps + 1)) * 8, 64, 64};
+          (size_t)(nsteps + 1) * 8, (size_t)(4 * (nsteps + 1)) * 8, 64, 64, (size_t)(2 * (nsteps + 2)) * 8};
 }
 }  // namespace
 
@@ -2020,6 +2020,7 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
     L.scratch = (double*)dev(sz[7]);
     L.state = (int32_t*)dev(sz[8]);
     L.eval = (double*)dev(sz[9]);
+    L.omega = (double*)dev(sz[10]);
   }
   LanczosDev& L = lc->L;
   bind_inputs(net, *p);
@@ -2081,10 +2082,13 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
         }
         ctx->prof = prof;
       }
-      // bytes of one step: two Gram-Schmidt passes over j+1 vectors (dots
-      // (j+1)n + n, update (j+1)n + 2n), norm folded in, scale (2n)
-      ProfScope ps(ctx, st, TNX_KC_VECTOR, 8.0 * (double)n * (2 * (2.0 * (j + 1) + 3) + 2));
-      CUDA_CHECK(tnx_launch_lanczos_step(L, j, p->d_slots + slot, st, vcopy == nullptr));
+      // bytes of a step without the Gram-Schmidt pass: alpha (2n), the
+      // three-term step with the norm (4n), scale (2n); a step that takes the
+      // pass (decided on the device) adds (j+1)n + n for the dots and
+      // (j+1)n + 2n for the update
+      ProfScope ps(ctx, st, TNX_KC_VECTOR, 8.0 * (double)n * 8);
+      CUDA_CHECK(tnx_launch_lanczos_step(L, j, p->d_slots + slot, st, vcopy == nullptr,
+                                         p->prec == TNX_PREC_F32 || p->prec == TNX_PREC_TF32));
       if (vcopy)
         CUDA_CHECK(tnx_launch_copy_scaled(vcopy->d, vcopy->chunks, vcopy->nchunks, p->d_slots, L.w,
                                           L.V + (int64_t)(j + 1) * n, n, vfull, L.scratch + 3 * L.nmax + 3, L.state,

@@ -47,3 +47,19 @@ def test_batched_chis_log_uniform():
     assert len(c) == 256 and min(c) >= 64 and max(c) <= 1024
     m = np.mean([math.log2(x) for x in c])
     assert 7.6 < m < 8.4
+
+
+def test_symmetrised_heff_is_hermitian_with_and_without_sector_scaling():
+    """The symmetrised environments make the two-site H_eff Hermitian (a Lanczos solve assumes it):
+    x.(H y) = y.(H x) to rounding, also when the sectors are scaled over three decades."""
+    from oracle import heff as oheff
+    for wl in (I.heisenberg_workload(96, 9), I.heisenberg_workload(96, 9, sector_scale=True),
+               I.hubbard_workload(64)):
+        net, T = oheff.make_heff(wl, symmetric=True)
+        ap = oheff.flat_apply(net, T["psi"])
+        n = T["psi"].flat().size
+        rng = np.random.default_rng(5)
+        x, y = rng.standard_normal(n), rng.standard_normal(n)
+        hx, hy = ap(x), ap(y)
+        asym = abs(x @ hy - y @ hx) / (np.linalg.norm(hx) * np.linalg.norm(y))
+        assert asym <= 1e-13, (wl.name, asym)

@@ -410,8 +410,12 @@ def heff_value_fn(wl: Workload, name: str, symmetric: bool = False):
     L, R, psi: N(0,1) from (seed, stream, row-major dense index); with
     ``symmetric``, L[a,w,a'] <- (L[a,w,a'] + L[a',wbar,a]) / 2 and the same for R,
     where wbar swaps the S+ / S- channels (Heisenberg) or the c / c+ channels
-    (Hubbard).  With ``wl.sector_scale``, every element is multiplied by
-    10^(-3 u) with u ~ U(0,1] drawn per sector of the first leg.  W: the MPO.
+    (Hubbard).  With ``wl.sector_scale``, every element of psi is multiplied by
+    10^(-3 u) with u ~ U(0,1] drawn per sector of its first leg, and every element
+    of L and R by 10^(-3 (u + u') / 2), u and u' drawn for the sectors of the two
+    virtual legs (first and last, which carry the same sectors): the same range,
+    and the symmetrised environments stay symmetric, so H_eff stays Hermitian.
+    W: the MPO.
     """
     bonds = heff_bonds(wl)[name]
     dims = [sum(d for _, d in secs) for _, secs in bonds]
@@ -447,8 +451,10 @@ def heff_value_fn(wl: Workload, name: str, symmetric: bool = False):
             v = 0.5 * (v + normal_at(seed, stream, flat([c[2], bar[c[1]], c[0]])))
         if wl.sector_scale:
             secs = bonds[0][1]
-            k = _sector_of(secs, c[0])
-            u = uniform_at(wl.seeds["scale"], stream, k)
+            u = uniform_at(wl.seeds["scale"], stream, _sector_of(secs, c[0]))
+            if name in ("L", "R"):
+                u2 = uniform_at(wl.seeds["scale"], stream, _sector_of(bonds[2][1], c[2]))
+                u = 0.5 * (u + u2)
             v = v * np.power(10.0, -3.0 * u)
         return v
 
