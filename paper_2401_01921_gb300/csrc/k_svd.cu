@@ -134,37 +134,39 @@ __global__ void __launch_bounds__(JT) jacobi_round_kernel(const SvdGroup* __rest
 // round, so its pairs go to as many SMs as there are pairs.  After each sweep
 // the CTAs read the largest squared relative off-diagonal of that sweep
 // (offmax[sweep], zeroed by the host) behind a barrier and all stop together
-// once it is at most tol2 (the launcher squares tol).  The barrier is a
-// counter plus a generation word; every wait on it is bounded (about a second
-// of clock): on expiry the CTA sets *status and leaves, and so do the others
-// at their next barrier.  sweeps_out[0] receives the number of sweeps run.
+// once it is at most tol2 (the launcher squares tol).  The barrier is one
+// 64-bit arrival counter that only grows (a release add to arrive, acquire
+// loads to wait); every wait on it is bounded (about a second of clock): on
+// expiry the CTA sets *status and leaves, and so do the others at their next
+// barrier.  sweeps_out[0] receives the number of sweeps run.
 constexpr long long BAR_LIMIT = 2000000000LL;
 
-__device__ bool grid_barrier(unsigned int* count, volatile unsigned int* gen, int* status) {
+__device__ bool grid_barrier(unsigned long long* count, int* status) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    int ok = *(volatile int*)status == 0;
-    const unsigned int g = *gen;
-    __threadfence();
-    if (ok) {
-      if (atomicAdd(count, 1u) == gridDim.x - 1) {
-        *count = 0;
-        __threadfence();
-        atomicAdd((unsigned int*)gen, 1u);
-      } else {
-        const long long t0 = clock64();
-        while (*gen == g) {
-          if (*(volatile int*)status != 0) { ok = 0; break; }
-          if (clock64() - t0 > BAR_LIMIT) {
-            atomicExch(status, 1);
-            ok = 0;
-            break;
-          }
-        }
+    // every CTA passes the same barriers in the same order, so the count
+    // before this arrival lies in [k G, (k+1) G) for barrier k of a grid of
+    // G CTAs; the barrier opens when it reaches (k+1) G
+    int ok = 1;
+    unsigned long long old;
+    asm volatile("atom.add.release.gpu.u64 %0, [%1], 1;" : "=l"(old) : "l"(count) : "memory");
+    const unsigned long long target = (old / gridDim.x + 1) * (unsigned long long)gridDim.x;
+    const long long t0 = clock64();
+    for (;;) {
+      unsigned long long cur;
+      asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(cur) : "l"(count) : "memory");
+      if (cur >= target) break;
+      if (*(volatile int*)status != 0) {
+        ok = 0;
+        break;
+      }
+      if (clock64() - t0 > BAR_LIMIT) {
+        atomicExch(status, 1);
+        ok = 0;
+        break;
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
@@ -179,13 +181,14 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+constexpr int VB = 8;     // vector entries per lane held in registers by the cooperative kernel
 constexpr int CJT = 32;   // threads per CTA of the cooperative kernel: one pair-warp per CTA, so that the
                           // pairs of a round spread over as many SMs (and FP64 pipes) as there are pairs
 
 __global__ void __launch_bounds__(CJT) jacobi_coop_kernel(const SvdGroup* __restrict__ groups,
                                                          const int2* __restrict__ slots, int nslots, int maxcp,
                                                          int max_sweeps, double tol2, unsigned long long* offmax,
-                                                         unsigned int* bar, int* status, int* sweeps_out) {
+                                                         unsigned long long* bar, int* status, int* sweeps_out) {
   // one warp per pair: the pairs of a round run side by side over the whole grid
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (CJT / 32) + (threadIdx.x >> 5), nwarps = gridDim.x * (CJT / 32);
@@ -213,12 +216,37 @@ __global__ void __launch_bounds__(CJT) jacobi_coop_kernel(const SvdGroup* __rest
         if (q >= g.c) continue;         // the pad index
         double* xp = g.X + (int64_t)p * g.r;
         double* xq = g.X + (int64_t)q * g.r;
+        double* jp = g.J + (int64_t)p * g.c;
+        double* jq = g.J + (int64_t)q * g.c;
+        // vectors and J rows of up to 32 VB entries stay in registers between
+        // the dots and the rotation: every load of the pair is issued at once
+        // (one trip to L2 instead of one per 32 entries)
+        const bool in_regs = g.r <= 32 * VB && g.c <= 32 * VB;
+        double u[VB], v[VB], ju[VB], jv[VB];
         double a = 0.0, b = 0.0, c = 0.0;
-        for (int64_t e = lane; e < g.r; e += 32) {
-          const double u = xp[e], v = xq[e];
-          a = fma(u, u, a);
-          b = fma(v, v, b);
-          c = fma(u, v, c);
+        if (in_regs) {
+#pragma unroll
+          for (int k = 0; k < VB; ++k) {
+            const int e = lane + 32 * k;
+            u[k] = e < g.r ? xp[e] : 0.0;
+            v[k] = e < g.r ? xq[e] : 0.0;
+            ju[k] = e < g.c ? jp[e] : 0.0;
+            jv[k] = e < g.c ? jq[e] : 0.0;
+          }
+#pragma unroll
+          for (int k = 0; k < VB; ++k) {
+            a = fma(u[k], u[k], a);
+            b = fma(v[k], v[k], b);
+            c = fma(u[k], v[k], c);
+          }
+        } else {
+#pragma unroll 4
+          for (int64_t e = lane; e < g.r; e += 32) {
+            const double uu = xp[e], vv = xq[e];
+            a = fma(uu, uu, a);
+            b = fma(vv, vv, b);
+            c = fma(uu, vv, c);
+          }
         }
         a = warp_sum(a);
         b = warp_sum(b);
@@ -241,21 +269,36 @@ __global__ void __launch_bounds__(CJT) jacobi_coop_kernel(const SvdGroup* __rest
           if (zeta < 0.0) t = -t;
         }
         const double cs = rsqrt(fma(t, t, 1.0)), sn = cs * t;
-        for (int64_t e = lane; e < g.r; e += 32) {
-          const double u = xp[e], v = xq[e];
-          xp[e] = cs * u - sn * v;
-          xq[e] = sn * u + cs * v;
-        }
-        double* jp = g.J + (int64_t)p * g.c;
-        double* jq = g.J + (int64_t)q * g.c;
-        for (int e = lane; e < g.c; e += 32) {
-          const double u = jp[e], v = jq[e];
-          jp[e] = cs * u - sn * v;
-          jq[e] = sn * u + cs * v;
+        if (in_regs) {
+#pragma unroll
+          for (int k = 0; k < VB; ++k) {
+            const int e = lane + 32 * k;
+            if (e < g.r) {
+              xp[e] = cs * u[k] - sn * v[k];
+              xq[e] = sn * u[k] + cs * v[k];
+            }
+            if (e < g.c) {
+              jp[e] = cs * ju[k] - sn * jv[k];
+              jq[e] = sn * ju[k] + cs * jv[k];
+            }
+          }
+        } else {
+#pragma unroll 4
+          for (int64_t e = lane; e < g.r; e += 32) {
+            const double uu = xp[e], vv = xq[e];
+            xp[e] = cs * uu - sn * vv;
+            xq[e] = sn * uu + cs * vv;
+          }
+#pragma unroll 4
+          for (int e = lane; e < g.c; e += 32) {
+            const double uu = jp[e], vv = jq[e];
+            jp[e] = cs * uu - sn * vv;
+            jq[e] = sn * uu + cs * vv;
+          }
         }
       }
       if (lane == 0 && off_w > 0.0) atomicMax(&offmax[sw], (unsigned long long)__double_as_longlong(off_w));
-      ok = grid_barrier(bar, bar + 1, status);
+      ok = grid_barrier(bar, status);
     }
     if (!ok) break;
     const double off = __longlong_as_double((long long)*(volatile unsigned long long*)&offmax[sw]);
@@ -263,6 +306,229 @@ __global__ void __launch_bounds__(CJT) jacobi_coop_kernel(const SvdGroup* __rest
     if (off <= tol2) break;   // every warp reads the same value behind the last barrier
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) sweeps_out[0] = sw;
+}
+
+// ---------------------------------------------------------------------------
+// QR preconditioning (Drmac and Veselic, SIAM J. Matrix Anal. Appl. 29, 2008):
+// one-sided Jacobi on the rows of the triangular factor of a column-pivoted
+// QR needs far fewer sweeps than on the block itself when the singular values
+// are graded (as in a DMRG wavefunction), since those rows are already close
+// to orthogonal.  With A = X^T (r x c) and A P = Q R:
+//   R = Jr^T Sigma W (Jacobi on the rows of R), so A = (Q Jr^T) Sigma (W P^T):
+//   the left singular vectors of A are u_p = Q Jr[p,:]^T, the right ones the
+//   rows of W with their columns put back through P.
+// The QR is Householder's, in the form of LAPACK's dlarfg: for the pivot
+// column x = A[k.., k], beta = -sign(x_0) |x|, tau = (beta - x_0) / beta,
+// v = (1, x_1 / (x_0 - beta), ...), H = I - tau v v^T, H x = beta e_0 (tau = 0
+// when x_1.. = 0); the pivot is the column with the largest remaining norm.
+
+// Reflector of the column x[0 .. len): all lanes get beta, tau, scale (v_i =
+// x_i scale for i >= 1).  The same lanes read the same entries every time, so
+// each call on the same data returns the same bits.
+__device__ __forceinline__ void reflector(const double* x, int len, int lane, double& beta, double& tau,
+                                          double& scale) {
+  double s = 0.0;
+  for (int i = lane; i < len; i += 32)
+    if (i > 0) s = fma(x[i], x[i], s);
+  s = warp_sum(s);
+  const double x0 = x[0];
+  if (s == 0.0) {
+    beta = x0;
+    tau = 0.0;
+    scale = 0.0;
+    return;
+  }
+  const double nrm = sqrt(fma(x0, x0, s));
+  beta = x0 >= 0.0 ? -nrm : nrm;
+  tau = (beta - x0) / beta;
+  scale = 1.0 / (x0 - beta);
+}
+
+// Writes the reflector of pivot position k (vector u) in place: X[u][k] =
+// beta (the diagonal of R), X[u][k+i] = v_i for i >= 1, tau[k].  Called once
+// nothing reads that column any more.
+__device__ void reflector_store(const SvdQr& q, int k, int u, int lane) {
+  double* x = q.X + (int64_t)u * q.r + k;
+  const int len = q.r - k;
+  double beta, tau, scale;
+  reflector(x, len, lane, beta, tau, scale);
+  __syncwarp();   // every lane has read x[0] before lane 0 replaces it
+  for (int i = lane; i < len; i += 32) x[i] = i == 0 ? beta : x[i] * scale;
+  if (lane == 0) q.tau[k] = tau;
+}
+
+// The pivoted QR of every block: a slot is (block, position j); step k runs
+// behind a grid barrier.  Every warp of a block reads the same trailing norms
+// and picks the same pivot (largest, lowest position on ties), so the
+// permutation needs no exchange; positions and norms alternate between two
+// buffers from step to step.  The warp of position k records the pivot and
+// stores the reflector of step k - 1 (and, at the last step, that of step
+// k); the warps of positions j > k apply the step-k reflector to their vector
+// and write its new trailing norm, summed from the updated entries.
+__global__ void __launch_bounds__(CJT) qr_coop_kernel(const SvdQr* __restrict__ qs, const int2* __restrict__ slots,
+                                                      int nslots, int maxc, unsigned long long* bar, int* status) {
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (CJT / 32) + (threadIdx.x >> 5), nwarps = gridDim.x * (CJT / 32);
+  for (int si = gw; si < nslots; si += nwarps) {
+    const int2 sl = slots[si];
+    const SvdQr q = qs[sl.x];
+    const double* x = q.X + (int64_t)sl.y * q.r;
+    double s = 0.0;
+    for (int i = lane; i < q.r; i += 32) s = fma(x[i], x[i], s);
+    s = warp_sum(s);
+    if (lane == 0) {
+      q.nrm[sl.y] = s;
+      q.pos[sl.y] = sl.y;
+    }
+  }
+  bool ok = grid_barrier(bar, status);
+  for (int k = 0; k < maxc && ok; ++k) {
+    const int cur = k & 1, nxt = cur ^ 1;
+    for (int si = gw; si < nslots; si += nwarps) {
+      const int2 sl = slots[si];
+      const SvdQr q = qs[sl.x];
+      const int j = sl.y;
+      if (k >= q.c || j < k) continue;
+      const double* nr = q.nrm + (int64_t)cur * q.c;
+      const int32_t* ps = q.pos + (int64_t)cur * q.c;
+      double best = -1.0;
+      int bp = q.c;
+      for (int i = k + lane; i < q.c; i += 32) {
+        const double v = nr[i];
+        if (v > best) {
+          best = v;
+          bp = i;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        if (ob > best || (ob == best && op < bp)) {
+          best = ob;
+          bp = op;
+        }
+      }
+      if (bp >= q.c) bp = k;   // no comparable norm (NaN): no exchange
+      const int pv = ps[bp], kv = ps[k];
+      if (j == k) {
+        if (lane == 0) q.perm[k] = pv;
+        if (k > 0) reflector_store(q, k - 1, q.perm[k - 1], lane);
+        if (k == q.c - 1) reflector_store(q, k, pv, lane);
+        continue;
+      }
+      const int vj = j == bp ? kv : ps[j];
+      const double* xp = q.X + (int64_t)pv * q.r + k;
+      double* a = q.X + (int64_t)vj * q.r + k;
+      const int len = q.r - k;
+      double beta, tau, scale;
+      reflector(xp, len, lane, beta, tau, scale);
+      double ns = 0.0;
+      if (tau != 0.0) {
+        double w = 0.0;
+        for (int i = lane; i < len; i += 32) w = fma(i == 0 ? 1.0 : xp[i] * scale, a[i], w);
+        w = warp_sum(w);
+        const double tw = tau * w;
+        for (int i = lane; i < len; i += 32) {
+          const double ai = fma(-tw, i == 0 ? 1.0 : xp[i] * scale, a[i]);
+          a[i] = ai;
+          if (i > 0) ns = fma(ai, ai, ns);
+        }
+      } else {
+        for (int i = lane; i < len; i += 32)
+          if (i > 0) ns = fma(a[i], a[i], ns);
+      }
+      ns = warp_sum(ns);
+      if (lane == 0) {
+        q.nrm[(int64_t)nxt * q.c + j] = ns;
+        q.pos[(int64_t)nxt * q.c + j] = vj;
+      }
+    }
+    ok = grid_barrier(bar, status);
+  }
+}
+
+// Xr[p][j] = R[p][j] = X[perm[j]][p] for j >= p (0 below the diagonal), Jr = I
+__global__ void qr_gather_r_kernel(const SvdQr* __restrict__ qs, int nq) {
+  tnx_grid_dependency();
+  for (int gi = blockIdx.y; gi < nq; gi += gridDim.y) {
+    const SvdQr q = qs[gi];
+    const int64_t n = (int64_t)q.c * q.c;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+      const int p = (int)(e / q.c), j = (int)(e % q.c);
+      q.Xr[e] = j >= p ? q.X[(int64_t)q.perm[j] * q.r + p] : 0.0;
+      q.Jr[e] = p == j ? 1.0 : 0.0;
+    }
+  }
+}
+
+// One warp per (block, vector p), after the Jacobi on the rows of R:
+// sigma_p = |Xr[p,:]|; J[p][perm[i]] = Xr[p][i] / sigma_p (the right singular
+// vector of A, 0 when sigma_p = 0); Xf[p,:] = sigma_p Q Jr[p,:]^T, with Q
+// applied as H_0 H_1 ... H_{c-1} to (Jr[p,:], 0, ..., 0).  Lane l keeps the
+// entries e = l (mod 32) of z throughout, in registers when r <= 32 VB.
+__global__ void qr_apply_kernel(const SvdQr* __restrict__ qs, const int2* __restrict__ vecs, int nvec) {
+  tnx_grid_dependency();
+  const int lane = threadIdx.x & 31;
+  for (int vi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vi < nvec; vi += gridDim.x * (blockDim.x >> 5)) {
+    const int2 gv = vecs[vi];
+    const SvdQr q = qs[gv.x];
+    const int p = gv.y, c = q.c, r = q.r;
+    const double* xr = q.Xr + (int64_t)p * c;
+    double s = 0.0;
+    for (int i = lane; i < c; i += 32) s = fma(xr[i], xr[i], s);
+    s = warp_sum(s);
+    const double sg = sqrt(s), inv = sg > 0.0 ? 1.0 / sg : 0.0;
+    for (int i = lane; i < c; i += 32) q.J[(int64_t)p * c + q.perm[i]] = xr[i] * inv;
+    if (lane == 0) q.sigma[p] = sg;
+    const double* jr = q.Jr + (int64_t)p * c;
+    double* xf = q.Xf + (int64_t)p * r;
+    if (r <= 32 * VB) {
+      double z[VB];
+#pragma unroll
+      for (int m = 0; m < VB; ++m) {
+        const int e = lane + 32 * m;
+        z[m] = e < c ? jr[e] : 0.0;
+      }
+      for (int k = c - 1; k >= 0; --k) {
+        const double tk = q.tau[k];
+        if (tk == 0.0) continue;
+        const double* v = q.X + (int64_t)q.perm[k] * r;   // v_e for e > k; v_k = 1
+        double vv[VB];
+        double w = 0.0;
+#pragma unroll
+        for (int m = 0; m < VB; ++m) {
+          const int e = lane + 32 * m;
+          vv[m] = e == k ? 1.0 : (e > k && e < r ? v[e] : 0.0);
+          w = fma(vv[m], z[m], w);
+        }
+        w = warp_sum(w);
+        const double tw = tk * w;
+#pragma unroll
+        for (int m = 0; m < VB; ++m) z[m] = fma(-tw, vv[m], z[m]);
+      }
+#pragma unroll
+      for (int m = 0; m < VB; ++m) {
+        const int e = lane + 32 * m;
+        if (e < r) xf[e] = sg * z[m];
+      }
+    } else {
+      for (int e = lane; e < r; e += 32) xf[e] = e < c ? jr[e] : 0.0;
+      for (int k = c - 1; k >= 0; --k) {
+        const double tk = q.tau[k];
+        if (tk == 0.0) continue;
+        const double* v = q.X + (int64_t)q.perm[k] * r;
+        double w = 0.0;
+        for (int e = lane; e < r; e += 32)
+          if (e >= k) w = fma(e == k ? 1.0 : v[e], xf[e], w);
+        w = warp_sum(w);
+        const double tw = tk * w;
+        for (int e = lane; e < r; e += 32)
+          if (e >= k) xf[e] = fma(-tw, e == k ? 1.0 : v[e], xf[e]);
+      }
+      for (int e = lane; e < r; e += 32) xf[e] *= sg;
+    }
+  }
 }
 
 // J = identity for every group (one CTA per group row block)
@@ -358,7 +624,7 @@ cudaError_t tnx_launch_jacobi_round(const SvdGroup* groups, const int2* slots, i
 }
 
 cudaError_t tnx_launch_jacobi_coop(const SvdGroup* groups, const int2* slots, int nslots, int maxcp, int max_sweeps,
-                                   double tol, unsigned long long* offmax, unsigned int* bar, int* status,
+                                   double tol, unsigned long long* offmax, unsigned long long* bar, int* status,
                                    int* sweeps_out, cudaStream_t st) {
   if (nslots <= 0 || maxcp < 2) return cudaSuccess;
   int dev = 0, nsm = 0, per_sm = 0, coop = 0;
@@ -378,6 +644,46 @@ cudaError_t tnx_launch_jacobi_coop(const SvdGroup* groups, const int2* slots, in
   if (e != cudaSuccess) return e;
   tnx_note_launch(1);
   return cudaSuccess;
+}
+
+cudaError_t tnx_launch_qr_coop(const SvdQr* qs, const int2* slots, int nslots, int maxc, unsigned long long* bar,
+                               int* status, cudaStream_t st) {
+  if (nslots <= 0 || maxc < 1) return cudaSuccess;
+  int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_coop_kernel, CJT, 0);
+  if (e != cudaSuccess) return e;
+  if (!coop || per_sm < 1) return cudaErrorNotSupported;
+  int grid = nsm * (per_sm < 4 ? per_sm : 4);
+  if (grid > nslots) grid = nslots;   // one warp per slot of a step
+  void* args[] = {(void*)&qs, (void*)&slots, (void*)&nslots, (void*)&maxc, (void*)&bar, (void*)&status};
+  e = cudaLaunchCooperativeKernel((const void*)qr_coop_kernel, dim3(grid), dim3(CJT), args, 0, st);
+  if (e != cudaSuccess) return e;
+  tnx_note_launch(1);
+  return cudaSuccess;
+}
+
+cudaError_t tnx_launch_qr_gather_r(const SvdQr* qs, int nq, int maxc, cudaStream_t st) {
+  if (nq <= 0) return cudaSuccess;
+  int bx = (int)(((int64_t)maxc * maxc + 255) / 256);
+  if (bx > 64) bx = 64;
+  if (bx < 1) bx = 1;
+  const cudaError_t le = tnx_launch(qr_gather_r_kernel, dim3(bx, nq < 65535 ? nq : 65535), dim3(256), 0, st, qs, nq);
+  if (le != cudaSuccess) return le;
+  tnx_note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tnx_launch_qr_apply(const SvdQr* qs, const int2* vecs, int nvec, cudaStream_t st) {
+  if (nvec <= 0) return cudaSuccess;
+  // one warp per vector, two warps per CTA: the vectors spread over the SMs' FP64 pipes
+  const int grid = (nvec + 1) / 2;
+  const cudaError_t le = tnx_launch(qr_apply_kernel, dim3(grid), dim3(64), 0, st, qs, vecs, nvec);
+  if (le != cudaSuccess) return le;
+  tnx_note_launch(1);
+  return cudaGetLastError();
 }
 
 cudaError_t tnx_launch_vector_norms(const SvdGroup* groups, const int2* vecs, int nvec, cudaStream_t st) {

@@ -308,13 +308,40 @@ struct Copy2D {
   int64_t sld, dld;
   int32_t rows, cols, trans, pad0;
 };
+// The QR-preconditioned path of one block (k_svd.cu): A = X^T is r x c, its
+// columns the working vectors.  The pivoted Householder QR A P = Q R runs in
+// place in X; the one-sided Jacobi then works on the rows of R (Xr, with
+// rotations Jr); Xf receives sigma_p u_p (u_p = Q Jr[p,:]^T, the left singular
+// vectors of A) and J the right singular vectors of A as rows.
+struct SvdQr {
+  double* X;        // c x r
+  double* tau;      // [c] reflector scalar of pivot position k
+  int32_t* perm;    // [c] vector at pivot position k
+  double* nrm;      // [2][c] squared norms of the trailing parts, by position
+  int32_t* pos;     // [2][c] vector at each position
+  double* Xr;       // c x c
+  double* Jr;       // c x c
+  double* Xf;       // c x r
+  double* J;        // c x c
+  double* sigma;    // [c]
+  int32_t c, r;
+};
 cudaError_t tnx_launch_jacobi_init(const SvdGroup* groups, int ngroups, cudaStream_t st);
+// the pivoted QR of every block in one cooperative launch over slots (block,
+// position); *bar and *status zeroed by the caller; cudaErrorNotSupported
+// without cooperative launch
+cudaError_t tnx_launch_qr_coop(const SvdQr* qs, const int2* slots, int nslots, int maxc, unsigned long long* bar,
+                               int* status, cudaStream_t st);
+// Xr = R (rows, zero below the diagonal) and Jr = identity for every block
+cudaError_t tnx_launch_qr_gather_r(const SvdQr* qs, int nq, int maxc, cudaStream_t st);
+// after the Jacobi on Xr: sigma, J and Xf for every (block, vector)
+cudaError_t tnx_launch_qr_apply(const SvdQr* qs, const int2* vecs, int nvec, cudaStream_t st);
 // round r of a sweep over slots (group, pair index); maxoff gets the largest
 // |x_p . x_q| / (|x_p| |x_q|) met, as the bits of a non-negative double
-// every round and sweep in one cooperative launch; offmax[max_sweeps], bar[2]
+// every round and sweep in one cooperative launch; offmax[max_sweeps], *bar
 // and status zeroed by the caller; cudaErrorNotSupported without cooperative launch
 cudaError_t tnx_launch_jacobi_coop(const SvdGroup* groups, const int2* slots, int nslots, int maxcp, int max_sweeps,
-                                   double tol, unsigned long long* offmax, unsigned int* bar, int* status,
+                                   double tol, unsigned long long* offmax, unsigned long long* bar, int* status,
                                    int* sweeps_out, cudaStream_t st);
 cudaError_t tnx_launch_jacobi_round(const SvdGroup* groups, const int2* slots, int nslots, int round,
                                     unsigned long long* maxoff, cudaStream_t st);

@@ -169,18 +169,87 @@ void tnx_svd_run(tnx_tensor* t, int rowrank, int64_t keepdim, double err, const 
   const Copy2D* dgather = (const Copy2D*)up(gather.data(), gather.size() * sizeof(Copy2D));
   CUDA_CHECK(cudaMemsetAsync(dX, 0, (size_t)std::max<int64_t>(nX, 1) * 8, st));
   CUDA_CHECK(tnx_launch_copy2d(dgather, (int)gather.size(), st));
-  CUDA_CHECK(tnx_launch_jacobi_init(dg, ngr, st));
-  // ---- sweeps until the largest relative off-diagonal met in a sweep is small:
-  // one cooperative launch for everything; without it, one launch per round
   constexpr int MAX_SWEEPS = 60;
   const int rounds = maxcp - 1;
   int sweeps = 0;
-  bool done = rounds <= 0;
+  bool done = rounds <= 0, via_qr = false;
+  // ---- blocks of 16 or more vectors: QR-preconditioned Jacobi (k_svd.cu), the
+  // pivoted QR and the sweeps on R each in one cooperative launch
+  int maxc = 0;
+  int64_t nC = 0, nC2 = 0, nCR = 0;
+  for (Group* G : groups) {
+    maxc = std::max(maxc, G->c);
+    nC += (G->c + 31) / 32 * 32;
+    nC2 += ((int64_t)G->c * G->c + 31) / 32 * 32;
+    nCR += ((int64_t)G->c * G->r + 31) / 32 * 32;
+  }
+  std::unique_ptr<DevBuf> QD, QI, QXf;
+  if (!done && maxc >= 16) {
+    QD.reset(new DevBuf(ctx, (size_t)(3 * nC + 2 * nC2) * 8));   // tau, nrm[2], Xr, Jr
+    QI.reset(new DevBuf(ctx, (size_t)(3 * nC) * 4));             // perm, pos[2]
+    QXf.reset(new DevBuf(ctx, (size_t)std::max<int64_t>(nCR, 1) * 8));
+    std::vector<SvdQr> hq(ngr);
+    std::vector<SvdGroup> hr(ngr);
+    std::vector<int2> qslots;
+    int64_t oc = 0, oc2 = 0, ocr = 0;
+    for (int i = 0; i < ngr; ++i) {
+      Group* G = groups[i];
+      SvdQr& q = hq[i];
+      q.X = dX + G->offX;
+      q.tau = (double*)QD->p + oc;
+      q.nrm = (double*)QD->p + nC + 2 * oc;
+      q.Xr = (double*)QD->p + 3 * nC + oc2;
+      q.Jr = (double*)QD->p + 3 * nC + nC2 + oc2;
+      q.perm = (int32_t*)QI->p + oc;
+      q.pos = (int32_t*)QI->p + nC + 2 * oc;
+      q.Xf = (double*)QXf->p + ocr;
+      q.J = dJ + G->offJ;
+      q.sigma = dS + G->offS;
+      q.c = G->c;
+      q.r = G->r;
+      hr[i] = SvdGroup{q.Xr, q.Jr, q.sigma, G->c, G->c};
+      for (int j = 0; j < G->c; ++j) qslots.push_back(make_int2(i, j));
+      oc += (G->c + 31) / 32 * 32;
+      oc2 += ((int64_t)G->c * G->c + 31) / 32 * 32;
+      ocr += ((int64_t)G->c * G->r + 31) / 32 * 32;
+    }
+    const SvdQr* dq = (const SvdQr*)up(hq.data(), hq.size() * sizeof(SvdQr));
+    const SvdGroup* dr = (const SvdGroup*)up(hr.data(), hr.size() * sizeof(SvdGroup));
+    const int2* dqs = (const int2*)up(qslots.data(), qslots.size() * sizeof(int2));
+    // [QR barrier count | QR status, pad | offmax per sweep | Jacobi barrier count | Jacobi status, sweeps]
+    std::vector<uint64_t> zero(MAX_SWEEPS + 4, 0);
+    unsigned long long* w = (unsigned long long*)up(zero.data(), zero.size() * 8);
+    int* qstat = (int*)(w + 1);
+    int* jstat = (int*)(w + MAX_SWEEPS + 3);
+    const cudaError_t ce = tnx_launch_qr_coop(dq, dqs, (int)qslots.size(), maxc, w, qstat, st);
+    if (ce == cudaSuccess) {
+      CUDA_CHECK(tnx_launch_qr_gather_r(dq, ngr, maxc, st));
+      CUDA_CHECK(tnx_launch_jacobi_coop(dr, dslots, (int)slots.size(), maxcp, MAX_SWEEPS, 1e-13, w + 2,
+                                        w + MAX_SWEEPS + 2, jstat, jstat + 1, st));
+      CUDA_CHECK(tnx_launch_qr_apply(dq, dvecs, (int)vecs.size(), st));
+      int hs[4] = {0, 0, 0, 0};
+      CUDA_CHECK(cudaMemcpyAsync(hs, qstat, 4, cudaMemcpyDeviceToHost, st));
+      CUDA_CHECK(cudaMemcpyAsync(hs + 2, jstat, 8, cudaMemcpyDeviceToHost, st));
+      CUDA_CHECK(cudaStreamSynchronize(st));
+      if (hs[0] != 0 || hs[2] != 0) fail(TNX_ERR_TIMEOUT, "SVD: a grid barrier of the QR or the Jacobi sweeps timed out");
+      sweeps = hs[3];
+      for (int i = 0; i < ngr; ++i) hg[i].X = hq[i].Xf;   // the extraction reads sigma_p u_p from Xf
+      done = via_qr = true;
+    } else if (ce == cudaErrorNotSupported || ce == cudaErrorCooperativeLaunchTooLarge) {
+      (void)cudaGetLastError();   // the plain path below
+    } else {
+      CUDA_CHECK(ce);
+    }
+  }
+  if (!via_qr) CUDA_CHECK(tnx_launch_jacobi_init(dg, ngr, st));
+  // ---- plain path: sweeps until the largest relative off-diagonal met in a
+  // sweep is small: one cooperative launch for everything; without it, one
+  // launch per round
   if (!done) {
-    // [offmax per sweep (8 B each) | barrier count, generation | status | sweeps]
+    // [offmax per sweep (8 B each) | barrier arrival count (8 B) | status | sweeps]
     std::vector<uint64_t> zero(MAX_SWEEPS + 2, 0);
     unsigned long long* w = (unsigned long long*)up(zero.data(), zero.size() * 8);
-    unsigned int* bar = (unsigned int*)(w + MAX_SWEEPS);
+    unsigned long long* bar = w + MAX_SWEEPS;
     int* cstat = (int*)(w + MAX_SWEEPS + 1);
     const cudaError_t ce = tnx_launch_jacobi_coop(dg, dslots, (int)slots.size(), maxcp, MAX_SWEEPS, 1e-13, w, bar,
                                                   cstat, cstat + 1, st);
@@ -213,7 +282,7 @@ void tnx_svd_run(tnx_tensor* t, int rowrank, int64_t keepdim, double err, const 
     }
   }
   if (sweeps_out) *sweeps_out = sweeps;
-  CUDA_CHECK(tnx_launch_vector_norms(dg, dvecs, (int)vecs.size(), st));
+  if (!via_qr) CUDA_CHECK(tnx_launch_vector_norms(dg, dvecs, (int)vecs.size(), st));
   std::vector<double> sig((size_t)std::max<int64_t>(nS, 1));
   CUDA_CHECK(cudaMemcpyAsync(sig.data(), dS, (size_t)std::max<int64_t>(nS, 1) * 8, cudaMemcpyDeviceToHost, st));
   CUDA_CHECK(cudaStreamSynchronize(st));
