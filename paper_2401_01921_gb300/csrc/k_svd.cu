@@ -22,6 +22,9 @@
 //    with grid barriers between rounds, when the device allows it);
 //  * then sigma_p = |x_p|, and X = J M^T (or J M): the singular vectors are
 //    x_p / sigma_p on one side and the rows of J on the other.
+// Blocks of 16 or more vectors go through a column-pivoted Householder QR
+// first and the sweeps run on the rows of its triangular factor (see the QR
+// preconditioning section below); the output has the same form.
 // All arithmetic is FP64.  Block reductions use a fixed order (deterministic).
 #include "tnx_internal.h"
 
