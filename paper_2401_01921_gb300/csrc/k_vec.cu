@@ -47,6 +47,23 @@ __device__ __forceinline__ bool gated_off(const int32_t* state, int gate) {
   return gate && *(volatile const int32_t*)(state + 2) == 0;
 }
 
+// Reductions finish in the launch that produces their partial sums: every
+// block publishes its partials, fences and counts itself in state[4]; the
+// block that counts last (no block waits for another) reads all partials
+// through L2, in a fixed order, so the result does not depend on which block
+// that is, and resets the counter for the next launch.
+__device__ bool last_block(int32_t* counter) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(counter, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
 __global__ void scale_kernel(double* x, int64_t n, double a) {
   tnx_grid_dependency();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -96,6 +113,7 @@ __global__ void lanczos_init_kernel(LanczosDev L, const double* v0) {
     L.state[1] = 0;
     L.state[2] = 0;
     L.state[3] = 0;
+    L.state[4] = 0;   // the last-block counter
     L.beta[0] = 0.0;
     L.omega[0] = 1.0;   // <v_0, v_0>; the row before it is empty
   }
@@ -196,35 +214,68 @@ __device__ void block_multidot(const LanczosDev& L, int m, int64_t c0, int64_t c
   }
 }
 
-__global__ void __launch_bounds__(MD_T) multidot_kernel(LanczosDev L, int m, int vb, int gate) {
+// coef[i] = sum_b partial[b*m + i] over the nb blocks of the launch (fixed
+// order); the sum of row alpha_i (if >= 0) is also alpha_j = <v_j, H v_j>.
+// Run by one block of any width.
+__device__ void finalize_coefs(const LanczosDev& L, int m, int nb, int alpha_i, int alpha_j, double* sh) {
+  for (int i = 0; i < m; ++i) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += __ldcg(L.partial + (int64_t)b * m + i);
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+      L.coef[i] = acc;
+      if (i == alpha_i) L.alpha[alpha_j] = acc;
+    }
+  }
+}
+
+// Dots of w against V_vb .. V_{vb+m-1}, the coefficients formed by the last block.
+__global__ void __launch_bounds__(MD_T) multidot_kernel(LanczosDev L, int m, int vb, int gate, int alpha_i,
+                                                        int alpha_j) {
   tnx_grid_dependency();
   __shared__ double sh[16][MD_T + 1];
+  __shared__ double shr[32];
   if (stopped(L.state) || gated_off(L.state, gate)) return;
   const int64_t chunk = (L.n + gridDim.x - 1) / gridDim.x;
   const int64_t c0 = chunk * blockIdx.x, c1 = min(L.n, c0 + chunk);
   block_multidot(L, m, c0, c1, sh, vb);
+  if (last_block(L.state + 4)) {
+    finalize_coefs(L, m, gridDim.x, alpha_i, alpha_j, shr);
+    if (threadIdx.x == 0) L.state[4] = 0;
+  }
 }
 
-// coef[i] = sum_b partial[b*m + i]   (one block per i, fixed order);
-// the sum of row alpha_i (if >= 0) is also alpha_j = <v_j, H v_j>.
-__global__ void __launch_bounds__(RT) multidot_finalize_kernel(LanczosDev L, int m, int nb, int alpha_i,
-                                                               int alpha_j, int gate) {
-  tnx_grid_dependency();
+// beta_{j+1} = sqrt(sum of the nb norm partials); decide stop; record k; point
+// the next apply's input slot at v_{j+1} (which the next kernel writes).  Run
+// by one block of RT threads.
+__device__ void beta_decide(const LanczosDev& L, int j, int nb, int last, double** next_slot) {
   __shared__ double sh[32];
-  if (stopped(L.state) || gated_off(L.state, gate)) return;
-  const int i = blockIdx.x;
+  __shared__ double s_amax;
   double acc = 0.0;
-  for (int b = threadIdx.x; b < nb; b += RT) acc += L.partial[(int64_t)b * m + i];
+  for (int b = threadIdx.x; b < nb; b += RT) acc += __ldcg(L.partial + b);
+  if (threadIdx.x < 32) {
+    double amax = 0.0;
+    // the scale of T seen so far: max |alpha_i| and max beta_i (i <= j; beta_0 = 0)
+    for (int i = threadIdx.x; i <= j; i += 32) amax = fmax(amax, fmax(fabs(L.alpha[i]), L.beta[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (threadIdx.x == 0) s_amax = amax;
+  }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) {
-    L.coef[i] = acc;
-    if (i == alpha_i) L.alpha[alpha_j] = acc;
+    const double beta = sqrt(acc);
+    L.beta[j + 1] = beta;
+    L.scratch[3 * L.nmax + 3] = 1.0 / beta;   // for the normalising kernel
+    L.state[0] = j + 1;
+    if (last || beta < 1e-14 * s_amax) L.state[1] = 1;
+    else *next_slot = L.V + (int64_t)(j + 1) * L.n;
   }
 }
 
 // w -= sum_i coef[i] V_i; with norm != 0 also partial[b] = sum of the new w^2
 // over this block's grid-stride share (fixed order).
-__global__ void __launch_bounds__(RT) gs_update_kernel(LanczosDev L, int m, int norm, int gate) {
+__global__ void __launch_bounds__(RT) gs_update_kernel(LanczosDev L, int m, int norm, int gate, int j, int last,
+                                                        double** next_slot) {
   tnx_grid_dependency();
   __shared__ double c[512];
   __shared__ double sh[32];
@@ -260,67 +311,12 @@ __global__ void __launch_bounds__(RT) gs_update_kernel(LanczosDev L, int m, int 
   if (norm) {
     nrm = block_sum(nrm, sh);
     if (threadIdx.x == 0) L.partial[blockIdx.x] = nrm;
+    // the last block: beta_{j+1} and the stopping test of this step
+    if (last_block(L.state + 4)) {
+      beta_decide(L, j, gridDim.x, last, next_slot);
+      if (threadIdx.x == 0) L.state[4] = 0;
+    }
   }
-}
-
-// beta_{j+1} = sqrt(sum of the norm partials); decide stop; record k; point
-// the next apply's input slot at v_{j+1} (which the next kernel writes)
-__global__ void __launch_bounds__(RT) lanczos_beta_decide_kernel(LanczosDev L, int j, int nb, int last,
-                                                                 double** next_slot, int gate) {
-  tnx_grid_dependency();
-  __shared__ double sh[32];
-  __shared__ double s_amax;
-  if (stopped(L.state) || gated_off(L.state, gate)) return;
-  double acc = 0.0;
-  for (int b = threadIdx.x; b < nb; b += RT) acc += L.partial[b];
-  if (threadIdx.x < 32) {
-    double amax = 0.0;
-    // the scale of T seen so far: max |alpha_i| and max beta_i (i <= j; beta_0 = 0)
-    for (int i = threadIdx.x; i <= j; i += 32) amax = fmax(amax, fmax(fabs(L.alpha[i]), L.beta[i]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if (threadIdx.x == 0) s_amax = amax;
-  }
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) {
-    const double beta = sqrt(acc);
-    L.beta[j + 1] = beta;
-    L.scratch[3 * L.nmax + 3] = 1.0 / beta;   // for the normalising kernel
-    L.state[0] = j + 1;
-    if (last || beta < 1e-14 * s_amax) L.state[1] = 1;
-    else *next_slot = L.V + (int64_t)(j + 1) * L.n;
-  }
-}
-
-// The three-term step w <- (w - alpha_j v_j) - beta_j v_{j-1} (beta_0 = 0), with
-// partial[b] = this block's share of the new |w|^2 (fixed order).
-__global__ void __launch_bounds__(RT) three_term_norm_kernel(LanczosDev L, int j) {
-  tnx_grid_dependency();
-  __shared__ double sh[32];
-  if (stopped(L.state)) return;
-  const double a = L.alpha[j], b = j > 0 ? L.beta[j] : 0.0;
-  const double* vj = L.V + (int64_t)j * L.n;
-  const double* vp = L.V + (int64_t)(j > 0 ? j - 1 : 0) * L.n;
-  double nrm = 0.0;
-  const int64_t stride = (int64_t)gridDim.x * RT;
-  int64_t x = (int64_t)blockIdx.x * RT + threadIdx.x;
-  for (; x + stride < L.n; x += 2 * stride) {
-    const double w0 = L.w[x], w1 = L.w[x + stride];
-    const double a0 = vj[x], a1 = vj[x + stride];
-    const double p0 = vp[x], p1 = vp[x + stride];
-    const double u0 = (w0 - a * a0) - b * p0, u1 = (w1 - a * a1) - b * p1;
-    L.w[x] = u0;
-    L.w[x + stride] = u1;
-    nrm = fma(u0, u0, nrm);
-    nrm = fma(u1, u1, nrm);
-  }
-  if (x < L.n) {
-    const double u = (L.w[x] - a * vj[x]) - b * vp[x];
-    L.w[x] = u;
-    nrm = fma(u, u, nrm);
-  }
-  nrm = block_sum(nrm, sh);
-  if (threadIdx.x == 0) L.partial[blockIdx.x] = nrm;
 }
 
 // Partial reorthogonalisation (Simon, Math. Comp. 42, 1984): omega_{j,k}
@@ -334,20 +330,18 @@ __global__ void __launch_bounds__(RT) three_term_norm_kernel(LanczosDev L, int j
 // Gram-Schmidt pass against v_0..v_j when the largest estimate exceeds
 // tau (1e-10; a negative tau: every step), and so does the step after it (the error that v_j carries reaches
 // v_{j+2} too); after a pass the estimates restart at eps1.  Without a pass
-// this kernel also does what the beta kernel does (beta_{j+1}, the stopping
+// it also does what beta_decide does (beta_{j+1}, the stopping
 // test, the next input slot); with one, the gated launches after it do.
 constexpr int PRO_MAX = 514;   // rows of at most 500 steps + 2
 
-__global__ void __launch_bounds__(RT) pro_decide_kernel(LanczosDev L, int j, int nb, int last, double** next_slot,
-                                                        double tau) {
-  tnx_grid_dependency();
+// Run by one block of RT threads over the nb norm partials.
+__device__ void pro_decide(const LanczosDev& L, int j, int nb, int last, double** next_slot, double tau) {
   __shared__ double sh[32];
   __shared__ double s_om[PRO_MAX];
   __shared__ double s_b, s_amax, s_anorm, s_mx[RT / 32];
   __shared__ int s_pass;
-  if (stopped(L.state)) return;
   double acc = 0.0;
-  for (int b = threadIdx.x; b < nb; b += RT) acc += L.partial[b];
+  for (int b = threadIdx.x; b < nb; b += RT) acc += __ldcg(L.partial + b);
   if (threadIdx.x < 32) {
     double amax = 0.0, an = 0.0;
     for (int i = threadIdx.x; i <= j; i += 32) {
@@ -415,6 +409,42 @@ __global__ void __launch_bounds__(RT) pro_decide_kernel(LanczosDev L, int j, int
     cur[k] = s_pass ? eps1 : s_om[k];
   }
   if (threadIdx.x == 0) cur[j + 1] = 1.0;
+}
+
+// The three-term step w <- (w - alpha_j v_j) - beta_j v_{j-1} (beta_0 = 0), with
+// partial[b] = this block's share of the new |w|^2 (fixed order).
+__global__ void __launch_bounds__(RT) three_term_norm_kernel(LanczosDev L, int j, int last, double** next_slot,
+                                                              double tau) {
+  tnx_grid_dependency();
+  __shared__ double sh[32];
+  if (stopped(L.state)) return;
+  const double a = L.alpha[j], b = j > 0 ? L.beta[j] : 0.0;
+  const double* vj = L.V + (int64_t)j * L.n;
+  const double* vp = L.V + (int64_t)(j > 0 ? j - 1 : 0) * L.n;
+  double nrm = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * RT;
+  int64_t x = (int64_t)blockIdx.x * RT + threadIdx.x;
+  for (; x + stride < L.n; x += 2 * stride) {
+    const double w0 = L.w[x], w1 = L.w[x + stride];
+    const double a0 = vj[x], a1 = vj[x + stride];
+    const double p0 = vp[x], p1 = vp[x + stride];
+    const double u0 = (w0 - a * a0) - b * p0, u1 = (w1 - a * a1) - b * p1;
+    L.w[x] = u0;
+    L.w[x + stride] = u1;
+    nrm = fma(u0, u0, nrm);
+    nrm = fma(u1, u1, nrm);
+  }
+  if (x < L.n) {
+    const double u = (L.w[x] - a * vj[x]) - b * vp[x];
+    L.w[x] = u;
+    nrm = fma(u, u, nrm);
+  }
+  nrm = block_sum(nrm, sh);
+  if (threadIdx.x == 0) L.partial[blockIdx.x] = nrm;
+  if (last_block(L.state + 4)) {
+    pro_decide(L, j, gridDim.x, last, next_slot, tau);
+    if (threadIdx.x == 0) L.state[4] = 0;
+  }
 }
 
 __global__ void lanczos_normalize_kernel(LanczosDev L, int j) {
@@ -632,39 +662,22 @@ cudaError_t tnx_launch_lanczos_step(const LanczosDev& L, int j, double** next_sl
   const int mb = multidot_blocks(L.n);
   const int last = j == L.nmax - 1;
   {
-    const cudaError_t le = tnx_launch(multidot_kernel, dim3(mb), dim3(MD_T), 0, st, L, 1, j, 0);
+    const cudaError_t le = tnx_launch(multidot_kernel, dim3(mb), dim3(MD_T), 0, st, L, 1, j, 0, 0, j);
     if (le != cudaSuccess) return le;
   }
   {
-    const cudaError_t le = tnx_launch(multidot_finalize_kernel, dim3(1), dim3(RT), 0, st, L, 1, mb, 0, j, 0);
+    const cudaError_t le = tnx_launch(three_term_norm_kernel, dim3(nb), dim3(RT), 0, st, L, j, last, next_slot, tau);
     if (le != cudaSuccess) return le;
   }
   {
-    const cudaError_t le = tnx_launch(three_term_norm_kernel, dim3(nb), dim3(RT), 0, st, L, j);
+    const cudaError_t le = tnx_launch(multidot_kernel, dim3(mb), dim3(MD_T), 0, st, L, m, 0, 1, -1, 0);
     if (le != cudaSuccess) return le;
   }
   {
-    const cudaError_t le = tnx_launch(pro_decide_kernel, dim3(1), dim3(RT), 0, st, L, j, nb, last, next_slot, tau);
+    const cudaError_t le = tnx_launch(gs_update_kernel, dim3(nb), dim3(RT), 0, st, L, m, 1, 1, j, last, next_slot);
     if (le != cudaSuccess) return le;
   }
-  {
-    const cudaError_t le = tnx_launch(multidot_kernel, dim3(mb), dim3(MD_T), 0, st, L, m, 0, 1);
-    if (le != cudaSuccess) return le;
-  }
-  {
-    const cudaError_t le = tnx_launch(multidot_finalize_kernel, dim3(m), dim3(RT), 0, st, L, m, mb, -1, 0, 1);
-    if (le != cudaSuccess) return le;
-  }
-  {
-    const cudaError_t le = tnx_launch(gs_update_kernel, dim3(nb), dim3(RT), 0, st, L, m, 1, 1);
-    if (le != cudaSuccess) return le;
-  }
-  {
-    const cudaError_t le = tnx_launch(lanczos_beta_decide_kernel, dim3(1), dim3(RT), 0, st,
-                                      L, j, nb, last, next_slot, 1);
-    if (le != cudaSuccess) return le;
-  }
-  tnx_note_launch(8);
+  tnx_note_launch(4);
   if (normalize) {
     {
       const cudaError_t le = tnx_launch(lanczos_normalize_kernel, dim3(nb), dim3(RT), 0, st, L, j);

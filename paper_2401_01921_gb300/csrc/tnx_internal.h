@@ -366,7 +366,7 @@ struct LanczosDev {
   double* y;          // [nmax]    Ritz coefficients
   double* scratch;    // [4*nmax]
   int32_t* state;     // [0] = active steps done (k), [1] = stopped flag, [2] = this step reorthogonalises,
-                      // [3] = the next step must reorthogonalise too
+                      // [3] = the next step must reorthogonalise too, [4] = blocks done (last-block reductions)
   double* omega;      // [2][nmax+2] estimates of <v_j, v_k> (row j, then row j-1)
   double* eval;       // [1]
   int64_t n;
