@@ -230,11 +230,19 @@ __device__ __forceinline__ int kx_shift(int raw, int sign) {
   return raw > 0 ? sign * (raw - 1023) : 0;   // raw: biased exponent, 0 for a zero column
 }
 
-template <bool F16, bool KX>
+// With VEC (vector mode, no K balancing) a row's entries come from the
+// Lanczos vector through the row table, scaled by *inv, and the scaled values
+// are written out as the next basis vector (VecSrc).
+template <bool F16, bool KX, bool VEC>
 __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restrict__ jobs,
                                                          const int2* __restrict__ items, int64_t total,
-                                                         double* const* __restrict__ slots) {
+                                                         double* const* __restrict__ slots, VecSrc vs) {
+  static_assert(!(KX && VEC), "vector mode slices without K balancing");
   tnx_grid_dependency();
+  if constexpr (VEC) {
+    if (*(volatile const int32_t*)(vs.state + 1) != 0) return;   // the solve has stopped
+  }
+  const double vinv = VEC ? *vs.inv : 1.0;
   __shared__ int s_max[8][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int r8 = lane >> 2, kq = lane & 3;
@@ -249,7 +257,14 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restr
     const int KT = (j.K + TK - 1) / TK;
     const int64_t row = rg * 8 + r8;
     const bool live = rg < ngroups && row < j.rows;
-    const double* src = slots[j.src_slot] + j.src_off + row * j.ld;
+    int64_t voff = 0;   // vector mode: offset of the row's K entries in the vector
+    const double* src;
+    if constexpr (VEC) {
+      voff = live ? vs.rowtab[j.src_off + row] : 0;
+      src = vs.w + voff;
+    } else {
+      src = slots[j.src_slot] + j.src_off + row * j.ld;
+    }
     // row exponent: the largest (effective) exponent field; eight independent
     // loads of the high words in flight per lane
     const uint32_t* src_hi = (const uint32_t*)src + 1;
@@ -264,7 +279,10 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restr
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int k = k0 + u * kstep;
-          h[u] = k < j.K ? src_hi[2 * k] : 0u;
+          if constexpr (VEC)
+            h[u] = k < j.K ? (uint32_t)((unsigned long long)__double_as_longlong(src[k] * vinv) >> 32) : 0u;
+          else
+            h[u] = k < j.K ? src_hi[2 * k] : 0u;
           if constexpr (KX) sx[u] = k < j.K ? kxp[k] : 0;
         }
 #pragma unroll
@@ -305,7 +323,16 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restr
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int k = kt0 * TK + kq * 8 + e;
-      cur[e] = (live && kt0 < KT && k < j.K) ? (unsigned long long)__double_as_longlong(src[k]) : 0ull;
+      if constexpr (VEC) {
+        cur[e] = 0ull;
+        if (live && kt0 < KT && k < j.K) {
+          const double x = src[k] * vinv;
+          vs.vdst[voff + k] = x;
+          cur[e] = (unsigned long long)__double_as_longlong(x);
+        }
+      } else {
+        cur[e] = (live && kt0 < KT && k < j.K) ? (unsigned long long)__double_as_longlong(src[k]) : 0ull;
+      }
     }
     if constexpr (KX) {
       const bool ok = live && kt0 < KT;
@@ -318,7 +345,16 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const SliceJob* __restr
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int k = (kt + kts) * TK + kq * 8 + e;
-        nxt[e] = (live && kt + kts < KT && k < j.K) ? (unsigned long long)__double_as_longlong(src[k]) : 0ull;
+        if constexpr (VEC) {
+          nxt[e] = 0ull;
+          if (live && kt + kts < KT && k < j.K) {
+            const double x = src[k] * vinv;
+            vs.vdst[voff + k] = x;
+            nxt[e] = (unsigned long long)__double_as_longlong(x);
+          }
+        } else {
+          nxt[e] = (live && kt + kts < KT && k < j.K) ? (unsigned long long)__double_as_longlong(src[k]) : 0ull;
+        }
       }
       if constexpr (KX) {
         const bool ok = live && kt + kts < KT;
@@ -790,11 +826,34 @@ cudaError_t tnx_launch_slices(const SliceJob* jobs, const int2* items, int64_t t
   if (blocks > 152 * 8) blocks = 152 * 8;
   {
     const dim3 g((int)blocks), b(256);
+    const VecSrc none{nullptr, nullptr, nullptr, nullptr, nullptr};
     const cudaError_t le =
-        f16 ? (use_kx ? tnx_launch(slice_rows_kernel<true, true>, g, b, 0, st, jobs, items, total_items, slots)
-                      : tnx_launch(slice_rows_kernel<true, false>, g, b, 0, st, jobs, items, total_items, slots))
-            : (use_kx ? tnx_launch(slice_rows_kernel<false, true>, g, b, 0, st, jobs, items, total_items, slots)
-                      : tnx_launch(slice_rows_kernel<false, false>, g, b, 0, st, jobs, items, total_items, slots));
+        f16 ? (use_kx ? tnx_launch(slice_rows_kernel<true, true, false>, g, b, 0, st, jobs, items, total_items, slots,
+                                   none)
+                      : tnx_launch(slice_rows_kernel<true, false, false>, g, b, 0, st, jobs, items, total_items,
+                                   slots, none))
+            : (use_kx ? tnx_launch(slice_rows_kernel<false, true, false>, g, b, 0, st, jobs, items, total_items,
+                                   slots, none)
+                      : tnx_launch(slice_rows_kernel<false, false, false>, g, b, 0, st, jobs, items, total_items,
+                                   slots, none));
+    if (le != cudaSuccess) return le;
+  }
+  tnx_note_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tnx_launch_slices_vec(const SliceJob* jobs, const int2* items, int64_t total_items, int nslice, int beta,
+                                  int f16, double* const* slots, const VecSrc& vs, cudaStream_t st) {
+  if (total_items <= 0) return cudaSuccess;
+  if (nslice != MAXN || beta != 7) return cudaErrorInvalidValue;   // the digit code is specialised
+  if (!vs.rowtab || !vs.w || !vs.vdst || !vs.inv || !vs.state) return cudaErrorInvalidValue;
+  int64_t blocks = total_items;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  {
+    const dim3 g((int)blocks), b(256);
+    const cudaError_t le =
+        f16 ? tnx_launch(slice_rows_kernel<true, false, true>, g, b, 0, st, jobs, items, total_items, slots, vs)
+            : tnx_launch(slice_rows_kernel<false, false, true>, g, b, 0, st, jobs, items, total_items, slots, vs);
     if (le != cudaSuccess) return le;
   }
   tnx_note_launch(1);

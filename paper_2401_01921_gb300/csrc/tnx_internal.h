@@ -260,6 +260,21 @@ cudaError_t tnx_launch_gemm_f32(const GemmGroup* groups, const GemmTile* tiles, 
                                 double* const* slots, cudaStream_t st);
 // row exponents, then the slices; items: (job, first 8-row group) per CTA work
 // item, which covers 8 / wpg groups of that job
+// Slicing straight from a Lanczos vector (the "vector mode" of the slicing
+// kernel): row `row` of job j reads w + rowtab[j.src_off + row] (its K entries
+// contiguous there), every entry is taken as w * (*inv), and that product is
+// also written to vdst at the same offset (v_{j+1} = w / beta_{j+1}, the same
+// FP64 product the normalising kernels form); nothing runs once state[1] (the
+// Lanczos stop flag) is set.
+struct VecSrc {
+  const int64_t* rowtab;
+  const double* w;
+  double* vdst;
+  const double* inv;
+  const int32_t* state;
+};
+cudaError_t tnx_launch_slices_vec(const SliceJob* jobs, const int2* items, int64_t total_items, int nslice, int beta,
+                                  int f16, double* const* slots, const VecSrc& vs, cudaStream_t st);
 cudaError_t tnx_launch_slices(const SliceJob* jobs, const int2* items, int64_t total_items, int nslice, int beta,
                               int f16, double* const* slots, cudaStream_t st, int use_kx = 0);
 // zero the K-balancing words of every job, then their column maxima

@@ -1616,9 +1616,13 @@ void enqueue_split(Plan& p, StepPlan& s, cudaStream_t st, bool needA, bool needB
 // operand unless A varies while B stays fixed (B's slices would then need A's
 // exponents of every apply); the choice is the same for every apply of the
 // sequence, so slices kept from a previous apply stay consistent.
-void enqueue_plan(Plan& p, cudaStream_t st, uint64_t fixed = 0, int skip_slot = -1, uint64_t vary = ~(uint64_t)0) {
+// skip_slice_step / skip_slice_A: the slices of that step's A (or B) operand
+// were written by the caller already (the Lanczos vector mode of the slicing).
+void enqueue_plan(Plan& p, cudaStream_t st, uint64_t fixed = 0, int skip_slot = -1, uint64_t vary = ~(uint64_t)0,
+                  int skip_slice_step = -1, bool skip_slice_A = true) {
   tnx_ctx* c = p.ctx;
-  for (auto& s : p.steps) {
+  for (size_t si = 0; si < p.steps.size(); ++si) {
+    StepPlan& s = p.steps[si];
     const bool needA = (s.leavesA & ~fixed) != 0;
     const bool needB = (s.leavesB & ~fixed) != 0;
     if (!needA && !needB) continue;
@@ -1651,7 +1655,8 @@ void enqueue_plan(Plan& p, cudaStream_t st, uint64_t fixed = 0, int skip_slot = 
       }
       default: {
         const bool balance = !((s.leavesA & vary) != 0 && (s.leavesB & vary) == 0);
-        enqueue_split(p, s, st, needA, needB, balance);
+        const bool pre = (int)si == skip_slice_step;
+        enqueue_split(p, s, st, needA && !(pre && skip_slice_A), needB && !(pre && !skip_slice_A), balance);
         break;
       }
     }
@@ -1951,6 +1956,13 @@ struct LanczosCache {
   std::vector<std::unique_ptr<DevBuf>> bufs;
   LanczosDev L;
   std::unique_ptr<GraphRec> graph;
+  // vector mode of the slicing (see vector_slicing): decided once per cache
+  bool vs_decided = false;
+  int vs_step = -1;                // the step whose operand is sliced straight from w (-1: not used)
+  bool vs_sideA = true;
+  std::unique_ptr<DevBuf> vs_rowtab, vs_jobs;
+  const int2* vs_items = nullptr;
+  int64_t vs_nitems = 0;
 };
 
 tnx_network::~tnx_network() = default;
@@ -1969,6 +1981,84 @@ size_t tnx_lanczos_workspace_bytes(int64_t n, int nsteps) {
   size_t b = 0;
   for (size_t x : lanczos_buffer_sizes(n, nsteps)) b += std::max<size_t>(x, 256);
   return b;
+}
+
+// The Lanczos vector mode of the slicing: when the only reader of the vector is
+// a plain relayout into a split product's operand that is sliced without K
+// balancing, and every packed row of that operand takes its K entries from one
+// contiguous run of the vector, the next apply's slices of the operand are
+// written straight from w at the end of a step, together with v_{j+1} = w /
+// beta_{j+1}: the FP64 packed operand is never formed.  rowtab[base(job) + row]
+// = offset in the vector of that packed row's K entries; jobs are the step's
+// slicing jobs with src_off = base(job).  Every element of every task is
+// mapped (the tasks may have merged or dropped legs in any order); false, with
+// nothing built, when a row's entries are not one run in order or a row is not
+// filled exactly once.
+bool vector_slicing_tables(const TaskList& vc, const std::vector<SliceJob>& jobs, std::vector<int64_t>& rowtab,
+                           std::vector<SliceJob>& vjobs) {
+  if (jobs.empty() || vc.h.empty()) return false;
+  std::vector<int64_t> base(jobs.size() + 1, 0);
+  for (size_t b = 0; b < jobs.size(); ++b) {
+    if (jobs[b].rows < 0 || jobs[b].ld < jobs[b].K || jobs[b].K < 1) return false;
+    base[b + 1] = base[b] + jobs[b].rows;
+  }
+  rowtab.assign((size_t)base.back(), -1);
+  std::vector<int32_t> cnt((size_t)base.back(), 0);
+  // jobs by their start in the operand slot
+  std::vector<int> ord(jobs.size());
+  std::iota(ord.begin(), ord.end(), 0);
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return jobs[a].src_off < jobs[b].src_off; });
+  auto find_job = [&](int64_t P) {
+    int lo = 0, hi = (int)ord.size() - 1, f = -1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) / 2;
+      if (jobs[ord[mid]].src_off <= P) {
+        f = ord[mid];
+        lo = mid + 1;
+      } else {
+        hi = mid - 1;
+      }
+    }
+    return f;
+  };
+  int f = -1;   // the job of the previous element (consecutive elements mostly share it)
+  for (const CopyTask& t : vc.h) {
+    const int r = t.rank;
+    if (t.tleg != -1 || r < 1 || r > TNX_MAXR) return false;
+    int64_t idx[TNX_MAXR] = {0};
+    int64_t so = 0, dof = 0;
+    for (int64_t e = 0; e < t.nelem; ++e) {
+      const int64_t P = t.dst_off + dof;
+      if (f < 0 || P < jobs[f].src_off || P >= jobs[f].src_off + (int64_t)jobs[f].rows * jobs[f].ld) f = find_job(P);
+      if (f < 0) return false;
+      const SliceJob& jb = jobs[f];
+      if (jb.src_slot != t.dst_slot) return false;
+      const int64_t off = P - jb.src_off, row = off / jb.ld, k = off % jb.ld;
+      if (row >= jb.rows || k >= jb.K) return false;
+      const size_t ri = (size_t)(base[f] + row);
+      const int64_t start = t.src_off + so - k;   // where entry 0 of this row must lie
+      if (rowtab[ri] == -1) rowtab[ri] = start;
+      else if (rowtab[ri] != start) return false;
+      ++cnt[ri];
+      // next element: the last leg fastest
+      for (int l = r - 1; l >= 0; --l) {
+        so += t.sstride[l];
+        dof += t.dstride[l];
+        if (++idx[l] < t.shape[l]) break;
+        so -= (int64_t)t.shape[l] * t.sstride[l];
+        dof -= (int64_t)t.shape[l] * t.dstride[l];
+        idx[l] = 0;
+      }
+    }
+  }
+  for (size_t b = 0; b < jobs.size(); ++b)
+    for (int64_t row = 0; row < jobs[b].rows; ++row) {
+      const size_t ri = (size_t)(base[b] + row);
+      if (rowtab[ri] < 0 || cnt[ri] != jobs[b].K) return false;   // a row not filled exactly once
+    }
+  vjobs = jobs;
+  for (size_t b = 0; b < jobs.size(); ++b) vjobs[b].src_off = base[b];
+  return true;
 }
 
 // A whole Lanczos solve enqueued on `st`; at its end the eigenvalue and the
@@ -2062,6 +2152,40 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
     }
     vfull = cover == n && starts.size() == vcopy->h.size() && vcopy->h.size() == (size_t)v0->nblk ? 1 : 0;
   }
+  // vector mode of the slicing (split precisions only, and only for an operand
+  // the Lanczos applies slice without K balancing)
+  if (!lc->vs_decided) {
+    lc->vs_decided = true;
+    const bool split = p->prec == TNX_PREC_SPLIT_BF16 || p->prec == TNX_PREC_SPLIT_F16;
+    if (split && vcopy && vfull) {
+      for (size_t si = 0; si < p->steps.size(); ++si) {
+        StepPlan& s = p->steps[si];
+        const bool sideA = vcopy == &s.copyA, sideB = vcopy == &s.copyB;
+        if (!sideA && !sideB) continue;
+        const uint64_t vary = ~fixed;
+        const bool balance = !((s.leavesA & vary) != 0 && (s.leavesB & vary) == 0);
+        const bool other = sideA ? (s.leavesB & ~fixed) != 0 : (s.leavesA & ~fixed) != 0;
+        const StepPlan::Jobs& J = sideA ? s.jobsA : s.jobsB;
+        std::vector<int64_t> rowtab;
+        std::vector<SliceJob> vjobs;
+        if (!balance && !other && !s.nftiles && J.n > 0 && J.nitems > 0 &&
+            vector_slicing_tables(*vcopy, J.h, rowtab, vjobs)) {
+          lc->vs_rowtab.reset(new DevBuf(ctx, std::max<size_t>(rowtab.size() * 8, 256)));
+          lc->vs_jobs.reset(new DevBuf(ctx, std::max<size_t>(vjobs.size() * sizeof(SliceJob), 256)));
+          CUDA_CHECK(cudaMemcpyAsync(lc->vs_rowtab->p, rowtab.data(), rowtab.size() * 8, cudaMemcpyHostToDevice, st));
+          CUDA_CHECK(cudaMemcpyAsync(lc->vs_jobs->p, vjobs.data(), vjobs.size() * sizeof(SliceJob),
+                                     cudaMemcpyHostToDevice, st));
+          CUDA_CHECK(cudaStreamSynchronize(st));   // the host tables are freed on return
+          lc->vs_step = (int)si;
+          lc->vs_sideA = sideA;
+          lc->vs_items = J.items;
+          lc->vs_nitems = J.nitems;
+        }
+        break;
+      }
+    }
+  }
+  const bool vslice = lc->vs_step >= 0;
   auto body = [&] {
     {
       ProfScope ps(ctx, st, TNX_KC_VECTOR, 24.0 * (double)n);
@@ -2075,7 +2199,8 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
         const uint32_t prof = ctx->prof;
         if ((prof & TNX_PROF_LAST_APPLY) && j != nsteps - 1) ctx->prof = 0;
         try {
-          enqueue_plan(*p, st, j == 0 ? 0 : fixed, (j > 0 && vcopy) ? slot : -1, ~fixed);
+          enqueue_plan(*p, st, j == 0 ? 0 : fixed, (j > 0 && vcopy) ? slot : -1, ~fixed,
+                       (j > 0 && vslice) ? lc->vs_step : -1, lc->vs_sideA);
         } catch (...) {
           ctx->prof = prof;
           throw;
@@ -2089,10 +2214,17 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
       ProfScope ps(ctx, st, TNX_KC_VECTOR, 8.0 * (double)n * 8);
       CUDA_CHECK(tnx_launch_lanczos_step(L, j, p->d_slots + slot, st, vcopy == nullptr,
                                          p->prec == TNX_PREC_F32 || p->prec == TNX_PREC_TF32));
-      if (vcopy)
+      if (vslice) {
+        // v_{j+1} and the next apply's slices of the vector operand in one pass over w
+        const VecSrc vs{(const int64_t*)lc->vs_rowtab->p, L.w, L.V + (int64_t)(j + 1) * n,
+                        L.scratch + 3 * L.nmax + 3, L.state};
+        CUDA_CHECK(tnx_launch_slices_vec((const SliceJob*)lc->vs_jobs->p, lc->vs_items, lc->vs_nitems, p->nslice,
+                                         p->beta, p->prec == TNX_PREC_SPLIT_F16 ? 1 : 0, p->d_slots, vs, st));
+      } else if (vcopy) {
         CUDA_CHECK(tnx_launch_copy_scaled(vcopy->d, vcopy->chunks, vcopy->nchunks, p->d_slots, L.w,
                                           L.V + (int64_t)(j + 1) * n, n, vfull, L.scratch + 3 * L.nmax + 3, L.state,
                                           st));
+      }
     }
     ProfScope ps(ctx, st, TNX_KC_VECTOR, evp ? 8.0 * (double)n * (nsteps + 2) : 0.0);
     CUDA_CHECK(tnx_launch_lanczos_finish(L, evp, st));
