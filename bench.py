@@ -56,8 +56,8 @@ SPLIT_TRAFFIC = {
         (9305600, "profiles/split_gemm_heisenberg_u1_chi512.md",
          "1edccaadeb9ebab7b4ab4b062a986006f94f024ad0ed51f81a11861a747bc22f"),
     "heisenberg_u1_chi2048_d2_D5_sectorscaled_lanczos20":
-        (90454144, "profiles/split_gemm_heisenberg_u1_chi2048.md",
-         "e1550ed725a44f91c70454252de5a020931028b96de062f913da4d6922d99265"),
+        (90162944, "profiles/split_gemm_heisenberg_u1_chi2048.md",
+         "3881178b94e7b3c07d3657f48af6a1640532fa838379ab8ed0827a232525ae31"),
 }
 
 
