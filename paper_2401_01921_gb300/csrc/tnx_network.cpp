@@ -1724,7 +1724,13 @@ void tnx_apply_enqueue(tnx_network* net, tnx_tensor* out, cudaStream_t st) {
   p->h_slots[p->out_slot] = out->data;
   sync_slots(*p, st);
   tnx_ctx* c = net->ctx;
-  if (st != nullptr && c->use_graphs) {
+  // The first apply of a plan runs eagerly; the graph is captured from the
+  // second on (a plan applied once, as in a DMRG sweep where every bond brings
+  // new bond dimensions, would pay capture and instantiation for one replay).
+  if (st != nullptr && c->use_graphs && !p->apply_graph && p->eager_applies == 0) {
+    ++p->eager_applies;
+    enqueue_plan(*p, st);
+  } else if (st != nullptr && c->use_graphs) {
     if (!p->apply_graph || p->apply_graph->prof != c->prof) {
       p->apply_graph.reset(new GraphRec());
       capture_graph(c, st, *p->apply_graph, [&] { enqueue_plan(*p, st); });
@@ -1956,7 +1962,8 @@ struct LanczosCache {
   std::vector<std::unique_ptr<DevBuf>> bufs;
   LanczosDev L;
   std::unique_ptr<GraphRec> graph;
-  // vector mode of the slicing (see vector_slicing): decided once per cache
+  int eager_runs = 0;
+  // vector mode of the slicing (see vector_slicing_tables): decided once per cache
   bool vs_decided = false;
   int vs_step = -1;                // the step whose operand is sliced straight from w (-1: not used)
   bool vs_sideA = true;
@@ -2229,7 +2236,10 @@ void tnx_lanczos_enqueue(tnx_network* net, int slot, tnx_tensor* v0, int nsteps,
     ProfScope ps(ctx, st, TNX_KC_VECTOR, evp ? 8.0 * (double)n * (nsteps + 2) : 0.0);
     CUDA_CHECK(tnx_launch_lanczos_finish(L, evp, st));
   };
-  if (st != nullptr && ctx->use_graphs) {
+  if (st != nullptr && ctx->use_graphs && !lc->graph && lc->eager_runs == 0) {
+    ++lc->eager_runs;   // the first solve of a plan runs eagerly (see tnx_apply_enqueue)
+    body();
+  } else if (st != nullptr && ctx->use_graphs) {
     if (!lc->graph || lc->v0 != v0->data || lc->evec != evp || lc->graph->prof != ctx->prof) {
       lc->graph.reset(new GraphRec());
       lc->v0 = v0->data;
@@ -2316,7 +2326,10 @@ extern "C" tnx_status tnx_lanczos(tnx_network* net, const char* vec_slot, tnx_te
     double* hp = (double*)ctx->pinned;
     tnx_lanczos_enqueue(net, slot, v0, nsteps, evec, ctx->stream, hp);
     CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
-    if (ctx->stream && ctx->use_graphs && ctx->prof) prof_accumulate(ctx, net->lanczos->graph->recs);
+    // a solve that ran from its graph keeps its profile records there (an eager
+    // one, the first of a plan, left them pending on the context)
+    if (ctx->stream && ctx->use_graphs && ctx->prof && net->lanczos && net->lanczos->graph)
+      prof_accumulate(ctx, net->lanczos->graph->recs);
     check_device_status(ctx);
     *eval = hp[0];
     if (nmatvec) *nmatvec = ((int32_t*)(hp + 1))[0];

@@ -122,6 +122,7 @@ struct Plan {
   tnx_ctx* ctx = nullptr;
   uint64_t serial = 0;            // unique per plan (cache key of dependent graphs)
   std::unique_ptr<GraphRec> apply_graph;
+  int eager_applies = 0;          // applies run without a graph (the first one)
   std::vector<std::unique_ptr<DevBuf>> bufs;
   std::vector<double*> h_slots, h_slots_dev;   // wanted / last uploaded
   double** d_slots = nullptr;
