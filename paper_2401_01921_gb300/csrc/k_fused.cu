@@ -24,8 +24,8 @@
 
 namespace {
 
-constexpr int FT = 256;           // threads; a tile has FR rows at most, two threads per row
-constexpr int FR = 128;
+constexpr int FR = TNX_FUSED_ROWS; // a tile has FR rows at most, two threads per row
+constexpr int FT = 2 * FR;         // threads
 constexpr int FMAXN = 64;         // output columns (rows of B_g) at most
 constexpr int FMAXK = 16;         // columns of A (ldK) at most
 
@@ -49,9 +49,9 @@ __global__ void __launch_bounds__(FT, 6) fused_skinny_kernel(const GemmGroup* __
   const FusedTile T = tiles[blockIdx.x];
   const int tid = threadIdx.x, half = tid / FR, t = tid & (FR - 1);
   const int rows = T.tP * T.tQ, W = T.W, N = T.N;
-  // output column descriptors (threads [192, 192 + N)), off the gather's path
+  // output column descriptors (threads [FR + FMAXN, FR + FMAXN + N)), off the gather's path
   if (tid >= FR + FMAXN && tid - FR - FMAXN < N && T.scol >= 0) S.s_sc[tid - FR - FMAXN] = cols[T.scol + tid - FR - FMAXN];
-  // B nonzeros (threads [128, 128 + N))
+  // B nonzeros (threads [FR, FR + N))
   const GemmGroup g = groups[T.group];
   if (half == 1 && t < N) {
     const int K = g.K;

@@ -248,6 +248,7 @@ struct FusedTile {
   int32_t p0, q0, tP, tQ;
   int32_t W, N, pad0, pad1;
 };
+#define TNX_FUSED_ROWS 128   // rows (p, q) of a fused MPO-step tile at most (two threads per row)
 cudaError_t tnx_launch_fused_skinny(const GemmGroup* groups, const FusedTile* tiles, int ntiles, const FusedCol* cols,
                                     int kp, int np, double* const* slots, cudaStream_t st);
 size_t tnx_fused_smem_bytes(int kp, int np);

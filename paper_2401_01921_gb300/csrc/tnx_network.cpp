@@ -1391,7 +1391,7 @@ bool fuse_skinny_step(Plan& p, size_t si, int ti, bool tA) {
       const size_t gcol = add_cols(ta, B.h, s.ldK[B.g], true);
       int64_t scol = -(int64_t)B.EQ - 1;   // write the rows to C
       if (ti >= 0) scol = (int64_t)add_cols(*tl, sidx[b] < 0 ? (size_t)-1 : (size_t)sidx[b], N, false);
-      const int tQ = (int)balance(B.EQ, 16), tP = (int)balance(B.EP, 128 / tQ);
+      const int tQ = (int)balance(B.EQ, 16), tP = (int)balance(B.EP, TNX_FUSED_ROWS / tQ);
       for (int p0 = 0; p0 < B.EP; p0 += tP)
         for (int q0 = 0; q0 < B.EQ; q0 += tQ)
           tiles.push_back(FusedTile{B.g, (int32_t)gcol, (int32_t)scol, (int32_t)B.row, p0, q0,
