@@ -889,55 +889,82 @@ void run_match(Plan& p, StepPlan& s) {
   for (int i = 0; i < a.nfa; ++i) a.fposA[i] = s.fa[i];
   for (int i = 0; i < a.nfb; ++i) a.fposB[i] = s.fb[i];
 
-  // temporary device buffers (freed when this function returns)
-  std::vector<std::unique_ptr<DevBuf>> tmp;
-  auto dev = [&](size_t bytes) {
-    tmp.emplace_back(new DevBuf(ctx, std::max<size_t>(bytes, 256)));
-    return tmp.back()->p;
+  // One device buffer for the call: the results first (one download), then
+  // the inputs (one upload), then the kernel's scratch; the kernel clears its
+  // scratch itself, so only the two status words are zeroed.
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = (off + std::max<size_t>(bytes, 8) + 255) & ~size_t(255);
+    return o;
   };
-  auto up = [&](const void* src, size_t bytes) {
-    void* d = dev(bytes);
-    if (bytes) CUDA_CHECK(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
-    return d;
+  const size_t o_ng = take(8);
+  const size_t o_ch = take((size_t)a.gmax * std::max(nsym, 1) * 4);
+  const size_t o_mkn = take((size_t)a.gmax * 3 * 8);
+  const size_t o_am = take((size_t)std::max<int64_t>(A.nblk, 1) * 3 * 8);
+  const size_t o_bm = take((size_t)std::max<int64_t>(B.nblk, 1) * 3 * 8);
+  const size_t out_bytes = off;
+  const size_t o_deg = take(deg.size() * 8);
+  const size_t o_kq = take(kq.size() * 4);
+  const size_t o_qa = take(A.qn.size() * 4);
+  const size_t o_qb = take(B.qn.size() * 4);
+  const size_t in_end = off;
+  const size_t o_kpres = take(kspace * 4), o_kgroup = take(kspace * 4), o_koff = take(kspace * 8);
+  const size_t o_rgroup = take(faspace * 4), o_roff = take(faspace * 8);
+  const size_t o_cgroup = take(fbspace * 4), o_coff = take(fbspace * 8);
+  const size_t o_cspres = take(cspace * 4), o_csgid = take(cspace * 4);
+  const size_t o_scan = take(((size_t)1024 * a.gmax + 3 * (size_t)a.gmax) * 8);
+  DevBuf buf(ctx, off);
+  char* d = (char*)buf.p;
+  std::vector<char> hin(in_end - out_bytes, 0);
+  auto put = [&](size_t o, const void* src, size_t bytes) {
+    if (bytes) memcpy(hin.data() + (o - out_bytes), src, bytes);
   };
-  a.deg = (const int64_t*)up(deg.data(), deg.size() * 8);
-  a.kcharge = (const int32_t*)up(kq.data(), kq.size() * 4);
-  a.qA = (const int32_t*)up(A.qn.data(), A.qn.size() * 4);
-  a.qB = (const int32_t*)up(B.qn.data(), B.qn.size() * 4);
-  a.kpres = (int32_t*)dev(kspace * 4);
-  a.kgroup = (int32_t*)dev(kspace * 4);
-  a.koff = (int64_t*)dev(kspace * 8);
-  a.rgroup = (int32_t*)dev(faspace * 4);
-  a.roff = (int64_t*)dev(faspace * 8);
-  a.cgroup = (int32_t*)dev(fbspace * 4);
-  a.coff = (int64_t*)dev(fbspace * 8);
-  a.cspres = (int32_t*)dev(cspace * 4);
-  a.csgid = (int32_t*)dev(cspace * 4);
-  a.scan_tmp = (int64_t*)dev(((size_t)1024 * a.gmax + 3 * (size_t)a.gmax) * 8);
-  a.ngroups = (int32_t*)dev(8);
+  put(o_deg, deg.data(), deg.size() * 8);
+  put(o_kq, kq.data(), kq.size() * 4);
+  put(o_qa, A.qn.data(), A.qn.size() * 4);
+  put(o_qb, B.qn.data(), B.qn.size() * 4);
+  CUDA_CHECK(cudaMemcpyAsync(d + out_bytes, hin.data(), hin.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_CHECK(cudaMemsetAsync(d + o_ng, 0, 8, ctx->stream));
+  a.deg = (const int64_t*)(d + o_deg);
+  a.kcharge = (const int32_t*)(d + o_kq);
+  a.qA = (const int32_t*)(d + o_qa);
+  a.qB = (const int32_t*)(d + o_qb);
+  a.kpres = (int32_t*)(d + o_kpres);
+  a.kgroup = (int32_t*)(d + o_kgroup);
+  a.koff = (int64_t*)(d + o_koff);
+  a.rgroup = (int32_t*)(d + o_rgroup);
+  a.roff = (int64_t*)(d + o_roff);
+  a.cgroup = (int32_t*)(d + o_cgroup);
+  a.coff = (int64_t*)(d + o_coff);
+  a.cspres = (int32_t*)(d + o_cspres);
+  a.csgid = (int32_t*)(d + o_csgid);
+  a.scan_tmp = (int64_t*)(d + o_scan);
+  a.ngroups = (int32_t*)(d + o_ng);
   a.status = a.ngroups + 1;
-  CUDA_CHECK(cudaMemsetAsync(a.ngroups, 0, 8, ctx->stream));
-  a.charges = (int32_t*)dev((size_t)a.gmax * std::max(nsym, 1) * 4);
-  a.mkn = (int64_t*)dev((size_t)a.gmax * 3 * 8);
-  a.amap = (int64_t*)dev((size_t)std::max<int64_t>(A.nblk, 1) * 3 * 8);
-  a.bmap = (int64_t*)dev((size_t)std::max<int64_t>(B.nblk, 1) * 3 * 8);
+  a.charges = (int32_t*)(d + o_ch);
+  a.mkn = (int64_t*)(d + o_mkn);
+  a.amap = (int64_t*)(d + o_am);
+  a.bmap = (int64_t*)(d + o_bm);
   CUDA_CHECK(tnx_launch_match(a, ctx->stream));
-  int32_t hs[2];
-  CUDA_CHECK(cudaMemcpyAsync(hs, a.ngroups, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  std::vector<char> hout(out_bytes);
+  CUDA_CHECK(cudaMemcpyAsync(hout.data(), d, out_bytes, cudaMemcpyDeviceToHost, ctx->stream));
   CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+  int32_t hs[2];
+  memcpy(hs, hout.data() + o_ng, 8);
   if (hs[1] == 1) fail(TNX_ERR_UNSUPPORTED, "more charge groups than the matching kernel supports");
   if (hs[1] == 2) fail(TNX_ERR_ARG, "internal: charge outside the planned range");
   if (hs[1] == 3) fail(TNX_ERR_ARG, "internal: a block's sector index lies outside its leg");
   s.G = hs[0];
+  if (s.G < 0 || s.G > a.gmax) fail(TNX_ERR_ARG, "internal: charge group count out of range");
   s.charges.resize((size_t)s.G * nsym);
   s.mkn.resize((size_t)s.G * 3);
   s.amap.resize((size_t)A.nblk * 3);
   s.bmap.resize((size_t)B.nblk * 3);
-  if (s.G && nsym) CUDA_CHECK(cudaMemcpyAsync(s.charges.data(), a.charges, s.charges.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
-  if (s.G) CUDA_CHECK(cudaMemcpyAsync(s.mkn.data(), a.mkn, s.mkn.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
-  if (A.nblk) CUDA_CHECK(cudaMemcpyAsync(s.amap.data(), a.amap, s.amap.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
-  if (B.nblk) CUDA_CHECK(cudaMemcpyAsync(s.bmap.data(), a.bmap, s.bmap.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
-  CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+  if (s.G && nsym) memcpy(s.charges.data(), hout.data() + o_ch, s.charges.size() * 4);
+  if (s.G) memcpy(s.mkn.data(), hout.data() + o_mkn, s.mkn.size() * 8);
+  if (A.nblk) memcpy(s.amap.data(), hout.data() + o_am, s.amap.size() * 8);
+  if (B.nblk) memcpy(s.bmap.data(), hout.data() + o_bm, s.bmap.size() * 8);
 }
 
 int64_t block_dim(const OpView& v, int64_t b, const std::vector<int>& legs) {
