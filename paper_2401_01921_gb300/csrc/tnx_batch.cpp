@@ -7,7 +7,10 @@
 //
 // Each instance keeps its own plan (tables, packed operands, intermediates);
 // the batch only merges the task tables, shifting every slot index by the
-// instance's offset in the merged slot table.
+// instance's offset in the merged slot table.  Instances whose plan fuses an
+// MPO step (gather, skinny product, scatter in one kernel) keep it: their
+// fused tiles join one fused launch and the relayouts it does are left out of
+// the merged relayouts; the other instances' products run as skinny tiles.
 #include <algorithm>
 #include <cstring>
 
@@ -33,6 +36,11 @@ struct BStep {
   int nst = 0;
   int kmax = 0;                 // largest K of the merged split groups
   double flops = 0, flops_skinny = 0;
+  // the fused MPO steps of the instances that fuse this step: merged tiles and
+  // column descriptors (the other instances run copies and skinny tiles)
+  FusedTile* dFT = nullptr;
+  FusedCol* dFC = nullptr;
+  int nft = 0, fkp = 0, fnp = 0;
 };
 
 struct tnx_batch {
@@ -64,19 +72,20 @@ namespace {
 
 int shift_slot(int s, int b) { return s < 0 ? s : s + b; }
 
-TaskList merge_tasks(tnx_batch& B, const std::vector<const TaskList*>& parts) {
+// parts: (instance, its task list) for the instances whose relayout runs
+TaskList merge_tasks(tnx_batch& B, const std::vector<std::pair<int, const TaskList*>>& parts) {
   std::vector<CopyTask> tasks;
   std::vector<int4> chunks;
   TaskList out;
-  // batches run the unfused kernels: bands, which only pay off inside a fused
-  // step, go back to plain tasks (small tasks of many instances pack together)
-  for (size_t i = 0; i < parts.size(); ++i) {
-    for (CopyTask t : tnx_unband_tasks(parts[i]->h)) {
-      t.src_slot = shift_slot(t.src_slot, B.base[i]);
-      t.dst_slot = shift_slot(t.dst_slot, B.base[i]);
+  // bands, which only pay off inside a fused step, go back to plain tasks
+  // (small tasks of many instances pack together)
+  for (const auto& pr : parts) {
+    for (CopyTask t : tnx_unband_tasks(pr.second->h)) {
+      t.src_slot = shift_slot(t.src_slot, B.base[pr.first]);
+      t.dst_slot = shift_slot(t.dst_slot, B.base[pr.first]);
       tasks.push_back(t);
     }
-    out.total += parts[i]->total;
+    out.total += pr.second->total;
   }
   tnx_make_copy_chunks(tasks, chunks);   // small tasks of different instances pack together
   out.n = (int)tasks.size();
@@ -90,10 +99,16 @@ void enqueue_batch(tnx_batch& B, cudaStream_t st) {
   tnx_ctx* c = B.ctx;
   const int f16 = B.prec == TNX_PREC_SPLIT_F16 ? 1 : 0;
   for (auto& s : B.steps) {
-    {
+    // the relayout lists leave out what fused steps do (their gathers, and the
+    // operands their scatters write)
+    if (s.A.n || s.B.n) {
       ProfScope ps(c, st, TNX_KC_RELAYOUT, 16.0 * (double)(s.A.total + s.B.total));
-      CUDA_CHECK(tnx_launch_copy(s.A.d, s.A.chunks, s.A.nchunks, B.d_slots, st));
-      CUDA_CHECK(tnx_launch_copy(s.B.d, s.B.chunks, s.B.nchunks, B.d_slots, st));
+      if (s.A.n) CUDA_CHECK(tnx_launch_copy(s.A.d, s.A.chunks, s.A.nchunks, B.d_slots, st));
+      if (s.B.n) CUDA_CHECK(tnx_launch_copy(s.B.d, s.B.chunks, s.B.nchunks, B.d_slots, st));
+    }
+    if (s.nft) {
+      ProfScope ps(c, st, TNX_KC_SKINNY, s.flops_skinny);
+      CUDA_CHECK(tnx_launch_fused_skinny(s.dG, s.dFT, s.nft, s.dFC, s.fkp, s.fnp, B.d_slots, st));
     }
     if (s.nts) {
       ProfScope ps(c, st, TNX_KC_SKINNY, s.flops_skinny);
@@ -177,10 +192,13 @@ extern "C" tnx_status tnx_batch_create(tnx_ctx* ctx, int n, tnx_network* const* 
     const bool split = B->prec == TNX_PREC_SPLIT_BF16 || B->prec == TNX_PREC_SPLIT_F16 || B->prec == TNX_PREC_TF32;
     for (size_t s = 0; s < nst; ++s) {
       BStep& bs = B->steps[s];
-      std::vector<const TaskList*> pa, pb;
-      for (auto* p : B->plans) {
-        pa.push_back(&p->steps[s].copyA);
-        pb.push_back(&p->steps[s].copyB);
+      // per instance: a fused step gathers its A itself, and a relayout that a
+      // fused step's scatter writes is left out
+      std::vector<std::pair<int, const TaskList*>> pa, pb;
+      for (size_t i = 0; i < B->plans.size(); ++i) {
+        const StepPlan& sp = B->plans[i]->steps[s];
+        if (!sp.nftiles && !sp.skipA) pa.push_back({(int)i, &sp.copyA});
+        if (!sp.skipB) pb.push_back({(int)i, &sp.copyB});
       }
       bs.A = merge_tasks(*B, pa);
       bs.B = merge_tasks(*B, pb);
@@ -190,10 +208,26 @@ extern "C" tnx_status tnx_batch_create(tnx_ctx* ctx, int n, tnx_network* const* 
       std::vector<KexpJob> kjobs;
       std::vector<SplitGroup> sg;
       std::vector<GemmTile> st;
+      std::vector<FusedTile> ft;
+      std::vector<FusedCol> fc;
       for (size_t i = 0; i < B->plans.size(); ++i) {
         const StepPlan& sp = B->plans[i]->steps[s];
         const int b = B->base[i];
         const int goff = (int)gg.size();
+        if (sp.nftiles) {
+          // descriptors hold device addresses of the instance's own buffers;
+          // tiles index the merged groups and descriptors
+          const int coff = (int)fc.size();
+          fc.insert(fc.end(), sp.hFC.begin(), sp.hFC.end());
+          for (FusedTile t : sp.hFT) {
+            t.group += goff;
+            t.gcol += coff;
+            if (t.scol >= 0) t.scol += coff;
+            ft.push_back(t);
+          }
+          bs.fkp = std::max(bs.fkp, sp.fkp);
+          bs.fnp = std::max(bs.fnp, sp.fnp);
+        }
         for (GemmGroup g : sp.hG) {
           g.a_slot = shift_slot(g.a_slot, b);
           g.b_slot = shift_slot(g.b_slot, b);
@@ -201,7 +235,8 @@ extern "C" tnx_status tnx_batch_create(tnx_ctx* ctx, int n, tnx_network* const* 
           gg.push_back(g);
         }
         for (GemmTile t : sp.hT) { t.group += goff; tt.push_back(t); }
-        for (GemmTile t : sp.hTs) { t.group += goff; ts.push_back(t); }
+        if (!sp.nftiles)   // a fused instance's skinny tiles run inside its fused tiles
+          for (GemmTile t : sp.hTs) { t.group += goff; ts.push_back(t); }
         bs.flops += sp.flops;
         bs.flops_skinny += sp.flops_skinny;
         if (split) {
@@ -236,6 +271,12 @@ extern "C" tnx_status tnx_batch_create(tnx_ctx* ctx, int n, tnx_network* const* 
       bs.nt = (int)tt.size();
       bs.dTs = B->upload(ts);
       bs.nts = (int)ts.size();
+      if (!ft.empty()) {
+        if (ft.size() > (size_t)INT32_MAX) fail(TNX_ERR_UNSUPPORTED, "too many fused tiles in one batch");
+        bs.dFT = B->upload(ft);
+        bs.dFC = B->upload(fc);
+        bs.nft = (int)ft.size();
+      }
       if (split) {
         // longest K first, so a persistent grid ends with short tiles
         std::stable_sort(st.begin(), st.end(), [&](const GemmTile& x, const GemmTile& y) {
@@ -259,8 +300,8 @@ extern "C" tnx_status tnx_batch_create(tnx_ctx* ctx, int n, tnx_network* const* 
         for (const GemmTile& t : st) bs.kmax = std::max(bs.kmax, (int)sg[t.group].K);
       }
     }
-    std::vector<const TaskList*> pf;
-    for (auto* p : B->plans) pf.push_back(&p->fin);
+    std::vector<std::pair<int, const TaskList*>> pf;
+    for (size_t i = 0; i < B->plans.size(); ++i) pf.push_back({(int)i, &B->plans[i]->fin});
     B->fin = merge_tasks(*B, pf);
     CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
     *out = B.release();
