@@ -456,6 +456,15 @@ __global__ void lanczos_normalize_kernel(LanczosDev L, int j) {
     vn[i] = L.w[i] * inv;
 }
 
+// A key that orders doubles as integers (-0 and +0 share key 0), and back.
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (long long)(0x8000000000000000ull - (unsigned long long)b);
+}
+__device__ __forceinline__ double dfromkey(long long key) {
+  return __longlong_as_double(key >= 0 ? key : (long long)(0x8000000000000000ull - (unsigned long long)key));
+}
+
 // Sturm count on the shared-memory copy of T: number of negative pivots of the
 // LDL^T factorisation of T - xI (b2[j] = beta_j^2, b2[0] unused).
 __device__ int sturm_count(const double* a, const double* b2, int k, double x) {
@@ -521,17 +530,37 @@ __global__ void __launch_bounds__(RT) tridiag_kernel(LanczosDev L) {
     __syncthreads();
     if (!(s_lo < s_hi) || (s_lo == lo && s_hi == hi)) break;
   }
-  if (threadIdx.x != 0) return;
-  // finish with plain bisection on the (tiny) bracket, as the oracle does
+  // Finish on the (tiny) bracket: the oracle bisects until lo and hi are
+  // adjacent doubles, which leaves hi = the smallest double of (lo, hi] whose
+  // count reaches 1.  Here the RT threads test the doubles lo+1, lo+2, ... ulps
+  // at once (a key that orders doubles like integers), after serial halving
+  // while more than RT of them remain.
+  __shared__ int s_t;
   double lo = s_lo, hi = s_hi;
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm_count(sa, sb2, k, mid) >= 1) hi = mid; else lo = mid;
+  if (threadIdx.x == 0) {
+    for (int it = 0; it < 200 && dkey(hi) - dkey(lo) > RT; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (sturm_count(sa, sb2, k, mid) >= 1) hi = mid; else lo = mid;
+    }
+    s_lo = lo;
+    s_hi = hi;
+    s_t = RT;
   }
-  const double lam = hi;
+  __syncthreads();
+  lo = s_lo;
+  hi = s_hi;
+  const long long span = dkey(hi) - dkey(lo);   // hi itself counts
+  if ((long long)threadIdx.x + 1 < span) {
+    const double x = dfromkey(dkey(lo) + threadIdx.x + 1);
+    if (sturm_count(sa, sb2, k, x) >= 1) atomicMin(&s_t, (int)threadIdx.x);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double lam = s_t < RT ? dfromkey(dkey(lo) + s_t + 1) : hi;
   *L.eval = lam;
-  // LU of T - shift I (no pivoting): sa becomes the pivots, sl the multipliers
+  // LU of T - shift I (no pivoting): sa becomes the pivots, sl the multipliers;
+  // the sweeps multiply by the pivots' reciprocals, formed once
   const double shift = lam - 1e-13 * fmax(1.0, fabs(lam));
   for (int j = 0; j < k; ++j) sa[j] -= shift;
   for (int j = 1; j < k; ++j) {
@@ -539,12 +568,13 @@ __global__ void __launch_bounds__(RT) tridiag_kernel(LanczosDev L) {
     sl[j] = sb[j] / piv;
     sa[j] -= sl[j] * sb[j];
   }
+  for (int j = 0; j < k; ++j) sb2[j] = 1.0 / (sa[j] != 0.0 ? sa[j] : 1e-300);   // sb2 is free now
   const double inv0 = 1.0 / sqrt((double)k);
   for (int j = 0; j < k; ++j) sy[j] = inv0;
   for (int sweep = 0; sweep < 3; ++sweep) {
     for (int j = 1; j < k; ++j) sy[j] -= sl[j] * sy[j - 1];
-    sy[k - 1] = sy[k - 1] / (sa[k - 1] != 0.0 ? sa[k - 1] : 1e-300);
-    for (int j = k - 2; j >= 0; --j) sy[j] = (sy[j] - sb[j + 1] * sy[j + 1]) / (sa[j] != 0.0 ? sa[j] : 1e-300);
+    sy[k - 1] = sy[k - 1] * sb2[k - 1];
+    for (int j = k - 2; j >= 0; --j) sy[j] = (sy[j] - sb[j + 1] * sy[j + 1]) * sb2[j];
     double nrm = 0.0;
     for (int j = 0; j < k; ++j) nrm += sy[j] * sy[j];
     const double inv = 1.0 / sqrt(nrm);
