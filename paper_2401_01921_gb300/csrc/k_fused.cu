@@ -28,6 +28,10 @@ constexpr int FR = TNX_FUSED_ROWS; // a tile has FR rows at most, two threads pe
 constexpr int FT = 2 * FR;         // threads
 constexpr int FMAXN = 64;         // output columns (rows of B_g) at most
 constexpr int FMAXK = 16;         // columns of A (ldK) at most
+// the prologue's thread ranges: B nonzeros by threads [FR, FR + N), output
+// column descriptors by [FR + FMAXN, FR + FMAXN + N), N <= FMAXN
+static_assert(FR + 2 * FMAXN <= FT, "the fused tile needs FR >= 2 * FMAXN rows (threads for its prologue loads)");
+static_assert((FR & (FR - 1)) == 0, "the fused tile row count must be a power of two");
 
 struct FusedSmem {
   double s_v[FMAXN][FMAXK];       // nonzero B entries of each output column
