@@ -142,6 +142,31 @@ def test_split_exact_on_integers(ctx, prec, chi, n):
     assert np.array_equal(res["f64"], res[prec])
 
 
+@pytest.mark.parametrize("K", [100, 200, 300, 700, 2000])
+@pytest.mark.parametrize("prec", ["split_bf16", "split_f16"])
+def test_split_level_sums_at_large_values(ctx, prec, K):
+    """C = A B with every entry of row i of A equal to x_i and every entry of column j of B to y_j, where
+    |x_i| and |y_j| are m = v 2^-40 times powers of two and v = 63 (2^35 + 2^28 + 2^21): each entry is its own
+    row (column) maximum, so its balanced 7-bit digits are (63, 63, 63, 0, 0, 0), every digit product of a
+    level adds with the same sign, and no dropped level holds a nonzero term.  The level sums of a 640-long
+    chunk reach 3 * 640 * 63^2 = 7.6e6, above the 2^22 that the one-add integer conversion covers, and the
+    product is exact: C_ij = K x_i y_j, exact in FP64 (51 significant bits).  K spans one chunk with every
+    level bound by 2^22 (100), fewer such levels (200, 300), and several chunks (700, 2000)."""
+    import paper_2401_01921_gb300 as tnx
+    from paper_2401_01921_gb300.heff import build_network
+    M, N = 200, 100
+    m = 63.0 * (2.0 ** 35 + 2.0 ** 28 + 2.0 ** 21) * 2.0 ** -40
+    x = np.array([(1.0 if i % 3 else -1.0) * m * 2.0 ** (i % 7 - 3) for i in range(M)])
+    y = np.array([(-1.0 if j % 4 == 1 else 1.0) * m * 2.0 ** (j % 5 - 2) for j in range(N)])
+    reg = lambda n: (tnx.BD_REG, [((), n)])
+    tensors = {"A": ([reg(M), reg(K)], lambda c: x[c[0]]), "B": ([reg(K), reg(N)], lambda c: y[c[1]])}
+    exact = float(K) * np.outer(x, y)
+    for p in ("f64", prec):
+        net, T, B = build_network(ctx, "A: i, k\nB: k, j\nTOUT: i, j\nORDER:\n", tensors, 0, prec=p)
+        got = net.launch([B["A"][0], B["B"][1]]).download().reshape(M, N)
+        assert np.array_equal(got, exact), (p, float(np.abs(got - exact).max()))
+
+
 def test_split_lanczos(ctx):
     wl = I.heisenberg_workload(512, 20)
     import paper_2401_01921_gb300 as tnx
