@@ -21,7 +21,7 @@ beside the same trace served one request at a time in plain FP64;
 
   python bench.py [--gpus N --steps K --warmup W] [--impl tnx|reference]
                   [--workload chi2048|chi512|dense32|batch256|serve|env2048|dmrg]
-                  [--prec auto|split_bf16|f64|...]
+                  [--prec auto|split_bf16|f64|...] [--max-bond 512 (dmrg)]
 
 --impl reference times the plain CPU FP64 oracle on the host (one thread,
 bounded sample) on the same metric.  With N > 1 (torchrun, NCCL) every rank
@@ -534,8 +534,8 @@ def run_env(args, torch, dev, tnx, I, dist, world, rank, local):
 # ------------------------------------------------------------------ two-site DMRG sweeps (Sec. 11)
 def run_dmrg(args, torch, dev, tnx, I, rank, local):
     """Two-site DMRG sweeps of the open XX chain (the paper's benchmark model, M_D = 4),
-    N = 40 sites, bond dimension raised 64 -> 128 -> 256 -> 512 (two sweeps each), H_eff
-    products in split BF16; the energy against the free-fermion closed form."""
+    N = 40 sites, bond dimension doubled from 64 up to --max-bond (default 512; two sweeps
+    each), H_eff products in split BF16; the energy against the free-fermion closed form."""
     import numpy as np
 
     from paper_2401_01921_gb300.heff import make_bonds
@@ -551,18 +551,21 @@ def run_dmrg(args, torch, dev, tnx, I, rank, local):
     exact = float(np.sum(e[e < 0]))   # free fermions with hopping 1/2: fill the negative levels
     sweeps = []
     t0 = time.perf_counter()
-    for dim in (64, 128, 256, 512):
+    dims = [64]
+    while dims[-1] * 2 <= args.max_bond:
+        dims.append(dims[-1] * 2)
+    for dim in dims:
         for _ in range(2):
             r = d.sweep(dim, 0.0, LANCZOS_STEPS, "split_bf16")
             sweeps.append({"maxdim": dim, "energy": r["energy"], "rel_err": abs(r["energy"] - exact) / abs(exact),
                            "max_bond": r["max_bond"], "max_trunc_err": r["max_trunc_err"], "ms": r["ms"]})
     total = time.perf_counter() - t0
     last = sweeps[-1]
-    line = {"metric": "two-site DMRG sweep time (s) at bond dimension 512, XX chain N=40",
+    line = {"metric": f"two-site DMRG sweep time (s) at bond dimension {dims[-1]}, XX chain N=40",
             "value": last["ms"]["sweep"] / 1e3, "unit": "s", "n_gpus": 1, "steps": len(sweeps), "warmup": 0,
             "ms_per_step": last["ms"]["sweep"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64 via split_bf16 slices (H_eff); FP64 Lanczos vectors and SVD", "data": "synthetic",
-            "config": {"workload": "xx_chain_n40_dmrg_chi64to512", "nsites": nsites, "D": 4,
+            "config": {"workload": f"xx_chain_n40_dmrg_chi64to{dims[-1]}", "nsites": nsites, "D": 4,
                        "lanczos_steps": LANCZOS_STEPS, "exact_energy": exact},
             "sweeps": sweeps, "total_s": total, "cpu_baseline": None}
     if rank == 0:
@@ -675,6 +678,7 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true", help="skip the oracle comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving sweep")
     ap.add_argument("--no-secondary", action="store_true", help="skip the chi = 512 solve")
+    ap.add_argument("--max-bond", type=int, default=512, help="dmrg: largest bond dimension of the ramp")
     ap.add_argument("--order", default=None,
                     help='contraction order: "sparse" (block-sparse-cost search, default; batch256: the MPO pair '
                          'pre-contracted), "dense" '
