@@ -156,10 +156,11 @@ __device__ bool grid_barrier(unsigned long long* count, int* status) {
     asm volatile("atom.add.release.gpu.u64 %0, [%1], 1;" : "=l"(old) : "l"(count) : "memory");
     const unsigned long long target = (old / gridDim.x + 1) * (unsigned long long)gridDim.x;
     const long long t0 = clock64();
-    for (;;) {
+    for (unsigned it = 1;; ++it) {
       unsigned long long cur;
       asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(cur) : "l"(count) : "memory");
       if (cur >= target) break;
+      if ((it & 31u) != 0) continue;   // the error word and the clock every 32 polls
       if (*(volatile int*)status != 0) {
         ok = 0;
         break;
@@ -184,10 +185,101 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-constexpr int VB = 8;     // vector entries per lane held in registers by the cooperative kernel
+// Vector entries per lane held in registers (VB = 8 or 16: vectors of up to 256
+// or 512 entries) by the cooperative Jacobi and the application of Q; the
+// launchers take the smaller width that holds the longest vector of the launch.
 constexpr int CJT = 32;   // threads per CTA of the cooperative kernel: one pair-warp per CTA, so that the
                           // pairs of a round spread over as many SMs (and FP64 pipes) as there are pairs
 
+// One rotation of the pair (p, q) of block g (the arithmetic of
+// jacobi_round_kernel); off_w takes the squared relative off-diagonal.
+template <int VB>
+__device__ __forceinline__ void jacobi_pair(const SvdGroup& g, int p, int q, int lane, double& off_w) {
+  double* xp = g.X + (int64_t)p * g.r;
+  double* xq = g.X + (int64_t)q * g.r;
+  double* jp = g.J + (int64_t)p * g.c;
+  double* jq = g.J + (int64_t)q * g.c;
+  // vectors and J rows of up to 32 VB entries stay in registers between
+  // the dots and the rotation: every load of the pair is issued at once
+  // (one trip to L2 instead of one per 32 entries)
+  const bool in_regs = g.r <= 32 * VB && g.c <= 32 * VB;
+  double u[VB], v[VB], ju[VB], jv[VB];
+  double a = 0.0, b = 0.0, c = 0.0;
+  if (in_regs) {
+#pragma unroll
+    for (int k = 0; k < VB; ++k) {
+      const int e = lane + 32 * k;
+      u[k] = e < g.r ? xp[e] : 0.0;
+      v[k] = e < g.r ? xq[e] : 0.0;
+      ju[k] = e < g.c ? jp[e] : 0.0;
+      jv[k] = e < g.c ? jq[e] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < VB; ++k) {
+      a = fma(u[k], u[k], a);
+      b = fma(v[k], v[k], b);
+      c = fma(u[k], v[k], c);
+    }
+  } else {
+#pragma unroll 4
+    for (int64_t e = lane; e < g.r; e += 32) {
+      const double uu = xp[e], vv = xq[e];
+      a = fma(uu, uu, a);
+      b = fma(vv, vv, b);
+      c = fma(uu, vv, c);
+    }
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  if (!(a > 0.0 && b > 0.0)) return;
+  // squared relative off-diagonal; the same tests as |gamma| / sqrt(alpha beta)
+  // against 1e-15 and tol, with one FP64 division instead of a root and two
+  const double ab = a * b, c2 = c * c;
+  off_w = fmax(off_w, c2 / ab);
+  if (c2 <= 1e-30 * ab) return;
+  // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) with zeta = d / (2 gamma), d = beta - alpha,
+  // multiplied through by 2 |gamma|: one root, one division and one reciprocal root
+  const double d = b - a;
+  double t;
+  if (fabs(d) < 1e150 && fabs(c) < 1e150) {
+    t = 2.0 * c / (d + copysign(sqrt(fma(d, d, 4.0 * c2)), d));
+  } else {   // squares out of range: the quotient form
+    const double zeta = d / (2.0 * c), az = fabs(zeta);
+    t = az > 1e100 ? 0.5 / az : 1.0 / (az + sqrt(1.0 + az * az));
+    if (zeta < 0.0) t = -t;
+  }
+  const double cs = rsqrt(fma(t, t, 1.0)), sn = cs * t;
+  if (in_regs) {
+#pragma unroll
+    for (int k = 0; k < VB; ++k) {
+      const int e = lane + 32 * k;
+      if (e < g.r) {
+        xp[e] = cs * u[k] - sn * v[k];
+        xq[e] = sn * u[k] + cs * v[k];
+      }
+      if (e < g.c) {
+        jp[e] = cs * ju[k] - sn * jv[k];
+        jq[e] = sn * ju[k] + cs * jv[k];
+      }
+    }
+  } else {
+#pragma unroll 4
+    for (int64_t e = lane; e < g.r; e += 32) {
+      const double uu = xp[e], vv = xq[e];
+      xp[e] = cs * uu - sn * vv;
+      xq[e] = sn * uu + cs * vv;
+    }
+#pragma unroll 4
+    for (int e = lane; e < g.c; e += 32) {
+      const double uu = jp[e], vv = jq[e];
+      jp[e] = cs * uu - sn * vv;
+      jq[e] = sn * uu + cs * vv;
+    }
+  }
+}
+
+template <int VB>
 __global__ void __launch_bounds__(CJT) jacobi_coop_kernel(const SvdGroup* __restrict__ groups,
                                                          const int2* __restrict__ slots, int nslots, int maxcp,
                                                          int max_sweeps, double tol2, unsigned long long* offmax,
@@ -198,13 +290,12 @@ __global__ void __launch_bounds__(CJT) jacobi_coop_kernel(const SvdGroup* __rest
   int sw = 0;
   bool ok = true;
   while (ok && sw < max_sweeps) {
+    double off_w = 0.0;   // this warp's largest squared relative off-diagonal of the sweep
     for (int round = 0; round < maxcp - 1 && ok; ++round) {
-      double off_w = 0.0;
       for (int si = gw; si < nslots; si += nwarps) {
         const int2 sl = slots[si];
         const SvdGroup g = groups[sl.x];
-        const int cp = g.c + (g.c & 1);
-        if (cp < 2) continue;
+        const int cp = g.c + (g.c & 1);   // >= 2: a block of one vector has no slot
         const int kk = round % (cp - 1);
         const int i = sl.y;
         int p, q;
@@ -216,91 +307,11 @@ __global__ void __launch_bounds__(CJT) jacobi_coop_kernel(const SvdGroup* __rest
           q = (kk - i + cp - 1) % (cp - 1);
         }
         if (p > q) { const int t = p; p = q; q = t; }
-        if (q >= g.c) continue;         // the pad index
-        double* xp = g.X + (int64_t)p * g.r;
-        double* xq = g.X + (int64_t)q * g.r;
-        double* jp = g.J + (int64_t)p * g.c;
-        double* jq = g.J + (int64_t)q * g.c;
-        // vectors and J rows of up to 32 VB entries stay in registers between
-        // the dots and the rotation: every load of the pair is issued at once
-        // (one trip to L2 instead of one per 32 entries)
-        const bool in_regs = g.r <= 32 * VB && g.c <= 32 * VB;
-        double u[VB], v[VB], ju[VB], jv[VB];
-        double a = 0.0, b = 0.0, c = 0.0;
-        if (in_regs) {
-#pragma unroll
-          for (int k = 0; k < VB; ++k) {
-            const int e = lane + 32 * k;
-            u[k] = e < g.r ? xp[e] : 0.0;
-            v[k] = e < g.r ? xq[e] : 0.0;
-            ju[k] = e < g.c ? jp[e] : 0.0;
-            jv[k] = e < g.c ? jq[e] : 0.0;
-          }
-#pragma unroll
-          for (int k = 0; k < VB; ++k) {
-            a = fma(u[k], u[k], a);
-            b = fma(v[k], v[k], b);
-            c = fma(u[k], v[k], c);
-          }
-        } else {
-#pragma unroll 4
-          for (int64_t e = lane; e < g.r; e += 32) {
-            const double uu = xp[e], vv = xq[e];
-            a = fma(uu, uu, a);
-            b = fma(vv, vv, b);
-            c = fma(uu, vv, c);
-          }
-        }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        c = warp_sum(c);
-        if (!(a > 0.0 && b > 0.0)) continue;
-        // squared relative off-diagonal; the same tests as |gamma| / sqrt(alpha beta)
-        // against 1e-15 and tol, with one FP64 division instead of a root and two
-        const double ab = a * b, c2 = c * c;
-        off_w = fmax(off_w, c2 / ab);
-        if (c2 <= 1e-30 * ab) continue;
-        // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) with zeta = d / (2 gamma), d = beta - alpha,
-        // multiplied through by 2 |gamma|: one root, one division and one reciprocal root
-        const double d = b - a;
-        double t;
-        if (fabs(d) < 1e150 && fabs(c) < 1e150) {
-          t = 2.0 * c / (d + copysign(sqrt(fma(d, d, 4.0 * c2)), d));
-        } else {   // squares out of range: the quotient form
-          const double zeta = d / (2.0 * c), az = fabs(zeta);
-          t = az > 1e100 ? 0.5 / az : 1.0 / (az + sqrt(1.0 + az * az));
-          if (zeta < 0.0) t = -t;
-        }
-        const double cs = rsqrt(fma(t, t, 1.0)), sn = cs * t;
-        if (in_regs) {
-#pragma unroll
-          for (int k = 0; k < VB; ++k) {
-            const int e = lane + 32 * k;
-            if (e < g.r) {
-              xp[e] = cs * u[k] - sn * v[k];
-              xq[e] = sn * u[k] + cs * v[k];
-            }
-            if (e < g.c) {
-              jp[e] = cs * ju[k] - sn * jv[k];
-              jq[e] = sn * ju[k] + cs * jv[k];
-            }
-          }
-        } else {
-#pragma unroll 4
-          for (int64_t e = lane; e < g.r; e += 32) {
-            const double uu = xp[e], vv = xq[e];
-            xp[e] = cs * uu - sn * vv;
-            xq[e] = sn * uu + cs * vv;
-          }
-#pragma unroll 4
-          for (int e = lane; e < g.c; e += 32) {
-            const double uu = jp[e], vv = jq[e];
-            jp[e] = cs * uu - sn * vv;
-            jq[e] = sn * uu + cs * vv;
-          }
-        }
+        if (q < g.c) jacobi_pair<VB>(g, p, q, lane, off_w);   // q = cp - 1 >= c: the pad index
       }
-      if (lane == 0 && off_w > 0.0) atomicMax(&offmax[sw], (unsigned long long)__double_as_longlong(off_w));
+      // one atomic per warp and sweep, before the sweep's last barrier
+      if (round == maxcp - 2 && lane == 0 && off_w > 0.0)
+        atomicMax(&offmax[sw], (unsigned long long)__double_as_longlong(off_w));
       ok = grid_barrier(bar, status);
     }
     if (!ok) break;
@@ -470,6 +481,7 @@ __global__ void qr_gather_r_kernel(const SvdQr* __restrict__ qs, int nq) {
 // vector of A, 0 when sigma_p = 0); Xf[p,:] = sigma_p Q Jr[p,:]^T, with Q
 // applied as H_0 H_1 ... H_{c-1} to (Jr[p,:], 0, ..., 0).  Lane l keeps the
 // entries e = l (mod 32) of z throughout, in registers when r <= 32 VB.
+template <int VB>
 __global__ void qr_apply_kernel(const SvdQr* __restrict__ qs, const int2* __restrict__ vecs, int nvec) {
   tnx_grid_dependency();
   const int lane = threadIdx.x & 31;
@@ -626,15 +638,16 @@ cudaError_t tnx_launch_jacobi_round(const SvdGroup* groups, const int2* slots, i
   return cudaGetLastError();
 }
 
-cudaError_t tnx_launch_jacobi_coop(const SvdGroup* groups, const int2* slots, int nslots, int maxcp, int max_sweeps,
-                                   double tol, unsigned long long* offmax, unsigned long long* bar, int* status,
-                                   int* sweeps_out, cudaStream_t st) {
-  if (nslots <= 0 || maxcp < 2) return cudaSuccess;
+namespace {
+template <int VB>
+cudaError_t launch_jacobi_coop(const SvdGroup* groups, const int2* slots, int nslots, int maxcp, int max_sweeps,
+                               double tol, unsigned long long* offmax, unsigned long long* bar, int* status,
+                               int* sweeps_out, cudaStream_t st) {
   int dev = 0, nsm = 0, per_sm = 0, coop = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel, CJT, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop_kernel<VB>, CJT, 0);
   if (e != cudaSuccess) return e;
   if (!coop || per_sm < 1) return cudaErrorNotSupported;
   int grid = nsm * (per_sm < 4 ? per_sm : 4);
@@ -643,10 +656,21 @@ cudaError_t tnx_launch_jacobi_coop(const SvdGroup* groups, const int2* slots, in
   double tol2 = tol * tol;   // the kernel compares squared relative off-diagonals
   void* args[] = {(void*)&groups, (void*)&slots, (void*)&nslots, (void*)&maxcp, (void*)&max_sweeps, (void*)&tol2,
                   (void*)&offmax, (void*)&bar, (void*)&status, (void*)&sweeps_out};
-  e = cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, dim3(grid), dim3(CJT), args, 0, st);
+  e = cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel<VB>, dim3(grid), dim3(CJT), args, 0, st);
   if (e != cudaSuccess) return e;
   tnx_note_launch(1);
   return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t tnx_launch_jacobi_coop(const SvdGroup* groups, const int2* slots, int nslots, int maxcp, int maxlen,
+                                   int max_sweeps, double tol, unsigned long long* offmax, unsigned long long* bar,
+                                   int* status, int* sweeps_out, cudaStream_t st) {
+  if (nslots <= 0 || maxcp < 2) return cudaSuccess;
+  return maxlen <= 32 * 8 ? launch_jacobi_coop<8>(groups, slots, nslots, maxcp, max_sweeps, tol, offmax, bar, status,
+                                                  sweeps_out, st)
+                          : launch_jacobi_coop<16>(groups, slots, nslots, maxcp, max_sweeps, tol, offmax, bar, status,
+                                                   sweeps_out, st);
 }
 
 cudaError_t tnx_launch_qr_coop(const SvdQr* qs, const int2* slots, int nslots, int maxc, unsigned long long* bar,
@@ -679,11 +703,12 @@ cudaError_t tnx_launch_qr_gather_r(const SvdQr* qs, int nq, int maxc, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t tnx_launch_qr_apply(const SvdQr* qs, const int2* vecs, int nvec, cudaStream_t st) {
+cudaError_t tnx_launch_qr_apply(const SvdQr* qs, const int2* vecs, int nvec, int maxr, cudaStream_t st) {
   if (nvec <= 0) return cudaSuccess;
   // one warp per vector, two warps per CTA: the vectors spread over the SMs' FP64 pipes
   const int grid = (nvec + 1) / 2;
-  const cudaError_t le = tnx_launch(qr_apply_kernel, dim3(grid), dim3(64), 0, st, qs, vecs, nvec);
+  const cudaError_t le = maxr <= 32 * 8 ? tnx_launch(qr_apply_kernel<8>, dim3(grid), dim3(64), 0, st, qs, vecs, nvec)
+                                        : tnx_launch(qr_apply_kernel<16>, dim3(grid), dim3(64), 0, st, qs, vecs, nvec);
   if (le != cudaSuccess) return le;
   tnx_note_launch(1);
   return cudaGetLastError();

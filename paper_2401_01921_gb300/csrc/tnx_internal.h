@@ -351,14 +351,16 @@ cudaError_t tnx_launch_qr_coop(const SvdQr* qs, const int2* slots, int nslots, i
 // Xr = R (rows, zero below the diagonal) and Jr = identity for every block
 cudaError_t tnx_launch_qr_gather_r(const SvdQr* qs, int nq, int maxc, cudaStream_t st);
 // after the Jacobi on Xr: sigma, J and Xf for every (block, vector)
-cudaError_t tnx_launch_qr_apply(const SvdQr* qs, const int2* vecs, int nvec, cudaStream_t st);
+// (maxr: the longest vector of the launch, which picks the register width)
+cudaError_t tnx_launch_qr_apply(const SvdQr* qs, const int2* vecs, int nvec, int maxr, cudaStream_t st);
 // round r of a sweep over slots (group, pair index); maxoff gets the largest
 // |x_p . x_q| / (|x_p| |x_q|) met, as the bits of a non-negative double
 // every round and sweep in one cooperative launch; offmax[max_sweeps], *bar
-// and status zeroed by the caller; cudaErrorNotSupported without cooperative launch
-cudaError_t tnx_launch_jacobi_coop(const SvdGroup* groups, const int2* slots, int nslots, int maxcp, int max_sweeps,
-                                   double tol, unsigned long long* offmax, unsigned long long* bar, int* status,
-                                   int* sweeps_out, cudaStream_t st);
+// and status zeroed by the caller; cudaErrorNotSupported without cooperative launch;
+// maxlen: the longest vector or J row of the launch, which picks the register width
+cudaError_t tnx_launch_jacobi_coop(const SvdGroup* groups, const int2* slots, int nslots, int maxcp, int maxlen,
+                                   int max_sweeps, double tol, unsigned long long* offmax, unsigned long long* bar,
+                                   int* status, int* sweeps_out, cudaStream_t st);
 cudaError_t tnx_launch_jacobi_round(const SvdGroup* groups, const int2* slots, int nslots, int round,
                                     unsigned long long* maxoff, cudaStream_t st);
 cudaError_t tnx_launch_vector_norms(const SvdGroup* groups, const int2* vecs, int nvec, cudaStream_t st);

@@ -120,12 +120,13 @@ void tnx_svd_run(tnx_tensor* t, int rowrank, int64_t keepdim, double err, const 
   double* dS = (double*)SG.p;
   std::vector<SvdGroup> hg(ngr);
   std::vector<int2> slots, vecs;
-  int maxcp = 0;
+  int maxcp = 0, maxr = 0;
   for (int i = 0; i < ngr; ++i) {
     Group* G = groups[i];
     hg[i] = SvdGroup{dX + G->offX, dJ + G->offJ, dS + G->offS, G->c, G->r};
     const int cp = G->c + (G->c & 1);
     maxcp = std::max(maxcp, cp);
+    maxr = std::max(maxr, G->r);   // r >= c
     for (int s = 0; s < cp / 2; ++s) slots.push_back(make_int2(i, s));
     for (int p = 0; p < G->c; ++p) vecs.push_back(make_int2(i, p));
   }
@@ -224,9 +225,10 @@ void tnx_svd_run(tnx_tensor* t, int rowrank, int64_t keepdim, double err, const 
     const cudaError_t ce = tnx_launch_qr_coop(dq, dqs, (int)qslots.size(), maxc, w, qstat, st);
     if (ce == cudaSuccess) {
       CUDA_CHECK(tnx_launch_qr_gather_r(dq, ngr, maxc, st));
-      CUDA_CHECK(tnx_launch_jacobi_coop(dr, dslots, (int)slots.size(), maxcp, MAX_SWEEPS, 1e-13, w + 2,
+      // the sweeps run on R: vectors of c entries
+      CUDA_CHECK(tnx_launch_jacobi_coop(dr, dslots, (int)slots.size(), maxcp, maxc, MAX_SWEEPS, 1e-13, w + 2,
                                         w + MAX_SWEEPS + 2, jstat, jstat + 1, st));
-      CUDA_CHECK(tnx_launch_qr_apply(dq, dvecs, (int)vecs.size(), st));
+      CUDA_CHECK(tnx_launch_qr_apply(dq, dvecs, (int)vecs.size(), maxr, st));
       int hs[4] = {0, 0, 0, 0};
       CUDA_CHECK(cudaMemcpyAsync(hs, qstat, 4, cudaMemcpyDeviceToHost, st));
       CUDA_CHECK(cudaMemcpyAsync(hs + 2, jstat, 8, cudaMemcpyDeviceToHost, st));
@@ -251,8 +253,8 @@ void tnx_svd_run(tnx_tensor* t, int rowrank, int64_t keepdim, double err, const 
     unsigned long long* w = (unsigned long long*)up(zero.data(), zero.size() * 8);
     unsigned long long* bar = w + MAX_SWEEPS;
     int* cstat = (int*)(w + MAX_SWEEPS + 1);
-    const cudaError_t ce = tnx_launch_jacobi_coop(dg, dslots, (int)slots.size(), maxcp, MAX_SWEEPS, 1e-13, w, bar,
-                                                  cstat, cstat + 1, st);
+    const cudaError_t ce = tnx_launch_jacobi_coop(dg, dslots, (int)slots.size(), maxcp, maxr, MAX_SWEEPS, 1e-13, w,
+                                                  bar, cstat, cstat + 1, st);
     if (ce == cudaSuccess) {
       int hs[2] = {0, 0};
       CUDA_CHECK(cudaMemcpyAsync(hs, cstat, sizeof(hs), cudaMemcpyDeviceToHost, st));
