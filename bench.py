@@ -20,7 +20,7 @@ beside the same trace served one request at a time in plain FP64;
 ``secondary`` holds the chi = 512 solve.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl tnx|reference]
-                  [--workload chi2048|chi512|dense32|batch256|serve|env2048|dmrg]
+                  [--workload chi2048|chi512|chi4096|dense32|batch256|serve|env2048|dmrg]
                   [--prec auto|split_bf16|f64|...] [--max-bond 512 (dmrg)]
 
 --impl reference times the plain CPU FP64 oracle on the host (one thread,
@@ -69,6 +69,8 @@ def workload(name: str):
         return I.heisenberg_workload(2048, 40, sector_scale=True), "heisenberg_u1_chi2048_d2_D5_sectorscaled_lanczos20"
     if name == "dense32":
         return I.dense_workload(32), "heisenberg_dense_chi32_d2_D5_lanczos20"
+    if name == "chi4096":
+        return I.heisenberg_workload(4096, 80, sector_scale=True), "heisenberg_u1_chi4096_d2_D5_sectorscaled_lanczos20"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -839,6 +841,8 @@ def main():
         lib_applies["f64"] = out64.block_dict()
         extra["fp64_value"] = fp64_value
         extra["fp64_ms_per_step"] = sum(r64["times"]) / len(r64["times"])
+        extra["fp64_eigenvalue"] = lib_evals["f64"]
+        extra["eigenvalue_rel_diff_vs_fp64"] = abs(lib_evals[prec] - lib_evals["f64"]) / abs(lib_evals["f64"])
         extra["speedup_vs_fp64"] = value / fp64_value
         extra["fp64_order"] = net64.get_order()
         del out64, net64, T64, B64, evec64
