@@ -185,14 +185,15 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Vector entries per lane held in registers (VB = 8 or 16: vectors of up to 256
-// or 512 entries) by the cooperative Jacobi and the application of Q; the
-// launchers take the smaller width that holds the longest vector of the launch.
 constexpr int CJT = 32;   // threads per CTA of the cooperative kernel: one pair-warp per CTA, so that the
                           // pairs of a round spread over as many SMs (and FP64 pipes) as there are pairs
 
-// One rotation of the pair (p, q) of block g (the arithmetic of
-// jacobi_round_kernel); off_w takes the squared relative off-diagonal.
+// One rotation of the pair (p, q) of block g by one warp: the three dots, the
+// test and the rotation of jacobi_round_kernel, the test on the squared
+// relative off-diagonal (kept in off_w) and the rotation angle from one root.
+// VB: vector entries per lane held in registers (8 or 16, vectors of up to 256
+// or 512 entries; the launchers take the smaller width that holds the longest
+// vector of the launch, and the same for applying Q); longer vectors stream.
 template <int VB>
 __device__ __forceinline__ void jacobi_pair(const SvdGroup& g, int p, int q, int lane, double& off_w) {
   double* xp = g.X + (int64_t)p * g.r;
