@@ -278,9 +278,11 @@ def run_batch(args, torch, dev, tnx, I, build_network, dist, world, rank, local)
     count = 256
     chis = I.batched_hubbard_chis(count)
     ctx = tnx.Context(local)
-    # contraction order: the headline's tree, MPO pair pre-contracted (measured 16% faster per batch step than the
-    # tree the searches pick for these Hubbard instances, whose cost models count flops only), unless --order is given
-    o = args.order or "(L,((psi,R),(W1,W2)))"
+    # contraction order, unless --order is given: the MPO pair pre-contracted (16% faster per batch step than the
+    # tree the searches pick for these Hubbard instances, whose cost models count flops only), and L taken as the
+    # right operand of the last product: a charge group's rows of L are one sector of a' (1-30 states here), which
+    # fill the 64-column side of the split-GEMM tiles better than the 128-row side (GEMM 17.6 -> 12.2 ms per 10 steps)
+    o = args.order or "(((psi,R),(W1,W2)),L)"
     order = {"sparse": "sparse", "dense": None}.get(o, o)
     res = {}
     prof_all = {}

@@ -76,12 +76,13 @@ def test_split_lanczos_chi2048_sector_scaled_vs_oracle(ctx):
     _check_solve(ctx, I.heisenberg_workload(2048, 40, sector_scale=True), "split_bf16", BENCH_ORDER, 20, 1e-10, 1e-8)
 
 
-def test_batch_spanning_chi64_to_1024_vs_oracle(ctx):
+@pytest.mark.parametrize("order", ["(L,(((psi,R),W2),W1))", "(((psi,R),(W1,W2)),L)"])
+def test_batch_spanning_chi64_to_1024_vs_oracle(ctx, order):
     """Eight Hubbard instances from chi = 64 to 1024 in one batch (split BF16, autotuned persistent
     grid): each instance's output against the oracle (relative Frobenius <= 1e-10) and against its own
-    single launch (bit-identical)."""
+    single launch (bit-identical).  Orders: the dense-cost optimum, and the batch benchmark's tree,
+    whose last product takes L as its right operand."""
     import paper_2401_01921_gb300 as tnx
-    order = "(L,(((psi,R),W2),W1))"
     chis = [64, 96, 160, 256, 384, 600, 800, 1024]
     wls = [I.hubbard_workload(c, seed_base=1000 + 4 * i) for i, c in enumerate(chis)]
     built = [lib_heff(ctx, wl, prec="split_bf16", order=order) for wl in wls]
