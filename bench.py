@@ -218,6 +218,7 @@ def oracle_sample(wname: str, order, seconds: float):
 
 WORKLOAD_NAMES = {"chi512": "heisenberg_u1_chi512_d2_D5_lanczos20",
                   "chi2048": "heisenberg_u1_chi2048_d2_D5_sectorscaled_lanczos20",
+                  "chi4096": "heisenberg_u1_chi4096_d2_D5_sectorscaled_lanczos20",
                   "dense32": "heisenberg_dense_chi32_d2_D5_lanczos20"}
 
 

@@ -18,3 +18,4 @@ def test_workload_table(name, chi, nsec, scaled):
     assert len(wl.left_sectors) == nsec and sum(d for _, d in wl.left_sectors) == chi
     assert wl.sector_scale == scaled
     assert f"chi{chi}" in wname and ("sectorscaled" in wname) == scaled and wname.endswith("lanczos20")
+    assert bench.WORKLOAD_NAMES[name] == wname   # the oracle sample of the CPU baseline finds it by that name
